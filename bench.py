@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Benchmark of the Split Bregman self-repelling snake hot path on GB300.
+
+One step = one outer iteration of Alg. 1 (S = 3 semi-implicit inner steps of
+Eq. (37), each with the repulsion window sum and the FFT solve of Eqs.
+(31)-(33), then the w update of Eqs. (41), (42), (40) and the Bregman update
+of Eq. (23)) over the whole image.  Metric: Mpixel.iter/s = H * W * steps /
+seconds.
+
+Default workload: the 2048 x 2048 six-ellipse scene (ribbons 3 px, gaps 2 px,
+noise 0.1, window l = R = d = 4), the size at which the HBM-roofline target
+is stated.  Inputs are resident in HBM when the timed region starts; L2 is
+flushed between timed steps (a 256 MiB write) outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+Under torchrun (N > 1) every rank runs an independent replica (the method has
+no cross-image exchange); value = all ranks' pixel-iterations / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("SR Mpixel·iter/s (% HBM peak); s per converged mask, plain vs "
+          "learned+batched")
+UNIT = "Mpixel·iter/s"
+
+# Algorithmic bytes per pixel of one launch of each kernel (FP32 planes):
+#   rhs_rowfft: read psi, g, w1, w2, b1, b2 (24 B), write the half spectrum (4 B)
+#   colsolve:   read and write the half spectrum (8 B)
+#   rowifft:    read the half spectrum (4 B) and psi (4 B), write psi (4 B)
+#   wb_update:  read phi, g, w1, w2, b1, b2 (24 B), write w1, w2, b1, b2 (16 B)
+BYTES_PER_PX = {"rhs_rowfft": 28, "colsolve": 8, "rowifft": 12, "wb_update": 40}
+KERNEL_NAMES = {"rhs_rowfft": "k_rowfwd", "colsolve": "k_colsolve", "rowifft": "k_rowinv",
+                "wb_update": "k_wb_update"}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("sr_kernels.cu", "sr_internal.h"):
+        with open(os.path.join(ROOT, "paper_2003_12693_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source and the same workload; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("source_hash") != _kernel_source_hash():
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle legs
+# ----------------------------------------------------------------------------
+def _oracle_rate(f, phi0, params: dict, budget_s: float, min_iters: int = 1):
+    """Time the FP64 oracle as it stands on the host cores: whole outer
+    iterations until the time budget is used.  Returns (Mpixel.iter/s, iters, s)."""
+    import numpy as np
+
+    import oracle
+    p = oracle.Params.from_dict(params)
+    g = oracle.edge(f)
+    st = oracle.initial_state(phi0)
+    H, W = f.shape
+    iters, t0 = 0, time.perf_counter()
+    while True:
+        oracle.iterate(st, g, 1, p)
+        iters += 1
+        el = time.perf_counter() - t0
+        if iters >= min_iters and el >= budget_s:
+            break
+    del np
+    return H * W * iters / el / 1e6, iters, el
+
+
+def _cores() -> int:
+    return int(os.environ.get("OMP_NUM_THREADS") or os.cpu_count() or 1)
+
+
+def run_reference(args, wl, rank: int, world: int):
+    if rank != 0:
+        return
+    from paper_2003_12693_gb300 import synth  # noqa: F401
+    f, phi0 = wl.image(), wl.phi0()
+    params = wl.params()
+    # per-step sample: one outer iteration on the largest centred crop that keeps
+    # the whole run within about two minutes
+    per_step = 120.0 / max(1, args.steps + args.warmup)
+    import numpy as np
+
+    import oracle
+    p = oracle.Params.from_dict(params)
+    crop = 128
+    t = _time_crop(f, phi0, p, 128)
+    for c in (256, 512, 1024, 2048, 4096):
+        if c > min(wl.H, wl.W):
+            break
+        est = t * (c / 128) ** 2 * (1.0 + np.log2(c / 128) / 7.0)
+        if est > per_step:
+            break
+        crop = c
+    i0, j0 = (wl.H - crop) // 2, (wl.W - crop) // 2
+    fc = np.ascontiguousarray(f[i0:i0 + crop, j0:j0 + crop])
+    pc = synth.inset_rect_sdf(crop, crop)
+    g = oracle.edge(fc)
+    st = oracle.initial_state(pc)
+    for _ in range(args.warmup):
+        oracle.iterate(st, g, 1, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.iterate(st, g, 1, p)
+    el = time.perf_counter() - t0
+    value = crop * crop * args.steps / el / 1e6
+    sample = (f"one outer iteration (S=3) per step on a centred {crop}x{crop} crop of the "
+              f"{wl.name} workload with its own inset-rectangle init, FP64 oracle")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl.name, "H": wl.H, "W": wl.W, "R": wl.R,
+                                        "d": wl.d, "S": 3, "crop": crop},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _time_crop(f, phi0, p, c):
+    import numpy as np
+
+    import oracle
+    from paper_2003_12693_gb300 import synth
+    fc = np.ascontiguousarray(f[:c, :c])
+    st = oracle.initial_state(synth.inset_rect_sdf(c, c))
+    g = oracle.edge(fc)
+    t0 = time.perf_counter()
+    oracle.iterate(st, g, 1, p)
+    return time.perf_counter() - t0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_gpu(args, wl, rank: int, world: int, local_rank: int):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2003_12693_gb300 import build, sr
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    f = np.ascontiguousarray(wl.image().astype(np.float32))
+    phi0 = np.ascontiguousarray(wl.phi0().astype(np.float32))
+    params = sr.make_params(win_radius=wl.R, d=wl.d)
+    stream = torch.cuda.current_stream()
+    ctx = sr.Context(wl.H, wl.W, params, stream)
+    f_d = torch.from_numpy(f).to(dev)
+    phi0_d = torch.from_numpy(phi0).to(dev)
+    ctx.edge_function(f_d)
+    ctx.set_phi(phi0_d)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    P = wl.H * wl.W
+
+    # warm-up (also builds the CUDA graphs)
+    ctx.iterate(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, each bracketed by events, L2 flushed between
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ctx.kernel_launches(reset=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            ctx.iterate(1)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    launches = ctx.kernel_launches(reset=True)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    value = world * P * args.steps / (total_ms / 1e3) / 1e6
+
+    # ---- per-kernel durations (events around every launch, no graph)
+    ctx.profile_enable(True)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ctx.iterate(1)
+    ktimes = {name: ctx.kernel_times(name) for name in BYTES_PER_PX}
+    ctx.kernel_times("reduce")
+    ctx.profile_enable(False)
+    hbm_peak, peak_kind = _peaks()
+    shares, kstats = {}, {}
+    tot = sum(ms for ms, _ in ktimes.values())
+    for name, (ms, n) in ktimes.items():
+        avg_s = ms / 1e3 / max(n, 1)
+        bytes_launch = BYTES_PER_PX[name] * P
+        kstats[name] = {"launches": n, "avg_us": avg_s * 1e6, "share": ms / tot if tot else None,
+                        "algorithmic_bytes_per_launch": bytes_launch,
+                        "achieved_gbs": bytes_launch / avg_s / 1e9 if avg_s else None}
+    dom = max(kstats, key=lambda k: kstats[k]["share"] or 0)
+    ach = kstats[dom]["achieved_gbs"]
+    roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": ach, "peak": hbm_peak,
+                "unit": "GB/s", "frac": ach / hbm_peak, "peak_kind": peak_kind,
+                "traffic": _ncu_traffic(KERNEL_NAMES[dom], wl.name)}
+    bytes_iter = sum(BYTES_PER_PX[k] * (3 if k != "wb_update" else 1) for k in BYTES_PER_PX)
+    it_gbs = bytes_iter * P / (total_ms / 1e3 / args.steps) / 1e9
+    iteration_roofline = {"algorithmic_bytes_per_px": bytes_iter, "achieved_gbs": it_gbs,
+                          "frac_of_measured_peak": it_gbs / hbm_peak,
+                          "frac_of_nominal_8tbs": it_gbs / 8000.0, "kernels": kstats}
+
+    # ---- end to end through the C-ABI with host buffers
+    f_h = torch.from_numpy(f).pin_memory()
+    phi0_h = torch.from_numpy(phi0).pin_memory()
+    mask_h = torch.empty((wl.H, wl.W), dtype=torch.uint8).pin_memory()
+    e2e_iters = args.steps
+    jobs = 2
+    ctx.segment_host(f_h, phi0_h, 2, 0.0, mask_h)  # warm path
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(jobs):
+        flush.fill_(0.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.segment_host(f_h, phi0_h, e2e_iters, 0.0, mask_h)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * P * e2e_iters * jobs / (float(e2e_t.item()) / 1e3) / 1e6
+    e2e = {"value": e2e_value, "unit": UNIT,
+           "h2d_bytes_per_step": (f.nbytes + phi0.nbytes) / e2e_iters,
+           "d2h_bytes_per_step": P / e2e_iters,
+           "job": f"sr_segment_host: copy image and phi0 from pinned host memory, edge "
+                  f"function, {e2e_iters} iterations, mask back to host; per-step bytes "
+                  f"amortised over the job"}
+    ctx.close()
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        rate, iters, el = _oracle_rate(f.astype(np.float64), phi0.astype(np.float64),
+                                       wl.params(), budget_s=args.cpu_budget)
+        cpu = {"value": rate, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+               "sample": f"{iters} outer iteration(s) (S=3) of the full {wl.H}x{wl.W} "
+                         f"workload, {el:.1f} s, FP64 C oracle with OpenMP"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "H": wl.H, "W": wl.W, "R": wl.R, "d": wl.d, "S": 3,
+                   "description": wl.description,
+                   "l2": "flushed (256 MiB write) between timed steps, outside the events",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "iteration_roofline": iteration_roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "wall_s_timed_region": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="ellipses_2048")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    from paper_2003_12693_gb300 import synth
+    wl = synth.WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_gpu(args, wl, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

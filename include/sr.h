@@ -1,0 +1,197 @@
+/*
+ * sr.h - C-ABI of the GB300 Split Bregman self-repelling snake (SR).
+ *
+ * The library runs the Split Bregman iteration for the self-repelling snake
+ * of Pan et al. (Alg. 1, Secs. 3-4) on one GPU with hand-written sm_103a
+ * kernels.  It takes plain pointers and sizes; nothing here depends on a
+ * framework's tensor types.
+ *
+ * Layout.  Every image-sized buffer is a float32 (or uint8 for masks) plane
+ * of H rows by W columns, row-major, with a leading dimension ld >= W
+ * elements between rows.  Row index i (the paper's x1), column index j (x2).
+ * Unless a function says "host", pointers are device pointers on the device
+ * that was current when the context was created.
+ *
+ * Ownership.  The caller owns every buffer it passes; no call keeps a caller
+ * pointer after it returns.  The context owns its state (phi, w, b, g), the
+ * FFT workspace and the CUDA graphs, and frees them in sr_destroy.
+ *
+ * Streams.  All work is enqueued on the stream given to sr_create (0 means
+ * the legacy default stream).  Calls return once the work is enqueued,
+ * except where a function says it synchronises.
+ *
+ * Errors.  Every call returns an sr_status; none exits, aborts or traps the
+ * device.  SR_ECUDA means a CUDA runtime call failed; sr_last_error gives the
+ * message.  A context that returned SR_ECUDA should be destroyed.
+ */
+#ifndef SR_H
+#define SR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sr_status {
+  SR_OK = 0,
+  SR_EINVAL = 1,          /* bad argument: size, pointer, parameter value */
+  SR_ENOMEM = 2,          /* device or host allocation failed */
+  SR_ECUDA = 3,           /* a CUDA runtime call failed (see sr_last_error) */
+  SR_ENONFINITE = 4,      /* NaN or Inf met in the state or the stopping test */
+  SR_ENOTCONVERGED = 5,   /* tol > 0 and max_outer reached before convergence */
+  SR_ETIMEOUT = 6,        /* reserved for bounded device-side waits */
+  SR_EUNSUPPORTED = 7     /* size or option this build does not implement */
+} sr_status;
+
+/* Model and solver parameters.  Defaults (sr_params_default) are the Fig. 1
+ * set of Sec. 5: alpha=4, gamma=4, beta=0.2, mu=8, eps=1, l=1, tau=0.1, S=3. */
+typedef struct sr_params {
+  float alpha;       /* balloon (area) weight, Eq. (7) */
+  float beta;        /* repulsion weight, Eq. (7) */
+  float gamma;       /* geodesic-length weight, Eq. (7) */
+  float mu;          /* splitting penalty, Eq. (22) */
+  float tau;         /* time step of the semi-implicit scheme, Eq. (30) */
+  float eps;         /* width of the regularised Heaviside / Dirac, Eqs. (5)-(6) */
+  float band_l;      /* narrow-band half width l of h, Eq. (11) */
+  float d;           /* Gaussian scale of the repulsion window, Sec. 4 */
+  int win_radius;    /* window half width R: offsets p, q in [-R, R], 0 <= R <= 8 */
+  int inner_S;       /* inner semi-implicit steps per outer iteration, Eq. (37) */
+  float inner_tol;   /* inner stopping tolerance; must be <= 0 (fixed S) in this build */
+  float rho;         /* edge-detector scale, Eq. (1) */
+  float sigma;       /* Gaussian smoothing of the image in Eq. (1); 0 disables */
+  int s_pow;         /* exponent s in Eq. (1): 1 or 2 */
+  int check_every;   /* outer iterations between FP64 stopping tests (>= 1) */
+} sr_params;
+
+typedef struct sr_ctx sr_ctx;
+
+/* Fill *p with the Fig. 1 defaults (and d = 3, R = 3, rho = 1, sigma = 1,
+ * s = 2, check_every = 10).  Returns SR_EINVAL if p is NULL. */
+sr_status sr_params_default(sr_params* p);
+
+/* Create a solver for H x W images.  Validates the parameters (finite, mu,
+ * tau, eps > 0, 0 <= R <= 8, S >= 1, s in {1, 2}), allocates the device state
+ * and FFT workspace and builds the twiddle and symbol tables of Eq. (32).
+ * Supported sizes in this build: H and W powers of two in [16, 4096]
+ * (SR_EUNSUPPORTED otherwise).  cuda_stream is a cudaStream_t (may be 0). */
+sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx** out);
+
+/* Release everything the context owns.  NULL is ignored. */
+void sr_destroy(sr_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none). */
+const char* sr_last_error(const sr_ctx* ctx);
+const char* sr_status_string(sr_status s);
+
+/* Eq. (1): g = 1 / (1 + rho |grad(G_sigma * f)|^s) from the image f
+ * (device, H x W, leading dimension ld).  The Gaussian is sampled on
+ * |t| <= ceil(3 sigma), normalised, with a replicated border; the gradient
+ * uses central differences inside and one-sided ones on the border.  Alg. 1
+ * computes g once per image, before the iterations. */
+sr_status sr_edge_function(sr_ctx* ctx, const float* image, int ld);
+
+/* Alg. 1 initialisation: phi^0 = phi0 (device, a signed distance function,
+ * Eq. (3): negative inside), w^0 = grad phi^0 (forward differences, Eq. (35),
+ * periodic), b^0 = 0.  Resets the iteration counter. */
+sr_status sr_set_phi(sr_ctx* ctx, const float* phi0, int ld);
+
+/* Alg. 1 outer loop.  Each outer iteration runs inner_S semi-implicit steps
+ * of Eq. (37) (repulsion window sum, right-hand side, FFT solve of Eqs.
+ * (31)-(33)) and then the w update of Eqs. (41), (42), (40) and the Bregman
+ * update of Eq. (23).
+ *   tol <= 0: run exactly max_outer iterations; asynchronous unless
+ *             rel_change is non-NULL, in which case the last iteration also
+ *             computes the relative change (FP64) and the call synchronises.
+ *   tol  > 0: every check_every iterations the relative change
+ *             ||phi^{k+1} - phi^k|| / (||phi^k|| + 1e-6) (the form of the
+ *             inner stopping rule of Sec. 4) is reduced in FP64 on the GPU
+ *             and read back; the loop stops once it is <= tol.  Returns
+ *             SR_ENOTCONVERGED if max_outer is reached first.
+ * outer_done (may be NULL) receives the iterations run by this call;
+ * rel_change (may be NULL) the last relative change computed.  A NaN or Inf
+ * in the stopping test returns SR_ENONFINITE. */
+sr_status sr_iterate(sr_ctx* ctx, int max_outer, double tol, int* outer_done,
+                     double* rel_change);
+
+/* Eq. (3): mask[i, j] = 1 where phi < 0 (inside the contour), else 0.
+ * mask is a device uint8 plane with leading dimension ld. */
+sr_status sr_mask(sr_ctx* ctx, unsigned char* mask, int ld);
+
+/* Copy the current phi to a device buffer (leading dimension ld). */
+sr_status sr_get_phi(sr_ctx* ctx, float* phi, int ld);
+
+/* Checkpoint / resume: copy the full iteration state (phi, w1, w2, b1, b2;
+ * device, contiguous H x W each) out of / into the context.  Iterating from a
+ * restored state gives bit-identical results to an uninterrupted run. */
+sr_status sr_get_state(sr_ctx* ctx, float* phi, float* w1, float* w2, float* b1, float* b2);
+sr_status sr_set_state(sr_ctx* ctx, const float* phi, const float* w1, const float* w2,
+                       const float* b1, const float* b2);
+
+/* Copy g out of / into the context (device, contiguous H x W). */
+sr_status sr_get_g(sr_ctx* ctx, float* g);
+sr_status sr_set_g(sr_ctx* ctx, const float* g);
+
+/* Discrete energy of Eqs. (7)-(10) at the current phi, accumulated in FP64 on
+ * the GPU: E = gamma E_g + alpha E_a + beta E_r with E_g = sum g |grad phi|
+ * delta(phi), E_a = sum g (1 - H(phi)), E_r = -sum_x h(phi_x) grad phi_x .
+ * sum_y K(x - y) h(phi_y) grad phi_y over the repulsion window (forward
+ * differences, terms outside the image dropped).  Synchronises.  Any output
+ * pointer may be NULL. */
+sr_status sr_energy(sr_ctx* ctx, double* E, double* Eg, double* Ea, double* Er);
+
+/* ---- Single steps of the hot path (device buffers, contiguous H x W) ----
+ * These run one row of the iteration on caller buffers with the context's
+ * parameters and g; they exist so each step can be checked on its own. */
+
+/* Sec. 4 repulsion field: v = sum_{p,q=-R..R} exp(-(p^2+q^2)/d^2)
+ * w_{i+p,j+q} h(phi_{i+p,j+q}), terms outside the image dropped. */
+sr_status sr_repulsion_field(sr_ctx* ctx, const float* phi, const float* w1, const float* w2,
+                             float* v1, float* v2);
+
+/* One inner step of Eq. (37): psi_out = phi^{k+1,s+1} from psi_in =
+ * phi^{k+1,s} and the frozen w^k, b^k.  psi_out may alias psi_in. */
+sr_status sr_phi_step(sr_ctx* ctx, const float* psi_in, const float* w1, const float* w2,
+                      const float* b1, const float* b2, float* psi_out);
+
+/* Eqs. (31)-(33) alone: out = Re F^{-1}[F(rhs) / F(1 - tau mu Laplacian)]. */
+sr_status sr_fft_solve(sr_ctx* ctx, const float* rhs, float* out);
+
+/* Eqs. (41), (42), (40), (23) after the inner loop: from phi^{k+1}, w^k, b^k
+ * compute w^{k+1} and b^{k+1}.  b_out may alias b_in; w_out must not alias
+ * w_in (the window sum reads w^k around every pixel). */
+sr_status sr_w_b_update(sr_ctx* ctx, const float* phi1, const float* w1_in,
+                        const float* w2_in, const float* b1_in, const float* b2_in,
+                        float* w1_out, float* w2_out, float* b1_out, float* b2_out);
+
+/* Kernel launches enqueued by this context since creation (or the last
+ * reset).  Graph launches count every kernel node they run. */
+long long sr_kernel_launches(const sr_ctx* ctx, int reset);
+
+/* Per-kernel timing: when enabled, sr_iterate launches without graphs and
+ * records CUDA events around every kernel on the context's stream.
+ * sr_kernel_times synchronises and returns, for kernel class c (see
+ * SR_KCLASS_*), the summed milliseconds and the launch count, then clears
+ * the accumulators. */
+#define SR_KCLASS_RHS_ROWFFT 0   /* repulsion + right-hand side + row R2C FFT */
+#define SR_KCLASS_COLSOLVE 1     /* column FFT, divide by the symbol, inverse */
+#define SR_KCLASS_ROWIFFT 2      /* row C2R FFT + phi update */
+#define SR_KCLASS_WB_UPDATE 3    /* repulsion + shrink + projection + Bregman */
+#define SR_KCLASS_REDUCE 4       /* FP64 stopping-test reduction */
+#define SR_KCLASS_COUNT 5
+sr_status sr_profile_enable(sr_ctx* ctx, int enable);
+sr_status sr_kernel_times(sr_ctx* ctx, int kclass, double* total_ms, long long* launches);
+
+/* Convenience for callers with host buffers: copy the image and phi0 from
+ * host memory (pinned memory gives asynchronous copies), compute g, set
+ * phi0, run max_outer iterations (tol as in sr_iterate), and copy the mask
+ * (uint8, H x W contiguous) and, if phi_host is non-NULL, phi back to host
+ * memory.  Synchronises.  outer_done / rel_change as in sr_iterate. */
+sr_status sr_segment_host(sr_ctx* ctx, const float* image_host, const float* phi0_host,
+                          int max_outer, double tol, unsigned char* mask_host,
+                          float* phi_host, int* outer_done, double* rel_change);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SR_H */

@@ -263,6 +263,11 @@ void oc_repulsion(int M, int N, const oc_params* p, const double* phi, const dou
   }
   int R = p->R;
   double d2 = p->d * p->d;
+  int side = 2 * R + 1;
+  double* K = alloc_d((size_t)side * side); /* K(p, q) = exp(-(p^2 + q^2) / d^2) */
+  for (int pp = -R; pp <= R; ++pp)
+    for (int qq = -R; qq <= R; ++qq)
+      K[(pp + R) * side + (qq + R)] = exp(-(double)(pp * pp + qq * qq) / d2);
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < M; ++i)
     for (int j = 0; j < N; ++j) {
@@ -273,7 +278,7 @@ void oc_repulsion(int M, int N, const oc_params* p, const double* phi, const dou
         for (int qq = -R; qq <= R; ++qq) {
           int jj = j + qq;
           if (jj < 0 || jj >= N) continue;
-          double kw = exp(-(double)(pp * pp + qq * qq) / d2);
+          double kw = K[(pp + R) * side + (qq + R)];
           s1 += kw * u1[IDX(ii, jj)];
           s2 += kw * u2[IDX(ii, jj)];
         }
@@ -281,6 +286,7 @@ void oc_repulsion(int M, int N, const oc_params* p, const double* phi, const dou
       v1[IDX(i, j)] = s1;
       v2[IDX(i, j)] = s2;
     }
+  free(K);
   free(u1);
   free(u2);
 }

@@ -1,0 +1,770 @@
+// Host side of the C-ABI declared in include/sr.h: parameter checks, device
+// state, FFT plans and tables, CUDA-graph capture of the outer iteration, and
+// the FP64 stopping test.  The kernels live in sr_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sr.h"
+#include "sr_internal.h"
+
+using srk::Fft;
+using srk::Geo;
+using srk::Model;
+
+struct sr_ctx {
+  int H = 0, W = 0, L = 0;
+  sr_params prm{};
+  cudaStream_t stream = nullptr;     // caller's stream
+  cudaStream_t cap_stream = nullptr; // private stream used only for graph capture
+  int device = 0;
+  int nsm = 0;
+  Geo geo{};
+  Model mod{};
+  Fft fft_row{}, fft_col{};
+  int row_T = 0, row_NT = 0, row_CW = 0;
+  int n_tile = 0;
+
+  // device state
+  float* phi[2] = {nullptr, nullptr};
+  float* w1[2] = {nullptr, nullptr};
+  float* w2[2] = {nullptr, nullptr};
+  float* b1 = nullptr;
+  float* b2 = nullptr;
+  float* g = nullptr;
+  float* tmp1 = nullptr;
+  float* tmp2 = nullptr;
+  float* stage = nullptr;
+  unsigned char* mask_dev = nullptr;
+  float2* X = nullptr;
+  float2* tw_row = nullptr;
+  float2* tw_col = nullptr;
+  float2* tw_n = nullptr;
+  float* aM = nullptr;
+  float* aN = nullptr;
+  double* partials = nullptr;
+  double* red = nullptr;       // device: reduction result
+  double* red_host = nullptr;  // pinned host copy
+  int cur = 0;                 // phi[cur], w*[cur] hold phi^k, w^k
+  long long iters = 0;
+
+  // graphs of one outer iteration without the stopping test, per parity
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_kernels = 0;
+
+  long long launches = 0;
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_pending;  // (kclass, event index of the start)
+  double ktime[SR_KCLASS_COUNT] = {0};
+  long long kcount[SR_KCLASS_COUNT] = {0};
+
+  std::string err;
+};
+
+namespace {
+
+sr_status fail(sr_ctx* c, sr_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+sr_status cuda_fail(sr_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(c, SR_ECUDA, m);
+}
+
+#define SR_CUDA(ctx, call)                                      \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);  \
+  } while (0)
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v) {
+  int r = 0;
+  while ((1 << r) < v) ++r;
+  return r;
+}
+
+bool finite_f(float v) { return std::isfinite(v); }
+
+sr_status check_params(const sr_params* p, std::string& why) {
+  const float vals[] = {p->alpha, p->beta, p->gamma, p->mu, p->tau, p->eps, p->band_l, p->d,
+                        p->inner_tol, p->rho, p->sigma};
+  for (float v : vals)
+    if (!finite_f(v)) {
+      why = "parameters must be finite";
+      return SR_EINVAL;
+    }
+  if (p->mu <= 0.f || p->tau <= 0.f || p->eps <= 0.f) {
+    why = "mu, tau and eps must be positive";
+    return SR_EINVAL;
+  }
+  if (p->win_radius < 0 || p->win_radius > srk::kMaxR) {
+    why = "win_radius must lie in [0, 8]";
+    return SR_EINVAL;
+  }
+  if (p->win_radius > 0 && p->d <= 0.f) {
+    why = "d must be positive";
+    return SR_EINVAL;
+  }
+  if (p->band_l < 0.f || p->rho < 0.f || p->sigma < 0.f) {
+    why = "band_l, rho and sigma must be non-negative";
+    return SR_EINVAL;
+  }
+  if (p->inner_S < 1) {
+    why = "inner_S must be >= 1";
+    return SR_EINVAL;
+  }
+  if (p->s_pow != 1 && p->s_pow != 2) {
+    why = "s_pow must be 1 or 2";
+    return SR_EINVAL;
+  }
+  if (p->check_every < 1) {
+    why = "check_every must be >= 1";
+    return SR_EINVAL;
+  }
+  if ((int)std::ceil(3.0 * p->sigma) > srk::kMaxGauss) {
+    why = "sigma too large (ceil(3 sigma) must be <= 32)";
+    return SR_EINVAL;
+  }
+  if (p->inner_tol > 0.f) {
+    why = "inner_tol > 0 (data-dependent inner exit) is not implemented; use a fixed inner_S";
+    return SR_EUNSUPPORTED;
+  }
+  return SR_OK;
+}
+
+void make_fft(Fft& f, int L, const float2* tw) {
+  f.L = L;
+  f.logL = ilog2(L);
+  f.tw = tw;
+  f.n16 = f.logL / 4;
+  f.tail = 1 << (f.logL % 4);
+}
+
+std::vector<float2> twiddles(int n, int len) {
+  // exp(-2 pi i q / len), q in [0, n), computed in double and rounded once
+  std::vector<float2> t(n);
+  for (int q = 0; q < n; ++q) {
+    const double a = -2.0 * M_PI * (double)q / (double)len;
+    t[q] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  return t;
+}
+
+template <class T>
+sr_status upload(sr_ctx* c, T** dst, const std::vector<T>& v) {
+  SR_CUDA(c, cudaMalloc((void**)dst, v.size() * sizeof(T)));
+  SR_CUDA(c, cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SR_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// ---- launch bookkeeping (per-kernel events in profile mode) ---------------
+int ev_take(sr_ctx* c) {
+  const int idx = (int)c->ev_pending.size() * 2;
+  while ((int)c->ev_pool.size() < idx + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    c->ev_pool.push_back(e);
+  }
+  return idx;
+}
+
+sr_status flush_profile(sr_ctx* c) {
+  if (c->ev_pending.empty()) return SR_OK;
+  SR_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (auto& pr : c->ev_pending) {
+    float ms = 0.f;
+    SR_CUDA(c, cudaEventElapsedTime(&ms, c->ev_pool[pr.second], c->ev_pool[pr.second + 1]));
+    c->ktime[pr.first] += ms;
+    c->kcount[pr.first] += 1;
+  }
+  c->ev_pending.clear();
+  return SR_OK;
+}
+
+// Run `launch` on stream s; in profile mode bracket it with events.
+template <class F>
+sr_status run_kernel(sr_ctx* c, int kclass, cudaStream_t s, const char* name, F launch) {
+  int ev = -1;
+  if (c->profile) {
+    if (c->ev_pending.size() >= 4096) {
+      sr_status st = flush_profile(c);
+      if (st != SR_OK) return st;
+    }
+    ev = ev_take(c);
+    if (ev < 0) return fail(c, SR_ECUDA, "cudaEventCreate failed");
+    SR_CUDA(c, cudaEventRecord(c->ev_pool[ev], s));
+  }
+  cudaError_t e = launch();
+  if (e != cudaSuccess) return cuda_fail(c, e, name);
+  c->launches += 1;
+  if (c->profile) {
+    SR_CUDA(c, cudaEventRecord(c->ev_pool[ev + 1], s));
+    c->ev_pending.push_back({kclass, ev});
+  }
+  return SR_OK;
+}
+
+// ---- one inner step: psi_out = psi_in + L^{-1} G ---------------------------
+sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const float* w1,
+                           const float* w2, const float* b1, const float* b2, float* psi_out,
+                           const float* load_src) {
+  srk::RowFwdArgs fa{};
+  fa.geo = c->geo;
+  fa.mod = c->mod;
+  fa.fft = c->fft_row;
+  fa.twN = c->tw_n;
+  fa.psi = psi_in;
+  fa.g = c->g;
+  fa.w1 = w1;
+  fa.w2 = w2;
+  fa.b1 = b1;
+  fa.b2 = b2;
+  fa.src = load_src;
+  fa.X = c->X;
+  fa.T = c->row_T;
+  fa.CW = c->row_CW;
+  const int mode = load_src ? srk::kRowLOAD : srk::kRowRHS;
+  sr_status st = run_kernel(c, SR_KCLASS_RHS_ROWFFT, s, "k_rowfwd",
+                            [&] { return srk::launch_rowfwd(fa, mode, c->row_NT, s); });
+  if (st != SR_OK) return st;
+  srk::ColArgs ca{};
+  ca.geo = c->geo;
+  ca.fft = c->fft_col;
+  ca.aM = c->aM;
+  ca.aN = c->aN;
+  ca.X = c->X;
+  st = run_kernel(c, SR_KCLASS_COLSOLVE, s, "k_colsolve",
+                  [&] { return srk::launch_colsolve(ca, s); });
+  if (st != SR_OK) return st;
+  srk::RowInvArgs ia{};
+  ia.geo = c->geo;
+  ia.fft = c->fft_row;
+  ia.twN = c->tw_n;
+  ia.X = c->X;
+  ia.psi_in = psi_in;
+  ia.out = psi_out;
+  ia.T = c->row_T;
+  const int imode = load_src ? srk::kInvSTORE : srk::kInvADD;
+  return run_kernel(c, SR_KCLASS_ROWIFFT, s, "k_rowinv",
+                    [&] { return srk::launch_rowinv(ia, imode, c->row_NT, s); });
+}
+
+sr_status enqueue_wb(sr_ctx* c, cudaStream_t s, const float* phi1, const float* w1i,
+                     const float* w2i, const float* b1i, const float* b2i, float* w1o, float* w2o,
+                     float* b1o, float* b2o, const float* phi_old) {
+  srk::WBArgs a{};
+  a.geo = c->geo;
+  a.mod = c->mod;
+  a.phi1 = phi1;
+  a.g = c->g;
+  a.w1 = w1i;
+  a.w2 = w2i;
+  a.b1 = b1i;
+  a.b2 = b2i;
+  a.w1o = w1o;
+  a.w2o = w2o;
+  a.b1o = b1o;
+  a.b2o = b2o;
+  a.phi_old = phi_old;
+  a.partials = c->partials;
+  sr_status st = run_kernel(c, SR_KCLASS_WB_UPDATE, s, "k_wb_update",
+                            [&] { return srk::launch_wb_update(a, s); });
+  if (st != SR_OK || !phi_old) return st;
+  return run_kernel(c, SR_KCLASS_REDUCE, s, "k_reduce", [&] {
+    return srk::launch_reduce(c->partials, c->n_tile, 2, c->red, s);
+  });
+}
+
+// One outer iteration of Alg. 1 from phi[p], w[p] to phi[1-p], w[1-p].
+sr_status enqueue_iteration(sr_ctx* c, cudaStream_t s, int p, bool check) {
+  const int q = 1 - p;
+  for (int it = 0; it < c->prm.inner_S; ++it) {
+    const float* in = it == 0 ? c->phi[p] : c->phi[q];
+    sr_status st = enqueue_phi_step(c, s, in, c->w1[p], c->w2[p], c->b1, c->b2, c->phi[q], nullptr);
+    if (st != SR_OK) return st;
+  }
+  return enqueue_wb(c, s, c->phi[q], c->w1[p], c->w2[p], c->b1, c->b2, c->w1[q], c->w2[q], c->b1,
+                    c->b2, check ? c->phi[p] : nullptr);
+}
+
+void drop_graphs(sr_ctx* c) {
+  for (int p = 0; p < 2; ++p)
+    if (c->graph[p]) {
+      cudaGraphExecDestroy(c->graph[p]);
+      c->graph[p] = nullptr;
+    }
+}
+
+sr_status build_graphs(sr_ctx* c) {
+  if (c->graph[0] && c->graph[1]) return SR_OK;
+  drop_graphs(c);
+  const long long before = c->launches;
+  for (int p = 0; p < 2; ++p) {
+    cudaGraph_t gph = nullptr;
+    SR_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    sr_status st = enqueue_iteration(c, c->cap_stream, p, false);
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &gph);
+    if (st != SR_OK) {
+      if (gph) cudaGraphDestroy(gph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->graph[p], gph, 0);
+    cudaGraphDestroy(gph);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  }
+  c->graph_kernels = (int)((c->launches - before) / 2);
+  c->launches = before;  // capture enqueues nothing
+  return SR_OK;
+}
+
+sr_status read_residual(sr_ctx* c, double* rel) {
+  SR_CUDA(c, cudaMemcpyAsync(c->red_host, c->red, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+  SR_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double num = c->red_host[0], den = c->red_host[1];
+  const double r = std::sqrt(num) / (std::sqrt(den) + 1e-6);
+  *rel = r;
+  if (!std::isfinite(r)) return fail(c, SR_ENONFINITE, "non-finite value in the stopping test");
+  return SR_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C-ABI
+// ============================================================================
+extern "C" {
+
+const char* sr_status_string(sr_status s) {
+  switch (s) {
+    case SR_OK: return "ok";
+    case SR_EINVAL: return "invalid argument";
+    case SR_ENOMEM: return "out of memory";
+    case SR_ECUDA: return "CUDA error";
+    case SR_ENONFINITE: return "non-finite value";
+    case SR_ENOTCONVERGED: return "not converged";
+    case SR_ETIMEOUT: return "timeout";
+    case SR_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* sr_last_error(const sr_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+sr_status sr_params_default(sr_params* p) {
+  if (!p) return SR_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->alpha = 4.f;
+  p->beta = 0.2f;
+  p->gamma = 4.f;
+  p->mu = 8.f;
+  p->tau = 0.1f;
+  p->eps = 1.f;
+  p->band_l = 1.f;
+  p->d = 3.f;
+  p->win_radius = 3;
+  p->inner_S = 3;
+  p->inner_tol = 0.f;
+  p->rho = 1.f;
+  p->sigma = 1.f;
+  p->s_pow = 2;
+  p->check_every = 10;
+  return SR_OK;
+}
+
+void sr_destroy(sr_ctx* c) {
+  if (!c) return;
+  drop_graphs(c);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  void* bufs[] = {c->phi[0], c->phi[1], c->w1[0], c->w1[1], c->w2[0], c->w2[1], c->b1, c->b2,
+                  c->g, c->tmp1, c->tmp2, c->stage, c->mask_dev, c->X, c->tw_row, c->tw_col,
+                  c->tw_n, c->aM, c->aN, c->partials, c->red};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (c->red_host) cudaFreeHost(c->red_host);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx** out) {
+  if (!out || !p) return SR_EINVAL;
+  *out = nullptr;
+  if (H < 1 || W < 1) return SR_EINVAL;
+  std::string why;
+  sr_status st = check_params(p, why);
+  if (st != SR_OK) return st;
+  if (!is_pow2(H) || !is_pow2(W) || H < 16 || W < 16 || H > 4096 || W > 4096)
+    return SR_EUNSUPPORTED;
+
+  sr_ctx* c = new (std::nothrow) sr_ctx();
+  if (!c) return SR_ENOMEM;
+  c->H = H;
+  c->W = W;
+  c->L = W / 2;
+  c->prm = *p;
+  c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  c->geo.M = H;
+  c->geo.N = W;
+  c->geo.L = W / 2;
+  c->geo.logN = ilog2(W);
+
+  auto bail = [&](sr_status s) {
+    sr_destroy(c);
+    return s;
+  };
+#define CREATE_CUDA(call)                                  \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) {                               \
+      if (e_ == cudaErrorMemoryAllocation) return bail(SR_ENOMEM); \
+      return bail(SR_ECUDA);                               \
+    }                                                      \
+  } while (0)
+
+  CREATE_CUDA(cudaGetDevice(&c->device));
+  CREATE_CUDA(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
+  CREATE_CUDA(srk::configure_kernels());
+  CREATE_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+
+  // model constants
+  Model& m = c->mod;
+  m.alpha = p->alpha;
+  m.beta = p->beta;
+  m.gamma = p->gamma;
+  m.mu = p->mu;
+  m.tau = p->tau;
+  m.eps = p->eps;
+  m.band_l = p->band_l;
+  m.beta2_mu = (float)(2.0 * (double)p->beta / (double)p->mu);
+  m.gamma_mu = (float)((double)p->gamma / (double)p->mu);
+  m.R = p->win_radius;
+  for (int t = -m.R; t <= m.R; ++t)
+    m.kw[t + m.R] = (float)std::exp(-(double)(t * t) / ((double)p->d * (double)p->d));
+
+  // row-pass shape: T rows per CTA with T * (W/2) = 16 * threads
+  const int L = c->L;
+  int NT = L >= 2048 ? 512 : 256;
+  int T = 16 * NT / L;
+  while (NT > 64 && T > 1 && (H + T - 1) / T < 2 * c->nsm) {
+    NT /= 2;
+    T = 16 * NT / L;
+  }
+  if (T > H) {
+    T = H;
+    NT = T * L / 16;
+  }
+  if (T < 1 || NT < 1 || NT * 16 != T * L) return bail(SR_EUNSUPPORTED);
+  c->row_T = T;
+  c->row_NT = NT;
+  c->row_CW = W < 128 ? W : 128;
+  c->n_tile = srk::tile_blocks(c->geo);
+
+  const size_t P = (size_t)H * W;
+  float** planes[] = {&c->phi[0], &c->phi[1], &c->w1[0], &c->w1[1], &c->w2[0], &c->w2[1],
+                      &c->b1,     &c->b2,     &c->g,     &c->tmp1,  &c->tmp2,  &c->stage};
+  for (float** pl : planes) CREATE_CUDA(cudaMalloc((void**)pl, P * sizeof(float)));
+  CREATE_CUDA(cudaMalloc((void**)&c->mask_dev, P));
+  CREATE_CUDA(cudaMalloc((void**)&c->X, (size_t)H * L * sizeof(float2)));
+  CREATE_CUDA(cudaMalloc((void**)&c->partials, (size_t)c->n_tile * 3 * sizeof(double)));
+  CREATE_CUDA(cudaMalloc((void**)&c->red, 4 * sizeof(double)));
+  CREATE_CUDA(cudaMallocHost((void**)&c->red_host, 4 * sizeof(double)));
+  for (float** pl : planes) CREATE_CUDA(cudaMemset(*pl, 0, P * sizeof(float)));
+
+  // tables: FFT twiddles, the post/pre-processing twiddles of the real row
+  // transform, and the two halves of the symbol of Eq. (32)
+  if (upload(c, &c->tw_row, twiddles(L, L)) != SR_OK) return bail(SR_ECUDA);
+  if (upload(c, &c->tw_col, twiddles(H, H)) != SR_OK) return bail(SR_ECUDA);
+  if (upload(c, &c->tw_n, twiddles(L, W)) != SR_OK) return bail(SR_ECUDA);
+  std::vector<float> aM(H), aN(L + 1);
+  const double tm = (double)p->tau * (double)p->mu;
+  for (int l = 0; l < H; ++l) {
+    const double s = std::sin(M_PI * (double)l / (double)H);
+    aM[l] = (float)(tm * 4.0 * s * s);
+  }
+  for (int k = 0; k <= L; ++k) {
+    const double s = std::sin(M_PI * (double)k / (double)W);
+    aN[k] = (float)(tm * 4.0 * s * s);
+  }
+  if (upload(c, &c->aM, aM) != SR_OK) return bail(SR_ECUDA);
+  if (upload(c, &c->aN, aN) != SR_OK) return bail(SR_ECUDA);
+  make_fft(c->fft_row, L, c->tw_row);
+  make_fft(c->fft_col, H, c->tw_col);
+
+  // g = 1 until sr_edge_function is called
+  std::vector<float> ones(P, 1.f);
+  CREATE_CUDA(cudaMemcpy(c->g, ones.data(), P * sizeof(float), cudaMemcpyHostToDevice));
+  CREATE_CUDA(cudaDeviceSynchronize());
+#undef CREATE_CUDA
+  *out = c;
+  return SR_OK;
+}
+
+sr_status sr_edge_function(sr_ctx* c, const float* image, int ld) {
+  if (!c) return SR_EINVAL;
+  if (!image || ld < c->W) return fail(c, SR_EINVAL, "image must be non-NULL with ld >= W");
+  srk::EdgeArgs a{};
+  a.geo = c->geo;
+  const double sigma = c->prm.sigma;
+  a.r = sigma > 0.0 ? (int)std::ceil(3.0 * sigma) : 0;
+  std::vector<double> k(2 * a.r + 1);
+  double sum = 0.0;
+  for (int t = -a.r; t <= a.r; ++t) {
+    k[t + a.r] = sigma > 0.0 ? std::exp(-(double)(t * t) / (2.0 * sigma * sigma)) : 1.0;
+    sum += k[t + a.r];
+  }
+  for (int t = 0; t <= 2 * a.r; ++t) a.k[t] = (float)(k[t] / sum);
+  a.rho = c->prm.rho;
+  a.s_pow = c->prm.s_pow;
+  c->launches += 3;
+  SR_CUDA(c, srk::launch_edge(a, image, ld, c->tmp1, c->tmp2, c->g, c->stream));
+  return SR_OK;
+}
+
+sr_status sr_set_phi(sr_ctx* c, const float* phi0, int ld) {
+  if (!c) return SR_EINVAL;
+  if (!phi0 || ld < c->W) return fail(c, SR_EINVAL, "phi0 must be non-NULL with ld >= W");
+  c->cur = 0;
+  c->iters = 0;
+  SR_CUDA(c, cudaMemcpy2DAsync(c->phi[0], c->W * sizeof(float), phi0, (size_t)ld * sizeof(float),
+                               c->W * sizeof(float), c->H, cudaMemcpyDeviceToDevice, c->stream));
+  c->launches += 1;
+  SR_CUDA(c, srk::launch_init_wb(c->phi[0], c->w1[0], c->w2[0], c->b1, c->b2, c->geo, c->stream));
+  return SR_OK;
+}
+
+sr_status sr_iterate(sr_ctx* c, int max_outer, double tol, int* outer_done, double* rel_change) {
+  if (!c) return SR_EINVAL;
+  if (outer_done) *outer_done = 0;
+  if (max_outer < 0 || !std::isfinite(tol)) return fail(c, SR_EINVAL, "bad max_outer or tol");
+  if (max_outer == 0) return SR_OK;
+  const bool use_graph = !c->profile;
+  if (use_graph) {
+    sr_status st = build_graphs(c);
+    if (st != SR_OK) return st;
+  }
+  double rel = NAN;
+  int done = 0;
+  for (int k = 0; k < max_outer; ++k) {
+    const bool last = k == max_outer - 1;
+    const bool check = tol > 0.0 ? ((k + 1) % c->prm.check_every == 0 || last)
+                                 : (last && rel_change != nullptr);
+    sr_status st;
+    if (!check && use_graph) {
+      cudaError_t e = cudaGraphLaunch(c->graph[c->cur], c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+      c->launches += c->graph_kernels;
+      st = SR_OK;
+    } else {
+      st = enqueue_iteration(c, c->stream, c->cur, check);
+    }
+    if (st != SR_OK) return st;
+    c->cur ^= 1;
+    c->iters += 1;
+    done = k + 1;
+    if (check) {
+      st = read_residual(c, &rel);
+      if (rel_change) *rel_change = rel;
+      if (outer_done) *outer_done = done;
+      if (st != SR_OK) return st;
+      if (tol > 0.0 && rel <= tol) break;
+    }
+  }
+  if (outer_done) *outer_done = done;
+  if (rel_change) *rel_change = rel;
+  if (c->profile) {
+    sr_status st = flush_profile(c);
+    if (st != SR_OK) return st;
+  }
+  if (tol > 0.0 && !(rel <= tol)) return SR_ENOTCONVERGED;
+  return SR_OK;
+}
+
+sr_status sr_mask(sr_ctx* c, unsigned char* mask, int ld) {
+  if (!c) return SR_EINVAL;
+  if (!mask || ld < c->W) return fail(c, SR_EINVAL, "mask must be non-NULL with ld >= W");
+  c->launches += 1;
+  SR_CUDA(c, srk::launch_mask(c->phi[c->cur], mask, ld, c->geo, c->stream));
+  return SR_OK;
+}
+
+sr_status sr_get_phi(sr_ctx* c, float* phi, int ld) {
+  if (!c) return SR_EINVAL;
+  if (!phi || ld < c->W) return fail(c, SR_EINVAL, "phi must be non-NULL with ld >= W");
+  SR_CUDA(c, cudaMemcpy2DAsync(phi, (size_t)ld * sizeof(float), c->phi[c->cur],
+                               c->W * sizeof(float), c->W * sizeof(float), c->H,
+                               cudaMemcpyDeviceToDevice, c->stream));
+  return SR_OK;
+}
+
+sr_status sr_get_state(sr_ctx* c, float* phi, float* w1, float* w2, float* b1, float* b2) {
+  if (!c) return SR_EINVAL;
+  if (!phi || !w1 || !w2 || !b1 || !b2) return fail(c, SR_EINVAL, "NULL state pointer");
+  const size_t bytes = (size_t)c->H * c->W * sizeof(float);
+  const float* src[] = {c->phi[c->cur], c->w1[c->cur], c->w2[c->cur], c->b1, c->b2};
+  float* dst[] = {phi, w1, w2, b1, b2};
+  for (int t = 0; t < 5; ++t)
+    SR_CUDA(c, cudaMemcpyAsync(dst[t], src[t], bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return SR_OK;
+}
+
+sr_status sr_set_state(sr_ctx* c, const float* phi, const float* w1, const float* w2,
+                       const float* b1, const float* b2) {
+  if (!c) return SR_EINVAL;
+  if (!phi || !w1 || !w2 || !b1 || !b2) return fail(c, SR_EINVAL, "NULL state pointer");
+  const size_t bytes = (size_t)c->H * c->W * sizeof(float);
+  c->cur = 0;
+  const float* src[] = {phi, w1, w2, b1, b2};
+  float* dst[] = {c->phi[0], c->w1[0], c->w2[0], c->b1, c->b2};
+  for (int t = 0; t < 5; ++t)
+    SR_CUDA(c, cudaMemcpyAsync(dst[t], src[t], bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return SR_OK;
+}
+
+sr_status sr_get_g(sr_ctx* c, float* g) {
+  if (!c) return SR_EINVAL;
+  if (!g) return fail(c, SR_EINVAL, "NULL g");
+  SR_CUDA(c, cudaMemcpyAsync(g, c->g, (size_t)c->H * c->W * sizeof(float),
+                             cudaMemcpyDeviceToDevice, c->stream));
+  return SR_OK;
+}
+
+sr_status sr_set_g(sr_ctx* c, const float* g) {
+  if (!c) return SR_EINVAL;
+  if (!g) return fail(c, SR_EINVAL, "NULL g");
+  SR_CUDA(c, cudaMemcpyAsync(c->g, g, (size_t)c->H * c->W * sizeof(float),
+                             cudaMemcpyDeviceToDevice, c->stream));
+  return SR_OK;
+}
+
+sr_status sr_energy(sr_ctx* c, double* E, double* Eg, double* Ea, double* Er) {
+  if (!c) return SR_EINVAL;
+  srk::EnergyArgs a{};
+  a.geo = c->geo;
+  a.mod = c->mod;
+  a.phi = c->phi[c->cur];
+  a.g = c->g;
+  a.partials = c->partials;
+  c->launches += 2;
+  SR_CUDA(c, srk::launch_energy(a, c->stream));
+  SR_CUDA(c, srk::launch_reduce(c->partials, c->n_tile, 3, c->red, c->stream));
+  SR_CUDA(c, cudaMemcpyAsync(c->red_host, c->red, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+  SR_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double eg = c->red_host[0], ea = c->red_host[1], er = c->red_host[2];
+  if (Eg) *Eg = eg;
+  if (Ea) *Ea = ea;
+  if (Er) *Er = er;
+  const double e = (double)c->prm.gamma * eg + (double)c->prm.alpha * ea + (double)c->prm.beta * er;
+  if (E) *E = e;
+  if (!std::isfinite(e)) return fail(c, SR_ENONFINITE, "non-finite energy");
+  return SR_OK;
+}
+
+sr_status sr_repulsion_field(sr_ctx* c, const float* phi, const float* w1, const float* w2,
+                             float* v1, float* v2) {
+  if (!c) return SR_EINVAL;
+  if (!phi || !w1 || !w2 || !v1 || !v2) return fail(c, SR_EINVAL, "NULL pointer");
+  srk::RepArgs a{};
+  a.geo = c->geo;
+  a.mod = c->mod;
+  a.phi = phi;
+  a.w1 = w1;
+  a.w2 = w2;
+  a.v1 = v1;
+  a.v2 = v2;
+  c->launches += 1;
+  SR_CUDA(c, srk::launch_repulsion(a, c->stream));
+  return SR_OK;
+}
+
+sr_status sr_phi_step(sr_ctx* c, const float* psi_in, const float* w1, const float* w2,
+                      const float* b1, const float* b2, float* psi_out) {
+  if (!c) return SR_EINVAL;
+  if (!psi_in || !w1 || !w2 || !b1 || !b2 || !psi_out)
+    return fail(c, SR_EINVAL, "NULL pointer");
+  if (!aligned16(psi_in) || !aligned16(psi_out))
+    return fail(c, SR_EINVAL, "psi buffers must be 16-byte aligned");
+  return enqueue_phi_step(c, c->stream, psi_in, w1, w2, b1, b2, psi_out, nullptr);
+}
+
+sr_status sr_fft_solve(sr_ctx* c, const float* rhs, float* out) {
+  if (!c) return SR_EINVAL;
+  if (!rhs || !out) return fail(c, SR_EINVAL, "NULL pointer");
+  if (!aligned16(out)) return fail(c, SR_EINVAL, "out must be 16-byte aligned");
+  return enqueue_phi_step(c, c->stream, nullptr, nullptr, nullptr, nullptr, nullptr, out, rhs);
+}
+
+sr_status sr_w_b_update(sr_ctx* c, const float* phi1, const float* w1_in, const float* w2_in,
+                        const float* b1_in, const float* b2_in, float* w1_out, float* w2_out,
+                        float* b1_out, float* b2_out) {
+  if (!c) return SR_EINVAL;
+  if (!phi1 || !w1_in || !w2_in || !b1_in || !b2_in || !w1_out || !w2_out || !b1_out || !b2_out)
+    return fail(c, SR_EINVAL, "NULL pointer");
+  if (w1_out == w1_in || w2_out == w2_in || w1_out == w2_in || w2_out == w1_in)
+    return fail(c, SR_EINVAL, "w_out must not alias w_in");
+  return enqueue_wb(c, c->stream, phi1, w1_in, w2_in, b1_in, b2_in, w1_out, w2_out, b1_out,
+                    b2_out, nullptr);
+}
+
+long long sr_kernel_launches(const sr_ctx* c, int reset) {
+  if (!c) return 0;
+  const long long n = c->launches;
+  if (reset) const_cast<sr_ctx*>(c)->launches = 0;
+  return n;
+}
+
+sr_status sr_profile_enable(sr_ctx* c, int enable) {
+  if (!c) return SR_EINVAL;
+  c->profile = enable != 0;
+  return SR_OK;
+}
+
+sr_status sr_kernel_times(sr_ctx* c, int kclass, double* total_ms, long long* launches) {
+  if (!c) return SR_EINVAL;
+  if (kclass < 0 || kclass >= SR_KCLASS_COUNT) return fail(c, SR_EINVAL, "bad kernel class");
+  sr_status st = flush_profile(c);
+  if (st != SR_OK) return st;
+  if (total_ms) *total_ms = c->ktime[kclass];
+  if (launches) *launches = c->kcount[kclass];
+  c->ktime[kclass] = 0.0;
+  c->kcount[kclass] = 0;
+  return SR_OK;
+}
+
+sr_status sr_segment_host(sr_ctx* c, const float* image_host, const float* phi0_host,
+                          int max_outer, double tol, unsigned char* mask_host, float* phi_host,
+                          int* outer_done, double* rel_change) {
+  if (!c) return SR_EINVAL;
+  if (!image_host || !phi0_host || !mask_host) return fail(c, SR_EINVAL, "NULL host pointer");
+  const size_t P = (size_t)c->H * c->W;
+  SR_CUDA(c, cudaMemcpyAsync(c->stage, image_host, P * sizeof(float), cudaMemcpyHostToDevice,
+                             c->stream));
+  sr_status st = sr_edge_function(c, c->stage, c->W);
+  if (st != SR_OK) return st;
+  SR_CUDA(c, cudaMemcpyAsync(c->stage, phi0_host, P * sizeof(float), cudaMemcpyHostToDevice,
+                             c->stream));
+  if ((st = sr_set_phi(c, c->stage, c->W)) != SR_OK) return st;
+  sr_status it = sr_iterate(c, max_outer, tol, outer_done, rel_change);
+  if (it != SR_OK && it != SR_ENOTCONVERGED) return it;
+  if ((st = sr_mask(c, c->mask_dev, c->W)) != SR_OK) return st;
+  SR_CUDA(c, cudaMemcpyAsync(mask_host, c->mask_dev, P, cudaMemcpyDeviceToHost, c->stream));
+  if (phi_host)
+    SR_CUDA(c, cudaMemcpyAsync(phi_host, c->phi[c->cur], P * sizeof(float),
+                               cudaMemcpyDeviceToHost, c->stream));
+  SR_CUDA(c, cudaStreamSynchronize(c->stream));
+  return it;
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// Internal interface between the host library (sr_api.cu) and the kernels
+// (sr_kernels.cu).  Not part of the public C-ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace srk {
+
+constexpr int kMaxR = 8;        // largest repulsion window half width
+constexpr int kE = 16;          // complex values each thread holds per FFT stage
+constexpr int kColCB = 4;       // columns per CTA in the column pass
+constexpr int kTileX = 32;      // 2-D tile of the window-sum kernels
+constexpr int kTileY = 8;
+constexpr int kMaxGauss = 32;   // taps of the edge-detector Gaussian
+
+// Scalar model parameters in FP32 as the kernels use them.
+struct Model {
+  float alpha, beta, gamma, mu, tau, eps, band_l;
+  float beta2_mu;   // 2 beta / mu       (Eq. (41))
+  float gamma_mu;   // gamma / mu        (Eq. (42))
+  int R;            // window half width
+  float kw[2 * kMaxR + 1];  // k(p) = exp(-p^2 / d^2), p = -R..R at index p + R
+};
+
+// Stockham FFT plan of one power-of-two length: n16 radix-16 stages, then
+// one stage of radix `tail` (2, 4 or 8) unless tail == 1.
+struct Fft {
+  int L;                  // transform length
+  int logL;
+  int n16;
+  int tail;
+  const float2* tw;       // tw[q] = exp(-2 pi i q / L), q in [0, L)
+};
+
+struct Geo {
+  int M, N;     // rows, columns
+  int L;        // N / 2: complex length of a row transform
+  int logN;
+};
+
+// Row pass, forward: build the right-hand side of one inner step (or load it)
+// and store the packed half spectrum X[M][L].
+struct RowFwdArgs {
+  Geo geo;
+  Model mod;
+  Fft fft;                 // length L
+  const float2* twN;       // exp(-2 pi i k / N), k in [0, L)
+  const float* psi;
+  const float* g;
+  const float* w1;
+  const float* w2;
+  const float* b1;
+  const float* b2;
+  const float* src;        // LOAD mode: the right-hand side itself
+  float2* X;
+  int T;                   // rows per CTA
+  int CW;                  // column chunk of the window sum
+};
+
+// Column pass: forward column FFT, divide by the symbol of Eq. (32), inverse.
+struct ColArgs {
+  Geo geo;
+  Fft fft;                 // length M
+  const float* aM;         // tau mu 4 sin^2(pi l / M), l in [0, M)
+  const float* aN;         // tau mu 4 sin^2(pi k / N), k in [0, L]
+  float2* X;
+};
+
+// Row pass, inverse: half spectrum to real rows; ADD mode adds psi_in.
+struct RowInvArgs {
+  Geo geo;
+  Fft fft;
+  const float2* twN;
+  const float2* X;
+  const float* psi_in;     // ADD mode
+  float* out;
+  int T;
+};
+
+// w and b update with the repulsion window sum fused in.
+struct WBArgs {
+  Geo geo;
+  Model mod;
+  const float* phi1;       // phi^{k+1}
+  const float* g;
+  const float* w1;         // w^k
+  const float* w2;
+  const float* b1;         // b^k
+  const float* b2;
+  float* w1o;              // w^{k+1}
+  float* w2o;
+  float* b1o;              // b^{k+1} (may alias b1)
+  float* b2o;
+  const float* phi_old;    // phi^k for the stopping test, or nullptr
+  double* partials;        // 2 doubles per CTA when phi_old != nullptr
+};
+
+struct RepArgs {
+  Geo geo;
+  Model mod;
+  const float* phi;
+  const float* w1;
+  const float* w2;
+  float* v1;
+  float* v2;
+};
+
+struct EnergyArgs {
+  Geo geo;
+  Model mod;
+  const float* phi;
+  const float* g;
+  double* partials;        // 3 doubles per CTA: E_g, E_a, E_r
+};
+
+struct EdgeArgs {
+  Geo geo;
+  int r;                   // Gaussian radius
+  float k[2 * kMaxGauss + 1];
+  float rho;
+  int s_pow;
+};
+
+enum { kRowRHS = 0, kRowLOAD = 1 };
+enum { kInvADD = 0, kInvSTORE = 1 };
+
+// Shared-memory bytes of each kernel for the given configuration.
+size_t rowfwd_smem(int T, int L, int R, int CW, int mode);
+size_t colsolve_smem(int M);
+size_t rowinv_smem(int T, int L);
+size_t tile_smem(int R);
+
+// Launchers: enqueue on the stream and return the launch error.
+cudaError_t launch_rowfwd(const RowFwdArgs& a, int mode, int nthreads, cudaStream_t s);
+cudaError_t launch_colsolve(const ColArgs& a, cudaStream_t s);
+cudaError_t launch_rowinv(const RowInvArgs& a, int mode, int nthreads, cudaStream_t s);
+cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s);
+cudaError_t launch_repulsion(const RepArgs& a, cudaStream_t s);
+cudaError_t launch_energy(const EnergyArgs& a, cudaStream_t s);
+cudaError_t launch_reduce(const double* partials, int nblocks, int ncomp, double* out,
+                          cudaStream_t s);
+cudaError_t launch_init_wb(const float* phi, float* w1, float* w2, float* b1, float* b2,
+                           Geo geo, cudaStream_t s);
+cudaError_t launch_mask(const float* phi, unsigned char* mask, int ld, Geo geo,
+                        cudaStream_t s);
+cudaError_t launch_edge(const EdgeArgs& a, const float* f, int ld, float* tmp1, float* tmp2,
+                        float* g, cudaStream_t s);
+cudaError_t configure_kernels();   // raise dynamic shared-memory limits once
+int tile_blocks(const Geo& geo);   // CTAs of the 2-D tile kernels
+
+}  // namespace srk

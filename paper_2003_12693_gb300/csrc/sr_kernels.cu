@@ -1,0 +1,841 @@
+// sm_103a kernels of the Split Bregman self-repelling snake.
+//
+// One outer iteration of Alg. 1 is, per inner step s (Eq. (37)):
+//   k_rowfwd   repulsion window sum (Sec. 4), right-hand side, row R2C FFT
+//   k_colsolve column FFT, divide by the symbol of Eq. (32), inverse column FFT
+//   k_rowinv   row C2R FFT and phi update
+// and after the inner loop:
+//   k_wb_update repulsion window sum of Eq. (41), soft threshold (42),
+//               projection (40), Bregman update (23)
+//
+// The phi solve uses the increment form of Eq. (30): with L = 1 - tau mu Lap,
+//   L^{-1} F = psi + L^{-1} (F - L psi) = psi + L^{-1} [tau (force + mu Lap psi)],
+// which is the same solution in exact arithmetic but rounds relative to the
+// increment instead of |psi| (|phi| reaches 10^3 on large images).
+//
+// All kernels are memory-bound stencils, window sums and FFT passes: FP32
+// CUDA-core arithmetic, shared-memory staging, coalesced global access.
+#include <math.h>
+
+#include "sr_internal.h"
+
+namespace srk {
+
+// ---------------------------------------------------------------------------
+// Complex helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// a * (-i) for the forward transform, a * (+i) for the inverse
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// a * (c_re + sgn c_im i) with the sign chosen by the direction
+template <bool INV>
+__device__ __forceinline__ float2 mul_w(float2 a, float cr, float ci) {
+  const float s = INV ? ci : -ci;
+  return make_float2(a.x * cr - a.y * s, a.x * s + a.y * cr);
+}
+
+// ---------------------------------------------------------------------------
+// Small DFTs in registers, natural-order output.  Forward: exp(-2 pi i tm/r).
+// ---------------------------------------------------------------------------
+template <bool INV>
+__device__ __forceinline__ void dft2(float2* x) {
+  const float2 a = x[0], b = x[1];
+  x[0] = cadd(a, b);
+  x[1] = csub(a, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2* x) {
+  const float2 a0 = cadd(x[0], x[2]), a1 = csub(x[0], x[2]);
+  const float2 a2 = cadd(x[1], x[3]), a3 = mul_mi<INV>(csub(x[1], x[3]));
+  x[0] = cadd(a0, a2);
+  x[2] = csub(a0, a2);
+  x[1] = cadd(a1, a3);
+  x[3] = csub(a1, a3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* x) {
+  float2 e[4] = {x[0], x[2], x[4], x[6]};
+  float2 o[4] = {x[1], x[3], x[5], x[7]};
+  dft4<INV>(e);
+  dft4<INV>(o);
+  const float c = 0.70710678118654752440f;
+  o[1] = mul_w<INV>(o[1], c, c);
+  o[2] = mul_mi<INV>(o[2]);
+  o[3] = mul_w<INV>(o[3], -c, c);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    x[m] = cadd(e[m], o[m]);
+    x[m + 4] = csub(e[m], o[m]);
+  }
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* x) {
+  float2 e[8], o[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    e[m] = x[2 * m];
+    o[m] = x[2 * m + 1];
+  }
+  dft8<INV>(e);
+  dft8<INV>(o);
+  // W16^m = cos(pi m / 8) -+ i sin(pi m / 8)
+  const float C1 = 0.92387953251128675613f, S1 = 0.38268343236508977173f;
+  const float c = 0.70710678118654752440f;
+  o[1] = mul_w<INV>(o[1], C1, S1);
+  o[2] = mul_w<INV>(o[2], c, c);
+  o[3] = mul_w<INV>(o[3], S1, C1);
+  o[4] = mul_mi<INV>(o[4]);
+  o[5] = mul_w<INV>(o[5], -S1, C1);
+  o[6] = mul_w<INV>(o[6], -c, c);
+  o[7] = mul_w<INV>(o[7], -C1, S1);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    x[m] = cadd(e[m], o[m]);
+    x[m + 8] = csub(e[m], o[m]);
+  }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* x) {
+  if constexpr (R == 16) dft16<INV>(x);
+  else if constexpr (R == 8) dft8<INV>(x);
+  else if constexpr (R == 4) dft4<INV>(x);
+  else dft2<INV>(x);
+}
+
+// ---------------------------------------------------------------------------
+// Stockham autosort FFT in shared memory.  A CTA transforms several
+// sequences at once; each thread holds kE complex values per stage (kE / R
+// butterflies).  Stage (R, Ns): butterfly j reads x[j + t L/R], multiplies by
+// W_{Ns R}^{(j mod Ns) t}, applies the R-point DFT and writes
+// y[(j div Ns) Ns R + (j mod Ns) + t Ns].  All reads of a stage finish before
+// any write (barrier), so one buffer suffices.
+// ---------------------------------------------------------------------------
+struct RowLay {  // sequences stored one after another, 1 pad per 16 values
+  int S;
+  __device__ __forceinline__ int transform(int g, int logLr) const { return g >> logLr; }
+  __device__ __forceinline__ int index(int g, int logLr) const { return g & ((1 << logLr) - 1); }
+  __device__ __forceinline__ int addr(int c, int a) const { return c * S + a + (a >> 4); }
+};
+
+struct ColLay {  // kColCB sequences interleaved: value a of sequence c at a*CB + c
+  __device__ __forceinline__ int transform(int g, int) const { return g % kColCB; }
+  __device__ __forceinline__ int index(int g, int) const { return g / kColCB; }
+  __device__ __forceinline__ int addr(int c, int a) const { return a * kColCB + c; }
+};
+
+template <int R>
+struct Log2 {
+  static constexpr int v = R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : 1;
+};
+
+template <int R, bool INV, class Lay>
+__device__ __forceinline__ void fft_stage(float2* buf, const Lay& lay, const Fft& f, int logNs) {
+  constexpr int NB = kE / R;
+  constexpr int logR = Log2<R>::v;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int logLr = f.logL - logR;
+  const int Lr = 1 << logLr;
+  const int Ns = 1 << logNs;
+  float2 v[NB][R];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int gi = tid + b * NT;
+    const int c = lay.transform(gi, logLr), j = lay.index(gi, logLr);
+#pragma unroll
+    for (int t = 0; t < R; ++t) v[b][t] = buf[lay.addr(c, j + t * Lr)];
+  }
+  __syncthreads();
+  const int tshift = f.logL - logNs - logR;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int gi = tid + b * NT;
+    const int c = lay.transform(gi, logLr), j = lay.index(gi, logLr);
+    const int k = j & (Ns - 1);
+    if (logNs > 0) {
+#pragma unroll
+      for (int t = 1; t < R; ++t) {
+        float2 w = __ldg(&f.tw[(k * t) << tshift]);
+        if (INV) w.y = -w.y;
+        v[b][t] = cmul(v[b][t], w);
+      }
+    }
+    dft<R, INV>(v[b]);
+    const int base = ((j >> logNs) << (logNs + logR)) + k;
+#pragma unroll
+    for (int t = 0; t < R; ++t) buf[lay.addr(c, base + (t << logNs))] = v[b][t];
+  }
+  __syncthreads();
+}
+
+template <bool INV, class Lay>
+__device__ void fft_run(float2* buf, const Lay& lay, const Fft& f) {
+  int logNs = 0;
+  for (int s = 0; s < f.n16; ++s) {
+    fft_stage<16, INV>(buf, lay, f, logNs);
+    logNs += 4;
+  }
+  if (f.tail == 8) fft_stage<8, INV>(buf, lay, f, logNs);
+  else if (f.tail == 4) fft_stage<4, INV>(buf, lay, f, logNs);
+  else if (f.tail == 2) fft_stage<2, INV>(buf, lay, f, logNs);
+}
+
+// ---------------------------------------------------------------------------
+// Regularised functions, Eqs. (5), (6), (11), (28), (29), in FP32
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float heps(float x, float eps) {
+  if (x > eps) return 1.f;
+  if (x < -eps) return 0.f;
+  const float y = x / eps;
+  return 0.5f * (1.f + y + sinpif(y) * 0.318309886183790671538f);
+}
+__device__ __forceinline__ float deps(float x, float eps) {
+  if (fabsf(x) > eps) return 0.f;
+  return (1.f + cospif(x / eps)) * (0.5f / eps);
+}
+__device__ __forceinline__ float dpeps(float x, float eps) {
+  if (fabsf(x) > eps) return 0.f;
+  return -(1.57079632679489661923f / (eps * eps)) * sinpif(x / eps);
+}
+__device__ __forceinline__ float band_h(float x, const Model& m) {
+  if (fabsf(x) >= m.band_l + m.eps) return 0.f;
+  return heps(x + m.band_l, m.eps) * (1.f - heps(x - m.band_l, m.eps));
+}
+__device__ __forceinline__ float band_hp(float x, const Model& m) {
+  if (fabsf(x) >= m.band_l + m.eps) return 0.f;
+  return deps(x + m.band_l, m.eps) * (1.f - heps(x - m.band_l, m.eps)) -
+         heps(x + m.band_l, m.eps) * deps(x - m.band_l, m.eps);
+}
+
+// ---------------------------------------------------------------------------
+// Row pass, forward.  CTA = T rows.  RHS mode: for each column chunk, stage
+// u = h(psi) w on the chunk plus an R halo (zero outside the image), sum the
+// window separably (rows, then columns), then form the increment right-hand
+// side G = tau (force + mu Lap psi) of one inner step.  LOAD mode: G is read.
+// G of the T rows goes to shared memory as z[n] = G[2n] + i G[2n+1]; a length
+// L = N/2 complex FFT and the even/odd split give the N/2+1 values of the
+// real row transform, stored packed: X[0] = X_0 + i X_{N/2}.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rhs_increment(const RowFwdArgs& a, int i, int j, float v1,
+                                               float v2) {
+  const int M = a.geo.M, N = a.geo.N;
+  const Model& m = a.mod;
+  const size_t o = (size_t)i * N + j;
+  const size_t up = (size_t)(i == 0 ? M - 1 : i - 1) * N + j;
+  const size_t dn = (size_t)(i == M - 1 ? 0 : i + 1) * N + j;
+  const size_t lf = (size_t)i * N + (j == 0 ? N - 1 : j - 1);
+  const size_t rt = (size_t)i * N + (j == N - 1 ? 0 : j + 1);
+  const float x = a.psi[o];
+  const float lap = (a.psi[up] + a.psi[dn]) + (a.psi[lf] + a.psi[rt]) - 4.f * x;
+  const float W1 = a.w1[o], W2 = a.w2[o];
+  const float dv = ((a.b1[o] - W1) - (a.b1[up] - a.w1[up])) +
+                   ((a.b2[o] - W2) - (a.b2[lf] - a.w2[lf]));
+  float force = m.mu * (dv + lap);
+  if (fabsf(x) < m.band_l + m.eps) {
+    const float gg = a.g[o];
+    const float wn = sqrtf(W1 * W1 + W2 * W2);
+    force += -m.gamma * gg * wn * dpeps(x, m.eps) + m.alpha * gg * deps(x, m.eps) +
+             2.f * m.beta * band_hp(x, m) * (W1 * v1 + W2 * v2);
+  }
+  return m.tau * force;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512) k_rowfwd(const RowFwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = a.geo.M, N = a.geo.N, L = a.geo.L, T = a.T;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int S = L + (L >> 4);
+  float2* Z = reinterpret_cast<float2*>(smem_raw);
+  float* Zf = reinterpret_cast<float*>(smem_raw);
+  const int r0 = blockIdx.x * T;
+
+  if (MODE == kRowLOAD) {
+    for (int idx = tid; idx < T * N; idx += NT) {
+      const int t = idx >> a.geo.logN, j = idx & (N - 1);
+      const int i = r0 + t;
+      const float G = i < M ? a.src[(size_t)i * N + j] : 0.f;
+      const int cz = j >> 1;
+      Zf[2 * (t * S + cz + (cz >> 4)) + (j & 1)] = G;
+    }
+  } else {
+    const int R = a.mod.R;
+    const int CW = a.CW, CWH = CW + 2 * R, TH = T + 2 * R;
+    float* U1 = reinterpret_cast<float*>(Z + T * S);
+    float* U2 = U1 + TH * CWH;
+    float* V1 = U2 + TH * CWH;
+    float* V2 = V1 + T * CWH;
+    for (int c0 = 0; c0 < N; c0 += CW) {
+      for (int idx = tid; idx < TH * CWH; idx += NT) {
+        const int rr = idx / CWH, cc = idx - rr * CWH;
+        const int i = r0 - R + rr, j = c0 - R + cc;
+        float u1 = 0.f, u2 = 0.f;
+        if (i >= 0 && i < M && j >= 0 && j < N) {
+          const size_t o = (size_t)i * N + j;
+          const float h = band_h(a.psi[o], a.mod);
+          if (h != 0.f) {
+            u1 = h * a.w1[o];
+            u2 = h * a.w2[o];
+          }
+        }
+        U1[idx] = u1;
+        U2[idx] = u2;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < T * CWH; idx += NT) {
+        const int t = idx / CWH, cc = idx - t * CWH;
+        float s1 = 0.f, s2 = 0.f;
+        for (int p = 0; p <= 2 * R; ++p) {
+          const float kw = a.mod.kw[p];
+          s1 = fmaf(kw, U1[(t + p) * CWH + cc], s1);
+          s2 = fmaf(kw, U2[(t + p) * CWH + cc], s2);
+        }
+        V1[idx] = s1;
+        V2[idx] = s2;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < T * CW; idx += NT) {
+        const int t = idx / CW, c = idx - t * CW;
+        const int i = r0 + t, j = c0 + c;
+        float G = 0.f;
+        if (i < M) {
+          float v1 = 0.f, v2 = 0.f;
+          for (int q = 0; q <= 2 * R; ++q) {
+            const float kw = a.mod.kw[q];
+            v1 = fmaf(kw, V1[t * CWH + c + q], v1);
+            v2 = fmaf(kw, V2[t * CWH + c + q], v2);
+          }
+          G = rhs_increment(a, i, j, v1, v2);
+        }
+        const int cz = j >> 1;
+        Zf[2 * (t * S + cz + (cz >> 4)) + (j & 1)] = G;
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  fft_run<false>(Z, RowLay{S}, a.fft);
+
+  const int half = L / 2;
+  for (int idx = tid; idx < T * (half + 1); idx += NT) {
+    const int t = idx / (half + 1), k = idx - t * (half + 1);
+    const int i = r0 + t;
+    if (i >= M) continue;
+    const float2 Zk = Z[t * S + k + (k >> 4)];
+    float2* Xrow = a.X + (size_t)i * L;
+    if (k == 0) {
+      Xrow[0] = make_float2(Zk.x + Zk.y, Zk.x - Zk.y);
+      continue;
+    }
+    const int km = L - k;
+    const float2 Zm = Z[t * S + km + (km >> 4)];
+    // E = (Z_k + conj Z_{L-k}) / 2, O = -i (Z_k - conj Z_{L-k}) / 2
+    const float2 E = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
+    const float2 D = make_float2(0.5f * (Zk.x - Zm.x), 0.5f * (Zk.y + Zm.y));
+    const float2 O = make_float2(D.y, -D.x);
+    Xrow[k] = cadd(E, cmul(__ldg(&a.twN[k]), O));
+    if (km != k) Xrow[km] = cadd(cconj(E), cmul(__ldg(&a.twN[km]), cconj(O)));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass: kColCB columns of X per CTA, all M rows, in shared memory.
+// Forward column FFT, multiply by 1 / (M N lambda), inverse column FFT, with
+// lambda(l, k) = 1 + tau mu (4 sin^2(pi l/M) + 4 sin^2(pi k/N)) (Eq. (32)).
+// Column 0 packs the DC and Nyquist columns of the row transforms; both are
+// transforms of real sequences, split here with the conjugate pair (l, M-l)
+// so that each gets its own symbol.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_colsolve(const ColArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* Z = reinterpret_cast<float2*>(smem_raw);
+  const int M = a.geo.M, L = a.geo.L;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int c0 = blockIdx.x * kColCB;
+  const float inv_mn = 1.f / ((float)M * (float)a.geo.N);
+  for (int idx = tid; idx < M * kColCB; idx += NT) {
+    const int r = idx / kColCB, c = idx - r * kColCB;
+    Z[idx] = a.X[(size_t)r * L + c0 + c];
+  }
+  __syncthreads();
+  fft_run<false>(Z, ColLay{}, a.fft);
+  for (int idx = tid; idx < M * kColCB; idx += NT) {
+    const int l = idx / kColCB, c = idx - l * kColCB;
+    const int k = c0 + c;
+    if (k == 0) continue;
+    const float s = inv_mn / (1.f + a.aM[l] + a.aN[k]);
+    Z[idx] = make_float2(Z[idx].x * s, Z[idx].y * s);
+  }
+  if (c0 == 0) {
+    const float aNy = a.aN[L];
+    for (int l = tid; l <= M / 2; l += NT) {
+      const int lm = (M - l) & (M - 1);
+      const float2 Cl = Z[l * kColCB], Cm = Z[lm * kColCB];
+      const float sA = inv_mn / (1.f + a.aM[l] + a.aN[0]);
+      const float sB = inv_mn / (1.f + a.aM[l] + aNy);
+      // A = (C_l + conj C_{M-l}) / 2, B = (C_l - conj C_{M-l}) / (2i)
+      const float2 A = make_float2(0.5f * (Cl.x + Cm.x) * sA, 0.5f * (Cl.y - Cm.y) * sA);
+      const float2 D = make_float2(0.5f * (Cl.x - Cm.x), 0.5f * (Cl.y + Cm.y));
+      const float2 B = make_float2(D.y * sB, -D.x * sB);
+      Z[l * kColCB] = make_float2(A.x - B.y, A.y + B.x);
+      if (lm != l) Z[lm * kColCB] = make_float2(A.x + B.y, B.x - A.y);
+    }
+  }
+  __syncthreads();
+  fft_run<true>(Z, ColLay{}, a.fft);
+  for (int idx = tid; idx < M * kColCB; idx += NT) {
+    const int r = idx / kColCB, c = idx - r * kColCB;
+    a.X[(size_t)r * L + c0 + c] = Z[idx];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row pass, inverse: rebuild the length-L complex sequence whose inverse FFT
+// interleaves the even and odd samples of the real row, transform, unpack.
+// ADD mode: out = psi_in + x (the increment form), STORE mode: out = x.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(512) k_rowinv(const RowInvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* Z = reinterpret_cast<float2*>(smem_raw);
+  const int M = a.geo.M, N = a.geo.N, L = a.geo.L, T = a.T;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int S = L + (L >> 4);
+  const int r0 = blockIdx.x * T;
+  const int half = L / 2;
+  for (int idx = tid; idx < T * (half + 1); idx += NT) {
+    const int t = idx / (half + 1), k = idx - t * (half + 1);
+    const int i = r0 + t;
+    const int km = (L - k) & (L - 1);
+    if (i >= M) {
+      Z[t * S + k + (k >> 4)] = make_float2(0.f, 0.f);
+      Z[t * S + km + (km >> 4)] = make_float2(0.f, 0.f);
+      continue;
+    }
+    const float2* Xrow = a.X + (size_t)i * L;
+    if (k == 0) {
+      const float2 Y = Xrow[0];  // (X_0, X_{N/2})
+      Z[t * S] = make_float2(Y.x + Y.y, Y.x - Y.y);
+      continue;
+    }
+    const float2 Xk = Xrow[k], Xm = Xrow[km];
+    // Xe = X_k + conj X_{L-k},  Xo = (X_k - conj X_{L-k}) exp(+2 pi i k / N)
+    const float2 Xe = make_float2(Xk.x + Xm.x, Xk.y - Xm.y);
+    const float2 D = make_float2(Xk.x - Xm.x, Xk.y + Xm.y);
+    const float2 Xo = cmul(D, cconj(__ldg(&a.twN[k])));
+    Z[t * S + k + (k >> 4)] = make_float2(Xe.x - Xo.y, Xe.y + Xo.x);
+    if (km != k) {
+      const float2 Xe2 = cconj(Xe);
+      const float2 D2 = make_float2(-D.x, D.y);
+      const float2 Xo2 = cmul(D2, cconj(__ldg(&a.twN[km])));
+      Z[t * S + km + (km >> 4)] = make_float2(Xe2.x - Xo2.y, Xe2.y + Xo2.x);
+    }
+  }
+  __syncthreads();
+  fft_run<true>(Z, RowLay{S}, a.fft);
+  for (int idx = tid; idx < T * L; idx += NT) {
+    const int t = idx / L, n = idx - t * L;
+    const int i = r0 + t;
+    if (i >= M) continue;
+    const float2 z = Z[t * S + n + (n >> 4)];
+    const size_t o = (size_t)i * N + 2 * n;
+    float2 r = z;
+    if (MODE == kInvADD) {
+      const float2 p = *reinterpret_cast<const float2*>(a.psi_in + o);
+      r = make_float2(p.x + z.x, p.y + z.y);
+    }
+    *reinterpret_cast<float2*>(a.out + o) = r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2-D tile helpers for the window sum: u = h(phi) w on the tile plus an R
+// halo (zero outside the image), rows then columns.
+// ---------------------------------------------------------------------------
+struct TileSmem {
+  float U1[(kTileY + 2 * kMaxR) * (kTileX + 2 * kMaxR)];
+  float U2[(kTileY + 2 * kMaxR) * (kTileX + 2 * kMaxR)];
+  float V1[kTileY * (kTileX + 2 * kMaxR)];
+  float V2[kTileY * (kTileX + 2 * kMaxR)];
+};
+
+// After the call, (v1, v2) hold the window sum at this thread's pixel.
+template <class UFn>
+__device__ __forceinline__ void tile_window_sum(TileSmem& sm, const Geo& geo, const Model& m,
+                                                int i0, int j0, UFn ufn, float& v1, float& v2) {
+  const int R = m.R;
+  const int TW = kTileX + 2 * R, TH = kTileY + 2 * R;
+  const int tid = threadIdx.y * kTileX + threadIdx.x;
+  const int NT = kTileX * kTileY;
+  for (int idx = tid; idx < TH * TW; idx += NT) {
+    const int rr = idx / TW, cc = idx - rr * TW;
+    const int i = i0 - R + rr, j = j0 - R + cc;
+    float u1 = 0.f, u2 = 0.f;
+    if (i >= 0 && i < geo.M && j >= 0 && j < geo.N) ufn(i, j, u1, u2);
+    sm.U1[idx] = u1;
+    sm.U2[idx] = u2;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < kTileY * TW; idx += NT) {
+    const int t = idx / TW, cc = idx - t * TW;
+    float s1 = 0.f, s2 = 0.f;
+    for (int p = 0; p <= 2 * R; ++p) {
+      const float kw = m.kw[p];
+      s1 = fmaf(kw, sm.U1[(t + p) * TW + cc], s1);
+      s2 = fmaf(kw, sm.U2[(t + p) * TW + cc], s2);
+    }
+    sm.V1[idx] = s1;
+    sm.V2[idx] = s2;
+  }
+  __syncthreads();
+  float a1 = 0.f, a2 = 0.f;
+  for (int q = 0; q <= 2 * R; ++q) {
+    const float kw = m.kw[q];
+    a1 = fmaf(kw, sm.V1[threadIdx.y * TW + threadIdx.x + q], a1);
+    a2 = fmaf(kw, sm.V2[threadIdx.y * TW + threadIdx.x + q], a2);
+  }
+  v1 = a1;
+  v2 = a2;
+}
+
+// Fixed-order block reduction of NC doubles; thread 0 writes out[0..NC).
+template <int NC>
+__device__ __forceinline__ void block_sum_store(double (&val)[NC], double* out) {
+  __shared__ double red[NC][32];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    double v = val[c];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[c][warp] = v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      double s = 0.0;
+      for (int w = 0; w < nwarps; ++w) s += red[c][w];
+      out[c] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// w and b update (Eqs. (41), (42), (40), (23)) with the window sum fused in.
+// Soft threshold then projection: w = B/|B| if |B| > t, else 0.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTileX* kTileY) k_wb_update(const WBArgs a) {
+  __shared__ TileSmem sm;
+  const int i0 = blockIdx.y * kTileY, j0 = blockIdx.x * kTileX;
+  const int M = a.geo.M, N = a.geo.N;
+  const Model& m = a.mod;
+  float v1, v2;
+  tile_window_sum(sm, a.geo, m, i0, j0,
+                  [&](int i, int j, float& u1, float& u2) {
+                    const size_t o = (size_t)i * N + j;
+                    const float h = band_h(a.phi1[o], m);
+                    if (h != 0.f) {
+                      u1 = h * a.w1[o];
+                      u2 = h * a.w2[o];
+                    }
+                  },
+                  v1, v2);
+  const int i = i0 + threadIdx.y, j = j0 + threadIdx.x;
+  double part[2] = {0.0, 0.0};
+  if (i < M && j < N) {
+    const size_t o = (size_t)i * N + j;
+    const float x = a.phi1[o];
+    const float d1 = a.phi1[(size_t)(i == M - 1 ? 0 : i + 1) * N + j] - x;
+    const float d2 = a.phi1[(size_t)i * N + (j == N - 1 ? 0 : j + 1)] - x;
+    float B1 = d1 + a.b1[o];
+    float B2 = d2 + a.b2[o];
+    float thr = 0.f;
+    if (fabsf(x) < m.band_l + m.eps) {
+      const float h = band_h(x, m);
+      B1 = fmaf(m.beta2_mu * h, v1, B1);
+      B2 = fmaf(m.beta2_mu * h, v2, B2);
+      thr = m.gamma_mu * a.g[o] * deps(x, m.eps);
+    }
+    const float nB = sqrtf(B1 * B1 + B2 * B2);
+    float W1 = 0.f, W2 = 0.f;
+    if (nB > thr) {
+      W1 = B1 / nB;
+      W2 = B2 / nB;
+    }
+    a.w1o[o] = W1;
+    a.w2o[o] = W2;
+    a.b1o[o] = (a.b1[o] + d1) - W1;
+    a.b2o[o] = (a.b2[o] + d2) - W2;
+    if (a.phi_old) {
+      const double po = a.phi_old[o];
+      const double df = (double)x - po;
+      part[0] = df * df;
+      part[1] = po * po;
+    }
+  }
+  if (a.phi_old) block_sum_store<2>(part, a.partials + 2 * (blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+__global__ void __launch_bounds__(kTileX* kTileY) k_repulsion(const RepArgs a) {
+  __shared__ TileSmem sm;
+  const int i0 = blockIdx.y * kTileY, j0 = blockIdx.x * kTileX;
+  const int N = a.geo.N;
+  float v1, v2;
+  tile_window_sum(sm, a.geo, a.mod, i0, j0,
+                  [&](int i, int j, float& u1, float& u2) {
+                    const size_t o = (size_t)i * N + j;
+                    const float h = band_h(a.phi[o], a.mod);
+                    if (h != 0.f) {
+                      u1 = h * a.w1[o];
+                      u2 = h * a.w2[o];
+                    }
+                  },
+                  v1, v2);
+  const int i = i0 + threadIdx.y, j = j0 + threadIdx.x;
+  if (i < a.geo.M && j < N) {
+    a.v1[(size_t)i * N + j] = v1;
+    a.v2[(size_t)i * N + j] = v2;
+  }
+}
+
+// Discrete energy: per-pixel terms in FP32, accumulated in FP64.
+__global__ void __launch_bounds__(kTileX* kTileY) k_energy(const EnergyArgs a) {
+  __shared__ TileSmem sm;
+  const int i0 = blockIdx.y * kTileY, j0 = blockIdx.x * kTileX;
+  const int M = a.geo.M, N = a.geo.N;
+  const Model& m = a.mod;
+  auto grad = [&](int i, int j, float& d1, float& d2) {
+    const float x = a.phi[(size_t)i * N + j];
+    d1 = a.phi[(size_t)(i == M - 1 ? 0 : i + 1) * N + j] - x;
+    d2 = a.phi[(size_t)i * N + (j == N - 1 ? 0 : j + 1)] - x;
+  };
+  float v1, v2;
+  tile_window_sum(sm, a.geo, m, i0, j0,
+                  [&](int i, int j, float& u1, float& u2) {
+                    const float h = band_h(a.phi[(size_t)i * N + j], m);
+                    if (h != 0.f) {
+                      float d1, d2;
+                      grad(i, j, d1, d2);
+                      u1 = h * d1;
+                      u2 = h * d2;
+                    }
+                  },
+                  v1, v2);
+  const int i = i0 + threadIdx.y, j = j0 + threadIdx.x;
+  double part[3] = {0.0, 0.0, 0.0};
+  if (i < M && j < N) {
+    const size_t o = (size_t)i * N + j;
+    const float x = a.phi[o];
+    float d1, d2;
+    grad(i, j, d1, d2);
+    const double gg = a.g[o];
+    part[0] = gg * (double)sqrtf(d1 * d1 + d2 * d2) * (double)deps(x, m.eps);
+    part[1] = gg * (1.0 - (double)heps(x, m.eps));
+    part[2] = -(double)band_h(x, m) * ((double)d1 * v1 + (double)d2 * v2);
+  }
+  block_sum_store<3>(part, a.partials + 3 * (blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+// Sum the per-CTA partials in a fixed order (one CTA, deterministic).
+__global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ partials, int nblocks,
+                                                int ncomp, double* __restrict__ out) {
+  __shared__ double red[4][256];
+  for (int c = 0; c < ncomp; ++c) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[(size_t)b * ncomp + c];
+    red[c][threadIdx.x] = s;
+  }
+  __syncthreads();
+  for (int stride = blockDim.x / 2; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride)
+      for (int c = 0; c < ncomp; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + stride];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < ncomp; ++c) out[c] = red[c][0];
+}
+
+// Alg. 1 initialisation: w = grad phi (forward, periodic), b = 0.
+__global__ void k_init_wb(const float* __restrict__ phi, float* __restrict__ w1,
+                          float* __restrict__ w2, float* __restrict__ b1, float* __restrict__ b2,
+                          Geo geo) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (j >= geo.N) return;
+  const size_t o = (size_t)i * geo.N + j;
+  const float x = phi[o];
+  w1[o] = phi[(size_t)(i == geo.M - 1 ? 0 : i + 1) * geo.N + j] - x;
+  w2[o] = phi[(size_t)i * geo.N + (j == geo.N - 1 ? 0 : j + 1)] - x;
+  b1[o] = 0.f;
+  b2[o] = 0.f;
+}
+
+__global__ void k_mask(const float* __restrict__ phi, unsigned char* __restrict__ mask, int ld,
+                       Geo geo) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (j >= geo.N) return;
+  mask[(size_t)i * ld + j] = phi[(size_t)i * geo.N + j] < 0.f ? 1 : 0;
+}
+
+// Edge detector, Eq. (1): blur along rows (index i), then columns, replicated
+// border; central differences inside, one-sided on the border.
+__global__ void k_blur_i(const EdgeArgs a, const float* __restrict__ f, int ld,
+                         float* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (j >= a.geo.N) return;
+  float s = 0.f;
+  for (int t = -a.r; t <= a.r; ++t) {
+    const int ii = min(max(i + t, 0), a.geo.M - 1);
+    s = fmaf(a.k[t + a.r], f[(size_t)ii * ld + j], s);
+  }
+  out[(size_t)i * a.geo.N + j] = s;
+}
+
+__global__ void k_blur_j(const EdgeArgs a, const float* __restrict__ in, float* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (j >= a.geo.N) return;
+  float s = 0.f;
+  for (int t = -a.r; t <= a.r; ++t) {
+    const int jj = min(max(j + t, 0), a.geo.N - 1);
+    s = fmaf(a.k[t + a.r], in[(size_t)i * a.geo.N + jj], s);
+  }
+  out[(size_t)i * a.geo.N + j] = s;
+}
+
+__global__ void k_edge_g(const EdgeArgs a, const float* __restrict__ b, float* __restrict__ g) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  const int M = a.geo.M, N = a.geo.N;
+  if (j >= N) return;
+  auto B = [&](int ii, int jj) { return b[(size_t)ii * N + jj]; };
+  float gi, gj;
+  if (M == 1) gi = 0.f;
+  else if (i == 0) gi = B(1, j) - B(0, j);
+  else if (i == M - 1) gi = B(M - 1, j) - B(M - 2, j);
+  else gi = 0.5f * (B(i + 1, j) - B(i - 1, j));
+  if (N == 1) gj = 0.f;
+  else if (j == 0) gj = B(i, 1) - B(i, 0);
+  else if (j == N - 1) gj = B(i, N - 1) - B(i, N - 2);
+  else gj = 0.5f * (B(i, j + 1) - B(i, j - 1));
+  const float m2 = gi * gi + gj * gj;
+  const float mag = a.s_pow == 2 ? m2 : sqrtf(m2);
+  g[(size_t)i * N + j] = 1.f / (1.f + a.rho * mag);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+size_t rowfwd_smem(int T, int L, int R, int CW, int mode) {
+  const size_t S = (size_t)L + (L >> 4);
+  size_t bytes = (size_t)T * S * sizeof(float2);
+  if (mode == kRowRHS) {
+    const size_t CWH = (size_t)CW + 2 * R, TH = (size_t)T + 2 * R;
+    bytes += (2 * TH * CWH + 2 * (size_t)T * CWH) * sizeof(float);
+  }
+  return bytes;
+}
+size_t colsolve_smem(int M) { return (size_t)M * kColCB * sizeof(float2); }
+size_t rowinv_smem(int T, int L) { return (size_t)T * (L + (L >> 4)) * sizeof(float2); }
+size_t tile_smem(int) { return sizeof(TileSmem); }
+
+int tile_blocks(const Geo& geo) {
+  return ((geo.N + kTileX - 1) / kTileX) * ((geo.M + kTileY - 1) / kTileY);
+}
+
+cudaError_t configure_kernels() {
+  const int big = 227 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_rowfwd<kRowRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_rowfwd<kRowLOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_colsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_rowinv<kInvADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_rowinv<kInvSTORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+    return e;
+  return cudaSuccess;
+}
+
+cudaError_t launch_rowfwd(const RowFwdArgs& a, int mode, int nthreads, cudaStream_t s) {
+  const int grid = (a.geo.M + a.T - 1) / a.T;
+  const size_t sm = rowfwd_smem(a.T, a.geo.L, a.mod.R, a.CW, mode);
+  if (mode == kRowRHS) k_rowfwd<kRowRHS><<<grid, nthreads, sm, s>>>(a);
+  else k_rowfwd<kRowLOAD><<<grid, nthreads, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colsolve(const ColArgs& a, cudaStream_t s) {
+  const int grid = a.geo.L / kColCB;
+  const int nthreads = a.geo.M * kColCB / kE;
+  k_colsolve<<<grid, nthreads, colsolve_smem(a.geo.M), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowinv(const RowInvArgs& a, int mode, int nthreads, cudaStream_t s) {
+  const int grid = (a.geo.M + a.T - 1) / a.T;
+  const size_t sm = rowinv_smem(a.T, a.geo.L);
+  if (mode == kInvADD) k_rowinv<kInvADD><<<grid, nthreads, sm, s>>>(a);
+  else k_rowinv<kInvSTORE><<<grid, nthreads, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+static dim3 tile_grid(const Geo& geo) {
+  return dim3((geo.N + kTileX - 1) / kTileX, (geo.M + kTileY - 1) / kTileY);
+}
+
+cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s) {
+  k_wb_update<<<tile_grid(a.geo), dim3(kTileX, kTileY), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_repulsion(const RepArgs& a, cudaStream_t s) {
+  k_repulsion<<<tile_grid(a.geo), dim3(kTileX, kTileY), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const EnergyArgs& a, cudaStream_t s) {
+  k_energy<<<tile_grid(a.geo), dim3(kTileX, kTileY), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const double* partials, int nblocks, int ncomp, double* out,
+                          cudaStream_t s) {
+  k_reduce<<<1, 256, 0, s>>>(partials, nblocks, ncomp, out);
+  return cudaGetLastError();
+}
+
+static dim3 row_grid(const Geo& geo) { return dim3((geo.N + 127) / 128, geo.M); }
+
+cudaError_t launch_init_wb(const float* phi, float* w1, float* w2, float* b1, float* b2, Geo geo,
+                           cudaStream_t s) {
+  k_init_wb<<<row_grid(geo), 128, 0, s>>>(phi, w1, w2, b1, b2, geo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask(const float* phi, unsigned char* mask, int ld, Geo geo, cudaStream_t s) {
+  k_mask<<<row_grid(geo), 128, 0, s>>>(phi, mask, ld, geo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_edge(const EdgeArgs& a, const float* f, int ld, float* tmp1, float* tmp2,
+                        float* g, cudaStream_t s) {
+  k_blur_i<<<row_grid(a.geo), 128, 0, s>>>(a, f, ld, tmp1);
+  k_blur_j<<<row_grid(a.geo), 128, 0, s>>>(a, tmp1, tmp2);
+  k_edge_g<<<row_grid(a.geo), 128, 0, s>>>(a, tmp2, g);
+  return cudaGetLastError();
+}
+
+}  // namespace srk

@@ -18,3 +18,10 @@ def oracle_lib():
     import oracle
     oracle.lib()
     return oracle
+
+
+def pytest_sessionfinish(session, exitstatus):
+    import sys as _sys
+    mod = _sys.modules.get("gpu_common")
+    if mod is not None:
+        mod.write_report()
