@@ -164,6 +164,33 @@ sr_status sr_w_b_update(sr_ctx* ctx, const float* phi1, const float* w1_in,
                         const float* w2_in, const float* b1_in, const float* b2_in,
                         float* w1_out, float* w2_out, float* b1_out, float* b2_out);
 
+/* One inner step of the phi update, like sr_phi_step, for callers that
+ * cannot allocate device memory.  The paper has no counterpart: this entry
+ * point exists for hosts that hand out all GPU memory from their own fixed
+ * arena, for code running while its stream is captured into a CUDA graph in a
+ * mode that forbids allocation, and for real-time loops that cannot afford
+ * the device synchronisation cudaMalloc / cudaFree may cause.
+ * It takes no context and allocates nothing: the half spectrum and the FFT and
+ * symbol tables live in a file-scope device array of 1 MiB + 16 KiB that the
+ * library reserves on every GPU that loads it, until the process exits.
+ *   H, W:  powers of two with 16 <= H, W <= 512; larger sizes return
+ *          SR_EUNSUPPORTED and launch nothing.
+ *   p:     model parameters (inner_S, inner_tol, rho, sigma, s_pow and
+ *          check_every are ignored); invalid values return SR_EINVAL.
+ *   g, psi_in, w1, w2, b1, b2: device inputs, contiguous H x W float32;
+ *          psi_out: device output, may alias psi_in; psi_in and psi_out must
+ *          be 16-byte aligned.
+ *   cuda_stream: cudaStream_t the work is enqueued on (0: legacy stream).
+ * The first call on a device looks up the array's device address and sets
+ * kernel attributes, so make that first call before any stream capture.
+ * Every call rewrites the whole array before reading it, so nothing carries
+ * over between calls, but calls whose work overlaps on the GPU race on the
+ * array: order them on one stream.  SR_ECUDA if a CUDA call fails. */
+sr_status sr_phi_step_noalloc(int H, int W, const sr_params* p, const float* g,
+                              const float* psi_in, const float* w1, const float* w2,
+                              const float* b1, const float* b2, float* psi_out,
+                              void* cuda_stream);
+
 /* Kernel launches enqueued by this context since creation (or the last
  * reset).  Graph launches count every kernel node they run. */
 long long sr_kernel_launches(const sr_ctx* ctx, int reset);

@@ -98,6 +98,8 @@ def lib() -> C.CDLL:
     L.sr_profile_enable.argtypes = [_P, C.c_int]
     L.sr_kernel_times.restype = st
     L.sr_kernel_times.argtypes = [_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.sr_phi_step_noalloc.restype = st
+    L.sr_phi_step_noalloc.argtypes = [C.c_int, C.c_int, C.POINTER(sr_params)] + [_P] * 7 + [_P]
     L.sr_segment_host.restype = st
     L.sr_segment_host.argtypes = [_P, _P, _P, C.c_int, C.c_double, _P, _P,
                                   C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -280,3 +282,26 @@ class Context:
                                    C.byref(done), C.byref(rel))
         _check(st, self)
         return done.value, rel.value
+
+
+def phi_step_noalloc(params: sr_params, g: torch.Tensor, psi: torch.Tensor, w1: torch.Tensor,
+                     w2: torch.Tensor, b1: torch.Tensor, b2: torch.Tensor,
+                     out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """sr_phi_step_noalloc: one inner phi step without a context and without
+    allocating device memory (for callers that cannot allocate; sizes up to
+    512 x 512).  Tensors: contiguous float32 (H, W) on the current device."""
+    H, W = psi.shape
+    for t in (g, psi, w1, w2, b1, b2):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or \
+                tuple(t.shape) != (H, W):
+            raise ValueError("inputs must be contiguous float32 CUDA tensors of one shape")
+    out = torch.empty_like(psi) if out is None else out
+    stream = torch.cuda.current_stream() if stream is None else stream
+    st = lib().sr_phi_step_noalloc(int(H), int(W), C.byref(params),
+                                   *[C.c_void_p(t.data_ptr()) for t in (g, psi, w1, w2, b1, b2, out)],
+                                   C.c_void_p(stream.cuda_stream))
+    if st == SR_EUNSUPPORTED:
+        raise SRError(st, f"{H} x {W} is not a power-of-two size within the 512 x 512 maximum "
+                          "of the fixed scratch array")
+    _check(st, None)
+    return out
