@@ -38,13 +38,14 @@ METRIC = ("SR Mpixel·iter/s (% HBM peak); s per converged mask, plain vs "
 UNIT = "Mpixel·iter/s"
 
 # Algorithmic bytes per pixel of one launch of each kernel (FP32 planes):
-#   rhs_rowfft: read psi, g, w1, w2, b1, b2 (24 B), write the half spectrum (4 B)
-#   colsolve:   read and write the half spectrum (8 B)
-#   rowifft:    read the half spectrum (4 B) and psi (4 B), write psi (4 B)
-#   wb_update:  read phi, g, w1, w2, b1, b2 (24 B), write w1, w2, b1, b2 (16 B)
-BYTES_PER_PX = {"rhs_rowfft": 28, "colsolve": 8, "rowifft": 12, "wb_update": 40}
-KERNEL_NAMES = {"rhs_rowfft": "k_rowfwd", "colsolve": "k_colsolve", "rowifft": "k_rowinv",
-                "wb_update": "k_wb_update"}
+#   prep:      read psi, g, w1, w2, b1, b2 (24 B), write the right-hand side G (4 B)
+#   rowfft:    read G (4 B), write the half spectrum (4 B)
+#   colsolve:  read and write the half spectrum (8 B)
+#   rowifft:   read the half spectrum (4 B) and psi (4 B), write psi (4 B)
+#   wb_update: read phi, g, w1, w2, b1, b2 (24 B), write w1, w2, b1, b2 (16 B)
+BYTES_PER_PX = {"prep": 28, "rowfft": 8, "colsolve": 8, "rowifft": 12, "wb_update": 40}
+KERNEL_NAMES = {"prep": "k_prep", "rowfft": "k_rowfwd", "colsolve": "k_colsolve",
+                "rowifft": "k_rowinv", "wb_update": "k_wb_update"}
 
 
 def _peaks():
@@ -254,6 +255,7 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
     ctx.set_phi(phi0_d)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     P = wl.H * wl.W
+    schedule = ctx.get_schedule()
 
     # warm-up (also builds the CUDA graphs)
     ctx.iterate(args.warmup)
@@ -357,7 +359,8 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
         "config": {"workload": wl.name, "H": wl.H, "W": wl.W, "R": wl.R, "d": wl.d, "S": 3,
                    "description": wl.description,
                    "l2": "flushed (256 MiB write) between timed steps, outside the events",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "fft_schedule": schedule},
         "roofline": roofline,
         "iteration_roofline": iteration_roofline,
         "cpu_baseline": cpu,

@@ -142,7 +142,9 @@ sr_status sr_energy(sr_ctx* ctx, double* E, double* Eg, double* Ea, double* Er);
 
 /* ---- Single steps of the hot path (device buffers, contiguous H x W) ----
  * These run one row of the iteration on caller buffers with the context's
- * parameters and g; they exist so each step can be checked on its own. */
+ * parameters and g; they exist so each step can be checked on its own.
+ * sr_phi_step, sr_fft_solve (out) and sr_w_b_update need 16-byte aligned
+ * buffers (SR_EINVAL otherwise). */
 
 /* Sec. 4 repulsion field: v = sum_{p,q=-R..R} exp(-(p^2+q^2)/d^2)
  * w_{i+p,j+q} h(phi_{i+p,j+q}), terms outside the image dropped. */
@@ -191,6 +193,29 @@ sr_status sr_phi_step_noalloc(int H, int W, const sr_params* p, const float* g,
                               const float* b1, const float* b2, float* psi_out,
                               void* cuda_stream);
 
+/* FFT schedule of the phi solve: how the row and column passes of Eqs.
+ * (31)-(33) are laid out on the GPU.  sr_create picks it by timing the
+ * candidates once per image size in the process (the result is cached), so
+ * it depends on the device.  Every schedule computes the same transform.
+ *   row_values_per_thread: 8 or 16 (radix-8 or radix-16 stages)
+ *   row_threads: threads per CTA of the row passes; rows per CTA =
+ *                row_threads * row_values_per_thread / (W / 2)
+ *   col_schedule: 0 = 4 columns per CTA, 16 values per thread (2 columns at
+ *                 H = 4096); 1 = 2 columns, 8 values; 2 = 4 columns, 8 values
+ *   tuned_us: measured microseconds of one row pair plus one column pass
+ *             when the autotuner chose the schedule, else 0.
+ * Sizes below W = 32 use fixed kernels and report row_threads = 0.
+ * sr_set_schedule validates the fields (SR_EINVAL) and rebuilds the
+ * iteration graphs. */
+typedef struct sr_schedule {
+  int row_values_per_thread;
+  int row_threads;
+  int col_schedule;
+  float tuned_us;
+} sr_schedule;
+sr_status sr_get_schedule(sr_ctx* ctx, sr_schedule* out);
+sr_status sr_set_schedule(sr_ctx* ctx, const sr_schedule* sched);
+
 /* Kernel launches enqueued by this context since creation (or the last
  * reset).  Graph launches count every kernel node they run. */
 long long sr_kernel_launches(const sr_ctx* ctx, int reset);
@@ -200,12 +225,13 @@ long long sr_kernel_launches(const sr_ctx* ctx, int reset);
  * sr_kernel_times synchronises and returns, for kernel class c (see
  * SR_KCLASS_*), the summed milliseconds and the launch count, then clears
  * the accumulators. */
-#define SR_KCLASS_RHS_ROWFFT 0   /* repulsion + right-hand side + row R2C FFT */
+#define SR_KCLASS_ROWFFT 0       /* row R2C FFT of the right-hand side */
 #define SR_KCLASS_COLSOLVE 1     /* column FFT, divide by the symbol, inverse */
 #define SR_KCLASS_ROWIFFT 2      /* row C2R FFT + phi update */
 #define SR_KCLASS_WB_UPDATE 3    /* repulsion + shrink + projection + Bregman */
 #define SR_KCLASS_REDUCE 4       /* FP64 stopping-test reduction */
-#define SR_KCLASS_COUNT 5
+#define SR_KCLASS_PREP 5         /* repulsion window sum + right-hand side */
+#define SR_KCLASS_COUNT 6
 sr_status sr_profile_enable(sr_ctx* ctx, int enable);
 sr_status sr_kernel_times(sr_ctx* ctx, int kclass, double* total_ms, long long* launches);
 

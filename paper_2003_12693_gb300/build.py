@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsr.so")
-SOURCES = ["sr_kernels.cu", "sr_api.cu", "sr_noalloc.cu"]
+SOURCES = ["sr_kernels.cu", "sr_fft.cu", "sr_api.cu", "sr_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 
@@ -53,9 +53,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 print(" ".join(cmd))
             procs.append(subprocess.Popen(cmd))
             objs.append(obj)
-        for p in procs:
-            if p.wait() != 0:
-                raise RuntimeError("nvcc failed while building libsr.so")
+        codes = [p.wait() for p in procs]
+        if any(codes):
+            raise RuntimeError("nvcc failed while building libsr.so")
         out_tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc, *ARCH, "-shared", "-o", out_tmp, *objs]
         subprocess.run(cmd, check=True)

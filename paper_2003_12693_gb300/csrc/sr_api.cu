@@ -6,8 +6,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "sr.h"
@@ -28,7 +31,10 @@ struct sr_ctx {
   Model mod{};
   Fft fft_row{}, fft_col{};
   int row_T = 0, row_NT = 0, row_CW = 0;
-  int n_tile = 0;
+  bool fft2 = false;  // register-resident FFT passes (sr_fft.cu) for this size
+  sr_schedule sched{};  // schedule of the fft2 passes
+  int n_tile = 0;    // CTAs of the 32 x 8 tile kernels (energy)
+  int n_tile32 = 0;  // CTAs of the 32 x 32 tile kernels (w/b update)
 
   // device state
   float* phi[2] = {nullptr, nullptr};
@@ -40,6 +46,7 @@ struct sr_ctx {
   float* tmp1 = nullptr;
   float* tmp2 = nullptr;
   float* stage = nullptr;
+  float* G = nullptr;         // increment right-hand side of the current inner step
   unsigned char* mask_dev = nullptr;
   float2* X = nullptr;
   float2* tw_row = nullptr;
@@ -215,28 +222,183 @@ sr_status run_kernel(sr_ctx* c, int kclass, cudaStream_t s, const char* name, F 
   return SR_OK;
 }
 
+// ---- FFT schedule -----------------------------------------------------------
+int sched_rows(const sr_ctx* c, const sr_schedule& sc) {
+  return sc.row_threads * sc.row_values_per_thread / c->L;
+}
+
+bool sched_valid(const sr_ctx* c, const sr_schedule& sc) {
+  if (!c->fft2) return false;
+  if (sc.row_values_per_thread != 8 && sc.row_values_per_thread != 16) return false;
+  if (sc.col_schedule < 0 || sc.col_schedule > 2) return false;
+  if (srk::colsolve2_threads(c->H, sc.col_schedule) > 1024) return false;
+  if (sc.row_threads < 1 || sc.row_threads > 512) return false;
+  const long long prod = (long long)sc.row_threads * sc.row_values_per_thread;
+  if (prod % c->L) return false;
+  const int T = (int)(prod / c->L);
+  if (T < 1 || T > c->H) return false;
+  if (sc.row_threads != T * c->L / sc.row_values_per_thread) return false;
+  return srk::rowfft2_smem(T, c->L) <= 200 * 1024;
+}
+
+// raise the shared-memory limits of the kernels a schedule uses
+cudaError_t sched_configure(sr_ctx* c, const sr_schedule& sc) {
+  srk::RowFwdArgs fa{};
+  fa.geo = c->geo;
+  fa.T = sched_rows(c, sc);
+  srk::RowInvArgs ia{};
+  ia.geo = c->geo;
+  ia.T = fa.T;
+  srk::ColArgs ca{};
+  ca.geo = c->geo;
+  const int le = sc.row_values_per_thread == 8 ? 3 : 4;
+  cudaError_t e = srk::launch_rowfft2(fa, le, sc.row_threads, nullptr, true);
+  if (e == cudaSuccess) e = srk::launch_rowifft2(ia, true, le, sc.row_threads, nullptr, true);
+  if (e == cudaSuccess) e = srk::launch_colsolve2(ca, sc.col_schedule, nullptr, true);
+  return e;
+}
+
+std::mutex g_tune_mutex;
+std::map<std::pair<int, int>, std::pair<int, sr_schedule>> g_tuned;  // (H, W) -> (device, schedule)
+
+// Time the candidate row and column schedules on the context's buffers and
+// keep the fastest (once per image size and device in the process).
+sr_status autotune(sr_ctx* c) {
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find({c->H, c->W});
+    if (it != g_tuned.end() && it->second.first == c->device) {
+      c->sched = it->second.second;
+      SR_CUDA(c, sched_configure(c, c->sched));
+      return SR_OK;
+    }
+  }
+  const size_t P = (size_t)c->H * c->W;
+  SR_CUDA(c, cudaMemset(c->G, 0, P * sizeof(float)));
+  SR_CUDA(c, cudaMemset(c->X, 0, (size_t)c->H * c->L * sizeof(float2)));
+  SR_CUDA(c, cudaDeviceSynchronize());
+  cudaStream_t s = c->cap_stream;
+  cudaEvent_t e0, e1;
+  SR_CUDA(c, cudaEventCreate(&e0));
+  SR_CUDA(c, cudaEventCreate(&e1));
+  auto time_it = [&](auto&& launch, float* us) -> cudaError_t {
+    cudaError_t e = launch();
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(e0, s)) != cudaSuccess) return e;
+    const int reps = 5;
+    for (int r = 0; r < reps; ++r)
+      if ((e = launch()) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(e1, s)) != cudaSuccess) return e;
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) return e;
+    *us = 1000.f * ms / reps;
+    return cudaSuccess;
+  };
+  sr_schedule best{};
+  float best_row = 1e30f;
+  const int vpts[2] = {16, 8};
+  const int threads[4] = {64, 128, 256, 512};
+  cudaError_t err = cudaSuccess;
+  for (int vi = 0; vi < 2 && err == cudaSuccess; ++vi)
+    for (int ti = 0; ti < 4 && err == cudaSuccess; ++ti) {
+      sr_schedule sc{vpts[vi], threads[ti], 0, 0.f};
+      if (!sched_valid(c, sc)) continue;
+      if ((err = sched_configure(c, sc)) != cudaSuccess) break;
+      srk::RowFwdArgs fa{};
+      fa.geo = c->geo;
+      fa.fft = c->fft_row;
+      fa.twN = c->tw_n;
+      fa.src = c->G;
+      fa.X = c->X;
+      fa.T = sched_rows(c, sc);
+      srk::RowInvArgs ia{};
+      ia.geo = c->geo;
+      ia.fft = c->fft_row;
+      ia.twN = c->tw_n;
+      ia.X = c->X;
+      ia.psi_in = c->tmp1;
+      ia.out = c->tmp2;
+      ia.T = fa.T;
+      const int le = sc.row_values_per_thread == 8 ? 3 : 4;
+      float us = 0.f;
+      err = time_it([&] {
+        cudaError_t e = srk::launch_rowfft2(fa, le, sc.row_threads, s, false);
+        return e != cudaSuccess ? e : srk::launch_rowifft2(ia, true, le, sc.row_threads, s, false);
+      }, &us);
+      if (err == cudaSuccess && us < best_row) {
+        best_row = us;
+        best.row_values_per_thread = sc.row_values_per_thread;
+        best.row_threads = sc.row_threads;
+      }
+    }
+  float best_col = 1e30f;
+  for (int cs = 0; cs < 3 && err == cudaSuccess; ++cs) {
+    sr_schedule sc = best;
+    sc.col_schedule = cs;
+    if (!sched_valid(c, sc)) continue;
+    if ((err = sched_configure(c, sc)) != cudaSuccess) break;
+    srk::ColArgs ca{};
+    ca.geo = c->geo;
+    ca.fft = c->fft_col;
+    ca.aM = c->aM;
+    ca.aN = c->aN;
+    ca.X = c->X;
+    float us = 0.f;
+    err = time_it([&] { return srk::launch_colsolve2(ca, cs, s, false); }, &us);
+    if (err == cudaSuccess && us < best_col) {
+      best_col = us;
+      best.col_schedule = cs;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(c, err, "FFT schedule autotuner");
+  best.tuned_us = best_row + best_col;
+  c->sched = best;
+  SR_CUDA(c, sched_configure(c, best));
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tuned[{c->H, c->W}] = {c->device, best};
+  return SR_OK;
+}
+
 // ---- one inner step: psi_out = psi_in + L^{-1} G ---------------------------
+// With load_src set, the step solves L out = load_src instead (Eqs. (31)-(33)
+// alone).
 sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const float* w1,
                            const float* w2, const float* b1, const float* b2, float* psi_out,
                            const float* load_src) {
+  sr_status st;
+  const float* src = load_src;
+  if (!load_src) {
+    srk::PrepArgs pa{};
+    pa.geo = c->geo;
+    pa.mod = c->mod;
+    pa.psi = psi_in;
+    pa.g = c->g;
+    pa.w1 = w1;
+    pa.w2 = w2;
+    pa.b1 = b1;
+    pa.b2 = b2;
+    pa.G = c->G;
+    st = run_kernel(c, SR_KCLASS_PREP, s, "k_prep", [&] { return srk::launch_prep(pa, s); });
+    if (st != SR_OK) return st;
+    src = c->G;
+  }
   srk::RowFwdArgs fa{};
   fa.geo = c->geo;
   fa.mod = c->mod;
   fa.fft = c->fft_row;
   fa.twN = c->tw_n;
-  fa.psi = psi_in;
-  fa.g = c->g;
-  fa.w1 = w1;
-  fa.w2 = w2;
-  fa.b1 = b1;
-  fa.b2 = b2;
-  fa.src = load_src;
+  fa.src = src;
   fa.X = c->X;
-  fa.T = c->row_T;
+  fa.T = c->fft2 ? sched_rows(c, c->sched) : c->row_T;
   fa.CW = c->row_CW;
-  const int mode = load_src ? srk::kRowLOAD : srk::kRowRHS;
-  sr_status st = run_kernel(c, SR_KCLASS_RHS_ROWFFT, s, "k_rowfwd",
-                            [&] { return srk::launch_rowfwd(fa, mode, c->row_NT, s); });
+  st = run_kernel(c, SR_KCLASS_ROWFFT, s, "k_rowfwd", [&] {
+    return c->fft2 ? srk::launch_rowfft2(fa, c->sched.row_values_per_thread == 8 ? 3 : 4,
+                                         c->sched.row_threads, s, false)
+                   : srk::launch_rowfwd(fa, srk::kRowLOAD, c->row_NT, s);
+  });
   if (st != SR_OK) return st;
   srk::ColArgs ca{};
   ca.geo = c->geo;
@@ -244,8 +406,10 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
   ca.aM = c->aM;
   ca.aN = c->aN;
   ca.X = c->X;
-  st = run_kernel(c, SR_KCLASS_COLSOLVE, s, "k_colsolve",
-                  [&] { return srk::launch_colsolve(ca, s); });
+  st = run_kernel(c, SR_KCLASS_COLSOLVE, s, "k_colsolve", [&] {
+    return c->fft2 ? srk::launch_colsolve2(ca, c->sched.col_schedule, s, false)
+                   : srk::launch_colsolve(ca, s);
+  });
   if (st != SR_OK) return st;
   srk::RowInvArgs ia{};
   ia.geo = c->geo;
@@ -254,10 +418,14 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
   ia.X = c->X;
   ia.psi_in = psi_in;
   ia.out = psi_out;
-  ia.T = c->row_T;
+  ia.T = c->fft2 ? sched_rows(c, c->sched) : c->row_T;
   const int imode = load_src ? srk::kInvSTORE : srk::kInvADD;
-  return run_kernel(c, SR_KCLASS_ROWIFFT, s, "k_rowinv",
-                    [&] { return srk::launch_rowinv(ia, imode, c->row_NT, s); });
+  return run_kernel(c, SR_KCLASS_ROWIFFT, s, "k_rowinv", [&] {
+    return c->fft2 ? srk::launch_rowifft2(ia, imode == srk::kInvADD,
+                                          c->sched.row_values_per_thread == 8 ? 3 : 4,
+                                          c->sched.row_threads, s, false)
+                   : srk::launch_rowinv(ia, imode, c->row_NT, s);
+  });
 }
 
 sr_status enqueue_wb(sr_ctx* c, cudaStream_t s, const float* phi1, const float* w1i,
@@ -282,7 +450,7 @@ sr_status enqueue_wb(sr_ctx* c, cudaStream_t s, const float* phi1, const float* 
                             [&] { return srk::launch_wb_update(a, s); });
   if (st != SR_OK || !phi_old) return st;
   return run_kernel(c, SR_KCLASS_REDUCE, s, "k_reduce", [&] {
-    return srk::launch_reduce(c->partials, c->n_tile, 2, c->red, s);
+    return srk::launch_reduce(c->partials, c->n_tile32, 2, c->red, s);
   });
 }
 
@@ -389,7 +557,7 @@ void sr_destroy(sr_ctx* c) {
   drop_graphs(c);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   void* bufs[] = {c->phi[0], c->phi[1], c->w1[0], c->w1[1], c->w2[0], c->w2[1], c->b1, c->b2,
-                  c->g, c->tmp1, c->tmp2, c->stage, c->mask_dev, c->X, c->tw_row, c->tw_col,
+                  c->g, c->tmp1, c->tmp2, c->stage, c->G, c->mask_dev, c->X, c->tw_row, c->tw_col,
                   c->tw_n, c->aM, c->aN, c->partials, c->red};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -470,10 +638,12 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   c->row_NT = NT;
   c->row_CW = W < 128 ? W : 128;
   c->n_tile = srk::tile_blocks(c->geo);
+  c->n_tile32 = srk::tile32_blocks(c->geo);
 
   const size_t P = (size_t)H * W;
   float** planes[] = {&c->phi[0], &c->phi[1], &c->w1[0], &c->w1[1], &c->w2[0], &c->w2[1],
-                      &c->b1,     &c->b2,     &c->g,     &c->tmp1,  &c->tmp2,  &c->stage};
+                      &c->b1,     &c->b2,     &c->g,     &c->tmp1,  &c->tmp2,  &c->stage,
+                      &c->G};
   for (float** pl : planes) CREATE_CUDA(cudaMalloc((void**)pl, P * sizeof(float)));
   CREATE_CUDA(cudaMalloc((void**)&c->mask_dev, P));
   CREATE_CUDA(cudaMalloc((void**)&c->X, (size_t)H * L * sizeof(float2)));
@@ -501,6 +671,8 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   if (upload(c, &c->aN, aN) != SR_OK) return bail(SR_ECUDA);
   make_fft(c->fft_row, L, c->tw_row);
   make_fft(c->fft_col, H, c->tw_col);
+  c->fft2 = srk::fft2_supported(c->geo);
+  if (c->fft2 && autotune(c) != SR_OK) return bail(SR_ECUDA);
 
   // g = 1 until sr_edge_function is called
   std::vector<float> ones(P, 1.f);
@@ -694,8 +866,9 @@ sr_status sr_phi_step(sr_ctx* c, const float* psi_in, const float* w1, const flo
   if (!c) return SR_EINVAL;
   if (!psi_in || !w1 || !w2 || !b1 || !b2 || !psi_out)
     return fail(c, SR_EINVAL, "NULL pointer");
-  if (!aligned16(psi_in) || !aligned16(psi_out))
-    return fail(c, SR_EINVAL, "psi buffers must be 16-byte aligned");
+  for (const void* ptr : {(const void*)psi_in, (const void*)w1, (const void*)w2, (const void*)b1,
+                          (const void*)b2, (const void*)psi_out})
+    if (!aligned16(ptr)) return fail(c, SR_EINVAL, "buffers must be 16-byte aligned");
   return enqueue_phi_step(c, c->stream, psi_in, w1, w2, b1, b2, psi_out, nullptr);
 }
 
@@ -714,8 +887,33 @@ sr_status sr_w_b_update(sr_ctx* c, const float* phi1, const float* w1_in, const 
     return fail(c, SR_EINVAL, "NULL pointer");
   if (w1_out == w1_in || w2_out == w2_in || w1_out == w2_in || w2_out == w1_in)
     return fail(c, SR_EINVAL, "w_out must not alias w_in");
+  for (const void* ptr : {(const void*)phi1, (const void*)w1_in, (const void*)w2_in,
+                          (const void*)b1_in, (const void*)b2_in, (const void*)w1_out,
+                          (const void*)w2_out, (const void*)b1_out, (const void*)b2_out})
+    if (!aligned16(ptr)) return fail(c, SR_EINVAL, "buffers must be 16-byte aligned");
   return enqueue_wb(c, c->stream, phi1, w1_in, w2_in, b1_in, b2_in, w1_out, w2_out, b1_out,
                     b2_out, nullptr);
+}
+
+sr_status sr_get_schedule(sr_ctx* c, sr_schedule* out) {
+  if (!c || !out) return SR_EINVAL;
+  if (c->fft2) {
+    *out = c->sched;
+  } else {
+    *out = sr_schedule{16, 0, 0, 0.f};
+  }
+  return SR_OK;
+}
+
+sr_status sr_set_schedule(sr_ctx* c, const sr_schedule* sc) {
+  if (!c || !sc) return SR_EINVAL;
+  if (!c->fft2) return fail(c, SR_EUNSUPPORTED, "this size uses fixed FFT kernels");
+  if (!sched_valid(c, *sc)) return fail(c, SR_EINVAL, "invalid FFT schedule for this size");
+  SR_CUDA(c, sched_configure(c, *sc));
+  c->sched = *sc;
+  c->sched.tuned_us = 0.f;
+  drop_graphs(c);
+  return SR_OK;
 }
 
 long long sr_kernel_launches(const sr_ctx* c, int reset) {

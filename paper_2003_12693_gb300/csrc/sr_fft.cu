@@ -1,0 +1,415 @@
+// Register-resident Stockham FFT passes of the phi solve (Eqs. (31)-(33)).
+//
+// A thread owns 16 values x[m] = seq[u + (L/16) m] of one sequence.  In every
+// Stockham stage (radix R, Ns = product of the earlier radices) the inputs of
+// the thread's 16/R butterflies are exactly those 16 values, so the
+// butterflies run in registers; only the outputs move, through shared memory,
+// to the positions the next stage reads.  The outputs of the last stage land
+// back in the thread's own positions (natural order).  So the first stage
+// reads global memory directly, the last stage writes it directly, and a
+// length-L transform needs ceil(log16 L) - 1 shared-memory exchanges.
+//
+//   k_rowfft<LOGL>    rows: z[n] = G[2n] + i G[2n+1] -> FFT_L -> even/odd split
+//                     -> packed half spectrum X[0] = X_0 + i X_{N/2}, X[k]
+//   k_colsolve2<..>   columns: FFT_M, multiply by 1/(M N lambda), inverse FFT_M
+//   k_rowifft<LOGL>   rows: rebuild the length-L sequence, inverse FFT_L,
+//                     interleave, add psi (increment form) or store
+#include "sr_internal.h"
+
+namespace srk {
+namespace fft2 {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+template <bool INV>
+__device__ __forceinline__ float2 mul_w(float2 a, float cr, float ci) {
+  const float s = INV ? ci : -ci;
+  return make_float2(a.x * cr - a.y * s, a.x * s + a.y * cr);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2* x) {
+  const float2 a = x[0], b = x[1];
+  x[0] = cadd(a, b);
+  x[1] = csub(a, b);
+}
+template <bool INV>
+__device__ __forceinline__ void dft4(float2* x) {
+  const float2 a0 = cadd(x[0], x[2]), a1 = csub(x[0], x[2]);
+  const float2 a2 = cadd(x[1], x[3]), a3 = mul_mi<INV>(csub(x[1], x[3]));
+  x[0] = cadd(a0, a2);
+  x[2] = csub(a0, a2);
+  x[1] = cadd(a1, a3);
+  x[3] = csub(a1, a3);
+}
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* x) {
+  float2 e[4] = {x[0], x[2], x[4], x[6]};
+  float2 o[4] = {x[1], x[3], x[5], x[7]};
+  dft4<INV>(e);
+  dft4<INV>(o);
+  const float c = 0.70710678118654752440f;
+  o[1] = mul_w<INV>(o[1], c, c);
+  o[2] = mul_mi<INV>(o[2]);
+  o[3] = mul_w<INV>(o[3], -c, c);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    x[m] = cadd(e[m], o[m]);
+    x[m + 4] = csub(e[m], o[m]);
+  }
+}
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* x) {
+  float2 e[8], o[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    e[m] = x[2 * m];
+    o[m] = x[2 * m + 1];
+  }
+  dft8<INV>(e);
+  dft8<INV>(o);
+  const float C1 = 0.92387953251128675613f, S1 = 0.38268343236508977173f;
+  const float c = 0.70710678118654752440f;
+  o[1] = mul_w<INV>(o[1], C1, S1);
+  o[2] = mul_w<INV>(o[2], c, c);
+  o[3] = mul_w<INV>(o[3], S1, C1);
+  o[4] = mul_mi<INV>(o[4]);
+  o[5] = mul_w<INV>(o[5], -S1, C1);
+  o[6] = mul_w<INV>(o[6], -c, c);
+  o[7] = mul_w<INV>(o[7], -C1, S1);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    x[m] = cadd(e[m], o[m]);
+    x[m + 8] = csub(e[m], o[m]);
+  }
+}
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* x) {
+  if constexpr (R == 16) dft16<INV>(x);
+  else if constexpr (R == 8) dft8<INV>(x);
+  else if constexpr (R == 4) dft4<INV>(x);
+  else dft2<INV>(x);
+}
+
+// padded shared-memory position of sequence index a (1 pad per 16 values)
+__device__ __forceinline__ int pad(int a) { return a + (a >> 4); }
+
+// Element a of the thread's sequence lives at smem[pad(a) * STRIDE] (STRIDE =
+// 1 for rows, CB for interleaved columns; `base` already includes the
+// sequence offset).  The thread holds E = 2^LOGE values x[m] = seq[u + (L/E) m];
+// stages use radix E, the last one radix 2^(LOGL mod LOGE) if that is not 1.
+template <int LOGL, int LOGE, int S, bool INV, int STRIDE>
+__device__ __forceinline__ void stages(float2 (&x)[1 << LOGE], float2* base, int u,
+                                       const float2* __restrict__ tw) {
+  constexpr int E = 1 << LOGE;
+  constexpr int NST = (LOGL + LOGE - 1) / LOGE;
+  if constexpr (S < NST) {
+    constexpr int LOGR = (S < LOGL / LOGE) ? LOGE : (LOGL % LOGE);
+    constexpr int R = 1 << LOGR, NB = E / R;
+    constexpr int LOGNS = LOGE * S;
+    constexpr int LOGTP = LOGL - LOGE;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = u + (b << LOGTP);
+      float2 v[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) v[t] = x[b + t * NB];
+      if constexpr (LOGNS > 0) {
+        const int k = j & ((1 << LOGNS) - 1);
+        constexpr int TSH = LOGL - LOGNS - LOGR;
+#pragma unroll
+        for (int t = 1; t < R; ++t) {
+          float2 w = __ldg(&tw[(k * t) << TSH]);
+          if (INV) w.y = -w.y;
+          v[t] = cmul(v[t], w);
+        }
+      }
+      dft<R, INV>(v);
+#pragma unroll
+      for (int t = 0; t < R; ++t) x[b + t * NB] = v[t];
+    }
+    if constexpr (S + 1 < NST) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int j = u + (b << LOGTP);
+        const int k = j & ((1 << LOGNS) - 1);
+        const int o = ((j >> LOGNS) << (LOGNS + LOGR)) + k;
+#pragma unroll
+        for (int t = 0; t < R; ++t) base[pad(o + (t << LOGNS)) * STRIDE] = x[b + t * NB];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < E; ++m) x[m] = base[pad(u + (m << LOGTP)) * STRIDE];
+      __syncthreads();
+      stages<LOGL, LOGE, S + 1, INV, STRIDE>(x, base, u, tw);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// rows, forward: packed half spectrum of the real rows of src
+// ---------------------------------------------------------------------------
+template <int LOGL, int LOGE>
+__global__ void __launch_bounds__(512) k_rowfft(const RowFwdArgs a) {
+  constexpr int E = 1 << LOGE;
+  constexpr int L = 1 << LOGL, LOGTP = LOGL - LOGE, TP = 1 << LOGTP;
+  constexpr int S = L + L / 16;
+  extern __shared__ __align__(16) float2 smem2[];
+  const int tid = threadIdx.x;
+  const int t = tid >> LOGTP, u = tid & (TP - 1);
+  const int i = blockIdx.x * a.T + t;
+  const bool live = i < a.geo.M;
+  float2* base = smem2 + t * S;
+  float2 x[E];
+  const float2* row = reinterpret_cast<const float2*>(a.src + (size_t)(live ? i : 0) * a.geo.N);
+#pragma unroll
+  for (int m = 0; m < E; ++m) x[m] = live ? __ldg(row + u + (m << LOGTP)) : make_float2(0.f, 0.f);
+  stages<LOGL, LOGE, 0, false, 1>(x, base, u, a.fft.tw);
+  // even/odd split needs Z_{L-k}: exchange through shared memory
+#pragma unroll
+  for (int m = 0; m < E; ++m) base[pad(u + (m << LOGTP))] = x[m];
+  __syncthreads();
+  if (!live) return;
+  float2* Xrow = a.X + (size_t)i * L;
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = u + (m << LOGTP);
+    const float2 Zk = x[m];
+    if (k == 0) {
+      Xrow[0] = make_float2(Zk.x + Zk.y, Zk.x - Zk.y);
+      continue;
+    }
+    const float2 Zm = base[pad(L - k)];
+    const float2 E = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
+    const float2 D = make_float2(0.5f * (Zk.x - Zm.x), 0.5f * (Zk.y + Zm.y));
+    const float2 O = make_float2(D.y, -D.x);
+    Xrow[k] = cadd(E, cmul(__ldg(&a.twN[k]), O));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// rows, inverse: out = psi_in + x (ADD) or out = x (STORE)
+// ---------------------------------------------------------------------------
+template <int LOGL, int LOGE, bool ADD>
+__global__ void __launch_bounds__(512) k_rowifft(const RowInvArgs a) {
+  constexpr int E = 1 << LOGE;
+  constexpr int L = 1 << LOGL, LOGTP = LOGL - LOGE, TP = 1 << LOGTP;
+  constexpr int S = L + L / 16;
+  extern __shared__ __align__(16) float2 smem2[];
+  const int tid = threadIdx.x;
+  const int t = tid >> LOGTP, u = tid & (TP - 1);
+  const int i = blockIdx.x * a.T + t;
+  const bool live = i < a.geo.M;
+  const int ii = live ? i : 0;
+  float2* base = smem2 + t * S;
+  float2 p[E];
+  if (ADD) {
+    const float2* prow = reinterpret_cast<const float2*>(a.psi_in + (size_t)ii * a.geo.N);
+#pragma unroll
+    for (int m = 0; m < E; ++m) p[m] = __ldg(prow + u + (m << LOGTP));
+  }
+  const float2* Xrow = a.X + (size_t)ii * L;
+  float2 xk[E], xm[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = u + (m << LOGTP);
+    xk[m] = __ldg(Xrow + k);
+    xm[m] = __ldg(Xrow + ((L - k) & (L - 1)));
+  }
+  float2 x[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = u + (m << LOGTP);
+    if (k == 0) {
+      x[m] = make_float2(xk[m].x + xk[m].y, xk[m].x - xk[m].y);  // (X_0 + X_{N/2}, X_0 - X_{N/2})
+      continue;
+    }
+    // Xe = X_k + conj X_{L-k},  Xo = (X_k - conj X_{L-k}) exp(+2 pi i k / N)
+    const float2 Xe = make_float2(xk[m].x + xm[m].x, xk[m].y - xm[m].y);
+    const float2 D = make_float2(xk[m].x - xm[m].x, xk[m].y + xm[m].y);
+    const float2 Xo = cmul(D, cconj(__ldg(&a.twN[k])));
+    x[m] = make_float2(Xe.x - Xo.y, Xe.y + Xo.x);
+  }
+  stages<LOGL, LOGE, 0, true, 1>(x, base, u, a.fft.tw);
+  if (!live) return;
+  float2* orow = reinterpret_cast<float2*>(a.out + (size_t)i * a.geo.N);
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    float2 r = x[m];
+    if (ADD) r = make_float2(p[m].x + r.x, p[m].y + r.y);
+    orow[u + (m << LOGTP)] = r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// columns: CB adjacent columns of X per CTA, thread (u, c) with c fastest
+// ---------------------------------------------------------------------------
+template <int LOGM, int CB, int LOGE>
+constexpr int col_threads() { return CB * (1 << LOGM) / (1 << LOGE); }
+template <int LOGM, int CB, int LOGE>
+constexpr int col_min_blocks() {
+  return (LOGE == 3 && col_threads<LOGM, CB, LOGE>() <= 512) ? 3 : 1;
+}
+
+template <int LOGM, int CB, int LOGE>
+__global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), col_min_blocks<LOGM, CB, LOGE>())
+    k_colsolve2(const ColArgs a) {
+  constexpr int E = 1 << LOGE;
+  constexpr int M = 1 << LOGM, LOGTP = LOGM - LOGE;
+  extern __shared__ __align__(16) float2 smem2[];
+  const int tid = threadIdx.x;
+  const int c = tid % CB, u = tid / CB;
+  const int L = a.geo.L;
+  const int c0 = blockIdx.x * CB;
+  const int k = c0 + c;
+  float2* base = smem2 + c;
+  float2 x[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) x[m] = a.X[(size_t)(u + (m << LOGTP)) * L + k];
+  stages<LOGM, LOGE, 0, false, CB>(x, base, u, a.fft.tw);
+  const float inv_mn = 1.f / ((float)M * (float)a.geo.N);
+  if (c0 == 0) {
+    // column 0 packs the DC and Nyquist columns of the row transforms: split
+    // them with the conjugate pair (l, M - l) so each gets its own symbol
+    if (c == 0) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) base[pad(u + (m << LOGTP)) * CB] = x[m];
+    }
+    __syncthreads();
+    if (c == 0) {
+      const float aNy = a.aN[L];
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int l = u + (m << LOGTP);
+        const float2 Cl = x[m], Cm = base[pad((M - l) & (M - 1)) * CB];
+        const float sA = inv_mn / (1.f + a.aM[l] + a.aN[0]);
+        const float sB = inv_mn / (1.f + a.aM[l] + aNy);
+        const float2 A = make_float2(0.5f * (Cl.x + Cm.x) * sA, 0.5f * (Cl.y - Cm.y) * sA);
+        const float2 D = make_float2(0.5f * (Cl.x - Cm.x), 0.5f * (Cl.y + Cm.y));
+        const float2 B = make_float2(D.y * sB, -D.x * sB);
+        x[m] = make_float2(A.x - B.y, A.y + B.x);
+      }
+    }
+    __syncthreads();
+  }
+  if (k != 0) {
+    const float ak = a.aN[k];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const float s = inv_mn / (1.f + a.aM[u + (m << LOGTP)] + ak);
+      x[m] = make_float2(x[m].x * s, x[m].y * s);
+    }
+  }
+  stages<LOGM, LOGE, 0, true, CB>(x, base, u, a.fft.tw);
+#pragma unroll
+  for (int m = 0; m < E; ++m) a.X[(size_t)(u + (m << LOGTP)) * L + k] = x[m];
+}
+
+}  // namespace fft2
+
+// ---------------------------------------------------------------------------
+// Host dispatch.  With set_attr the call only raises the kernel's dynamic
+// shared-memory limit (done once per context, outside any graph capture).
+// The schedule (values per thread E for rows and columns, columns per CTA)
+// is chosen by the context's autotuner.
+// ---------------------------------------------------------------------------
+using namespace fft2;
+
+template <class K>
+static cudaError_t set_smem(K kernel, size_t smem) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int LOGL, int LOGE>
+static cudaError_t rowfft_go(const RowFwdArgs& a, int nthreads, size_t smem, cudaStream_t s,
+                             bool set_attr) {
+  if (set_attr) return set_smem(k_rowfft<LOGL, LOGE>, smem);
+  k_rowfft<LOGL, LOGE><<<(a.geo.M + a.T - 1) / a.T, nthreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int LOGL, int LOGE>
+static cudaError_t rowifft_go(const RowInvArgs& a, bool add, int nthreads, size_t smem,
+                              cudaStream_t s, bool set_attr) {
+  if (set_attr) {
+    cudaError_t e = set_smem(k_rowifft<LOGL, LOGE, true>, smem);
+    return e != cudaSuccess ? e : set_smem(k_rowifft<LOGL, LOGE, false>, smem);
+  }
+  const int grid = (a.geo.M + a.T - 1) / a.T;
+  if (add) k_rowifft<LOGL, LOGE, true><<<grid, nthreads, smem, s>>>(a);
+  else k_rowifft<LOGL, LOGE, false><<<grid, nthreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int LOGM, int CB, int LOGE>
+static cudaError_t col_go(const ColArgs& a, cudaStream_t s, bool set_attr) {
+  constexpr int M = 1 << LOGM;
+  const size_t smem = (size_t)CB * (M + M / 16) * sizeof(float2);
+  if (set_attr) return set_smem(k_colsolve2<LOGM, CB, LOGE>, smem);
+  k_colsolve2<LOGM, CB, LOGE><<<a.geo.L / CB, CB * M / (1 << LOGE), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+bool fft2_supported(const Geo& geo) { return geo.L >= 16 && geo.L <= 2048 && geo.M >= 16 && geo.M <= 4096; }
+
+size_t rowfft2_smem(int T, int L) { return (size_t)T * (L + L / 16) * sizeof(float2); }
+
+#define SR_ROW_SWITCH(CALL)                         \
+  switch (a.geo.L) {                                \
+    case 16: CALL(4) case 32: CALL(5)               \
+    case 64: CALL(6) case 128: CALL(7)              \
+    case 256: CALL(8) case 512: CALL(9)             \
+    case 1024: CALL(10) case 2048: CALL(11)         \
+  }
+
+cudaError_t launch_rowfft2(const RowFwdArgs& a, int logE, int nthreads, cudaStream_t s,
+                           bool set_attr) {
+  const size_t sm = rowfft2_smem(a.T, a.geo.L);
+#define SR_CALL(l)                                                                   \
+  return logE == 3 ? rowfft_go<l, 3>(a, nthreads, sm, s, set_attr)                  \
+                   : rowfft_go<l, 4>(a, nthreads, sm, s, set_attr);
+  SR_ROW_SWITCH(SR_CALL)
+#undef SR_CALL
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rowifft2(const RowInvArgs& a, bool add, int logE, int nthreads, cudaStream_t s,
+                            bool set_attr) {
+  const size_t sm = rowfft2_smem(a.T, a.geo.L);
+#define SR_CALL(l)                                                                   \
+  return logE == 3 ? rowifft_go<l, 3>(a, add, nthreads, sm, s, set_attr)            \
+                   : rowifft_go<l, 4>(a, add, nthreads, sm, s, set_attr);
+  SR_ROW_SWITCH(SR_CALL)
+#undef SR_CALL
+  return cudaErrorInvalidValue;
+}
+
+// column schedules: 0 = (CB 4, E 16), 1 = (CB 2, E 8), 2 = (CB 4, E 8)
+cudaError_t launch_colsolve2(const ColArgs& a, int sched, cudaStream_t s, bool set_attr) {
+#define SR_COL(lm)                                                   \
+  case (1 << lm):                                                    \
+    if (sched == 1) return col_go<lm, 2, 3>(a, s, set_attr);         \
+    if (sched == 2) return col_go<lm, 4, 3>(a, s, set_attr);         \
+    return (lm == 12) ? col_go<lm, 2, 4>(a, s, set_attr) : col_go<lm, 4, 4>(a, s, set_attr);
+  switch (a.geo.M) {
+    SR_COL(4) SR_COL(5) SR_COL(6) SR_COL(7) SR_COL(8) SR_COL(9) SR_COL(10) SR_COL(11) SR_COL(12)
+  }
+#undef SR_COL
+  return cudaErrorInvalidValue;
+}
+
+int colsolve2_threads(int M, int sched) {
+  if (sched == 1) return 2 * M / 8;
+  if (sched == 2) return 4 * M / 8;
+  return M == 4096 ? 2 * M / 16 : 4 * M / 16;
+}
+
+}  // namespace srk

@@ -78,6 +78,19 @@ struct RowInvArgs {
   int T;
 };
 
+// Right-hand side of one inner step on 2-D tiles (window sum fused in).
+struct PrepArgs {
+  Geo geo;
+  Model mod;
+  const float* psi;
+  const float* g;
+  const float* w1;
+  const float* w2;
+  const float* b1;
+  const float* b2;
+  float* G;                // increment right-hand side, H x W
+};
+
 // w and b update with the repulsion window sum fused in.
 struct WBArgs {
   Geo geo;
@@ -93,7 +106,7 @@ struct WBArgs {
   float* b1o;              // b^{k+1} (may alias b1)
   float* b2o;
   const float* phi_old;    // phi^k for the stopping test, or nullptr
-  double* partials;        // 2 doubles per CTA when phi_old != nullptr
+  double* partials;        // 2 doubles per 32 x 32 tile when phi_old != nullptr
 };
 
 struct RepArgs {
@@ -136,6 +149,8 @@ cudaError_t launch_rowfwd(const RowFwdArgs& a, int mode, int nthreads, cudaStrea
 cudaError_t launch_colsolve(const ColArgs& a, cudaStream_t s);
 cudaError_t launch_rowinv(const RowInvArgs& a, int mode, int nthreads, cudaStream_t s);
 cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s);
+cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
+int tile32_blocks(const Geo& geo);  // CTAs of the 32 x 32 tile kernels
 cudaError_t launch_repulsion(const RepArgs& a, cudaStream_t s);
 cudaError_t launch_energy(const EnergyArgs& a, cudaStream_t s);
 cudaError_t launch_reduce(const double* partials, int nblocks, int ncomp, double* out,
@@ -147,6 +162,20 @@ cudaError_t launch_mask(const float* phi, unsigned char* mask, int ld, Geo geo,
 cudaError_t launch_edge(const EdgeArgs& a, const float* f, int ld, float* tmp1, float* tmp2,
                         float* g, cudaStream_t s);
 cudaError_t configure_kernels();   // raise dynamic shared-memory limits once
+
+// Register-resident FFT passes (sr_fft.cu) for L = W/2 in [16, 2048] and
+// H in [16, 4096].  Rows: 2^logE values per thread (logE 3 or 4), T rows per
+// CTA, T * L / 2^logE threads.  Columns: schedule 0 (4 columns per CTA, 16
+// values per thread; 2 columns at H = 4096), 1 (2 columns, 8 values),
+// 2 (4 columns, 8 values).
+bool fft2_supported(const Geo& geo);
+size_t rowfft2_smem(int T, int L);
+cudaError_t launch_rowfft2(const RowFwdArgs& a, int logE, int nthreads, cudaStream_t s,
+                           bool set_attr);
+cudaError_t launch_rowifft2(const RowInvArgs& a, bool add, int logE, int nthreads, cudaStream_t s,
+                            bool set_attr);
+cudaError_t launch_colsolve2(const ColArgs& a, int sched, cudaStream_t s, bool set_attr);
+int colsolve2_threads(int M, int sched);
 int tile_blocks(const Geo& geo);   // CTAs of the 2-D tile kernels
 
 }  // namespace srk

@@ -1,9 +1,12 @@
 // sm_103a kernels of the Split Bregman self-repelling snake.
 //
 // One outer iteration of Alg. 1 is, per inner step s (Eq. (37)):
-//   k_rowfwd   repulsion window sum (Sec. 4), right-hand side, row R2C FFT
+//   k_prep     repulsion window sum (Sec. 4) and the right-hand side, 2-D tiles
+//   k_rowfwd   row R2C FFT of the right-hand side
 //   k_colsolve column FFT, divide by the symbol of Eq. (32), inverse column FFT
 //   k_rowinv   row C2R FFT and phi update
+// (k_rowfwd can also build the right-hand side itself from row blocks; the
+// allocation-free single step uses that form.)
 // and after the inner loop:
 //   k_wb_update repulsion window sum of Eq. (41), soft threshold (42),
 //               projection (40), Bregman update (23)
@@ -18,6 +21,9 @@
 #include <math.h>
 
 #include "sr_internal.h"
+
+// every supported repulsion window half width R
+#define SR_FOR_R(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
 
 namespace srk {
 
@@ -534,56 +540,279 @@ __device__ __forceinline__ void block_sum_store(double (&val)[NC], double* out) 
 }
 
 // ---------------------------------------------------------------------------
-// w and b update (Eqs. (41), (42), (40), (23)) with the window sum fused in.
-// Soft threshold then projection: w = B/|B| if |B| > t, else 0.
+// 32 x 32 output tiles, block (8, 32): a thread owns four consecutive pixels
+// of one row, so every global access is a float4.  The tile is staged with a
+// halo of HY = max(R, 1) rows and HX >= max(R, 1) columns, HX a multiple of 4
+// so that staged float4s stay aligned; the kernels are templated on R so the
+// staging and window loops unroll.
+//
+// u = h(psi) w vanishes outside the narrow band |psi| < l + eps (Eq. (11)), so
+// a tile whose halo holds no band pixel has v = 0 exactly: psi is staged
+// first, the block tests for band pixels, and w is staged and summed over the
+// window only when the test succeeds.  Neighbours of the periodic stencils
+// that fall outside the image are read from global memory with the wrap.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTileX* kTileY) k_wb_update(const WBArgs a) {
-  __shared__ TileSmem sm;
-  const int i0 = blockIdx.y * kTileY, j0 = blockIdx.x * kTileX;
+constexpr int kT = 32;
+constexpr int kTBX = 8, kTBY = 32;      // block shape
+constexpr int kTN = kTBX * kTBY;        // threads per tile CTA
+
+template <int R>
+struct Tile {
+  static constexpr int HY = R > 1 ? R : 1;
+  static constexpr int HX = R > 4 ? 8 : 4;
+  static constexpr int SH = kT + 2 * HY;   // staged rows
+  static constexpr int SW = kT + 2 * HX;   // staged columns
+  static constexpr int SW4 = SW / 4;
+  static constexpr int N4 = SH * SW4;      // staged float4 per plane
+  static constexpr int IT = (N4 + kTN - 1) / kTN;
+  static constexpr int NP = SH * SW;       // floats per staged plane
+  static constexpr int FLOATS = 5 * NP + 2 * kT * SW;
+};
+
+__host__ __device__ constexpr int tile32_floats(int R) {
+  return 5 * (kT + 2 * (R > 1 ? R : 1)) * (kT + 2 * (R > 4 ? 8 : 4)) +
+         2 * kT * (kT + 2 * (R > 4 ? 8 : 4));
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ bool in_band(float x, const Model& m) { return fabsf(x) < m.band_l + m.eps; }
+
+// Stage one plane (zero outside the image); returns whether a staged value
+// lies in the narrow band when BAND is set.
+template <int R, bool BAND>
+__device__ __forceinline__ int stage4(float* dst, const float* __restrict__ src, const Geo& geo,
+                                      int i0, int j0, const Model& m) {
+  using TL = Tile<R>;
+  const int tid = threadIdx.y * kTBX + threadIdx.x;
+  float4 val[TL::IT];
+#pragma unroll
+  for (int k = 0; k < TL::IT; ++k) {
+    const int idx = tid + k * kTN;
+    const int r = idx / TL::SW4, c4 = idx - r * TL::SW4;
+    const int i = i0 - TL::HY + r, j = j0 - TL::HX + 4 * c4;
+    val[k] = (idx < TL::N4 && i >= 0 && i < geo.M && j >= 0 && j < geo.N)
+                 ? ld4(src + (size_t)i * geo.N + j)
+                 : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  int any = 0;
+#pragma unroll
+  for (int k = 0; k < TL::IT; ++k) {
+    const int idx = tid + k * kTN;
+    if (idx < TL::N4) {
+      st4(dst + 4 * idx, val[k]);
+      if (BAND)
+        any |= in_band(val[k].x, m) | in_band(val[k].y, m) | in_band(val[k].z, m) |
+               in_band(val[k].w, m);
+    }
+  }
+  return any;
+}
+
+// With psi staged: stage w, form u = h(psi) w and return the window sums of
+// the thread's four pixels (zero for tiles without band pixels).
+template <int R>
+__device__ __forceinline__ void tile_window(float* sm, const Geo& geo, const Model& m,
+                                            const float* __restrict__ w1,
+                                            const float* __restrict__ w2, int i0, int j0,
+                                            bool band, float (&v1)[4], float (&v2)[4]) {
+  using TL = Tile<R>;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v1[q] = v2[q] = 0.f;
+  if (!band) return;  // uniform across the block
+  float* t_psi = sm;
+  float* t_u1 = sm + TL::NP;
+  float* t_u2 = sm + 2 * TL::NP;
+  float* t_w1 = sm + 3 * TL::NP;
+  float* t_w2 = sm + 4 * TL::NP;
+  float* t_V1 = sm + 5 * TL::NP;
+  float* t_V2 = t_V1 + kT * TL::SW;
+  stage4<R, false>(t_w1, w1, geo, i0, j0, m);
+  stage4<R, false>(t_w2, w2, geo, i0, j0, m);
+  __syncthreads();
+  const int tid = threadIdx.y * kTBX + threadIdx.x;
+  for (int idx = tid; idx < TL::NP; idx += kTN) {
+    const float x = t_psi[idx];
+    const float hh = in_band(x, m) ? band_h(x, m) : 0.f;
+    t_u1[idx] = hh * t_w1[idx];  // w = 0 outside the image
+    t_u2[idx] = hh * t_w2[idx];
+  }
+  __syncthreads();
+  // sum down the columns: a task is 4 rows x 4 columns, sliding over 4 + 2R rows
+  constexpr int NTASK = (kT / 4) * TL::SW4;
+  if (tid < NTASK) {
+    const int r0 = (tid / TL::SW4) * 4, c = 4 * (tid % TL::SW4);
+    float4 a1[4], a2[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a1[q] = a2[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < 4 + 2 * R; ++t) {
+      const int row = r0 + TL::HY - R + t;
+      const float4 x1 = *reinterpret_cast<const float4*>(t_u1 + row * TL::SW + c);
+      const float4 x2 = *reinterpret_cast<const float4*>(t_u2 + row * TL::SW + c);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int p = t - q;  // output row r0 + q takes input rows r0 + q - R .. r0 + q + R
+        if (p >= 0 && p <= 2 * R) {
+          const float kw = m.kw[p];
+          a1[q].x = fmaf(kw, x1.x, a1[q].x);
+          a1[q].y = fmaf(kw, x1.y, a1[q].y);
+          a1[q].z = fmaf(kw, x1.z, a1[q].z);
+          a1[q].w = fmaf(kw, x1.w, a1[q].w);
+          a2[q].x = fmaf(kw, x2.x, a2[q].x);
+          a2[q].y = fmaf(kw, x2.y, a2[q].y);
+          a2[q].z = fmaf(kw, x2.z, a2[q].z);
+          a2[q].w = fmaf(kw, x2.w, a2[q].w);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      st4(t_V1 + (r0 + q) * TL::SW + c, a1[q]);
+      st4(t_V2 + (r0 + q) * TL::SW + c, a2[q]);
+    }
+  }
+  __syncthreads();
+  // across the row: outputs c .. c+3 take inputs c - R .. c + 3 + R
+  const int r = threadIdx.y, c = 4 * threadIdx.x + TL::HX;
+#pragma unroll
+  for (int t = 0; t < 4 + 2 * R; ++t) {
+    const float x1 = t_V1[r * TL::SW + c - R + t];
+    const float x2 = t_V2[r * TL::SW + c - R + t];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int p = t - q;
+      if (p >= 0 && p <= 2 * R) {
+        v1[q] = fmaf(m.kw[p], x1, v1[q]);
+        v2[q] = fmaf(m.kw[p], x2, v2[q]);
+      }
+    }
+  }
+}
+
+size_t tile32_smem(int R) { return (size_t)tile32_floats(R) * sizeof(float); }
+
+// Increment right-hand side of one inner step, Eq. (37) in the form
+// G = tau [ -gamma g |w| delta'(psi) + alpha g delta(psi) + 2 beta h'(psi) (w . v)
+//           + mu (div(b - w) + Lap psi) ], so that phi^{k+1,s+1} = psi + L^{-1} G.
+template <int R>
+__global__ void __launch_bounds__(kTN, 4) k_prep(const PrepArgs a) {
+  using TL = Tile<R>;
+  extern __shared__ __align__(16) float smem_f[];
+  const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
   const int M = a.geo.M, N = a.geo.N;
   const Model& m = a.mod;
-  float v1, v2;
-  tile_window_sum(sm, a.geo, m, i0, j0,
-                  [&](int i, int j, float& u1, float& u2) {
-                    const size_t o = (size_t)i * N + j;
-                    const float h = band_h(a.phi1[o], m);
-                    if (h != 0.f) {
-                      u1 = h * a.w1[o];
-                      u2 = h * a.w2[o];
-                    }
-                  },
-                  v1, v2);
-  const int i = i0 + threadIdx.y, j = j0 + threadIdx.x;
+  const int any = stage4<R, true>(smem_f, a.psi, a.geo, i0, j0, m);
+  const bool band = __syncthreads_or(any) != 0;
+  float v1[4], v2[4];
+  tile_window<R>(smem_f, a.geo, m, a.w1, a.w2, i0, j0, band, v1, v2);
+  const int i = i0 + threadIdx.y, j = j0 + 4 * threadIdx.x;
+  if (i >= M || j >= N) return;
+  const size_t o = (size_t)i * N + j;
+  const size_t ou = (size_t)(i > 0 ? i - 1 : M - 1) * N + j;
+  const size_t ol = (size_t)i * N + (j > 0 ? j - 1 : N - 1);
+  const float4 W1 = ld4(a.w1 + o), W2 = ld4(a.w2 + o), B1 = ld4(a.b1 + o), B2 = ld4(a.b2 + o);
+  const float4 W1u = ld4(a.w1 + ou), B1u = ld4(a.b1 + ou);
+  const float w2l = __ldg(a.w2 + ol), b2l = __ldg(a.b2 + ol);
+  const float4 G4 = ld4(a.g + o);
+  const float* t_psi = smem_f;
+  const int q = (threadIdx.y + TL::HY) * TL::SW + 4 * threadIdx.x + TL::HX;
+  const float4 X = *reinterpret_cast<const float4*>(t_psi + q);
+  const float4 UP = i > 0 ? *reinterpret_cast<const float4*>(t_psi + q - TL::SW) : ld4(a.psi + ou);
+  const float4 DN = i < M - 1 ? *reinterpret_cast<const float4*>(t_psi + q + TL::SW)
+                              : ld4(a.psi + j);
+  const float LF = j > 0 ? t_psi[q - 1] : __ldg(a.psi + ol);
+  const float RT = j + 4 < N ? t_psi[q + 4] : __ldg(a.psi + (size_t)i * N);
+  const float x[4] = {X.x, X.y, X.z, X.w};
+  const float up[4] = {UP.x, UP.y, UP.z, UP.w}, dn[4] = {DN.x, DN.y, DN.z, DN.w};
+  const float lf[4] = {LF, X.x, X.y, X.z}, rt[4] = {X.y, X.z, X.w, RT};
+  const float w1[4] = {W1.x, W1.y, W1.z, W1.w}, w2[4] = {W2.x, W2.y, W2.z, W2.w};
+  const float b1[4] = {B1.x, B1.y, B1.z, B1.w}, b2[4] = {B2.x, B2.y, B2.z, B2.w};
+  const float w1u[4] = {W1u.x, W1u.y, W1u.z, W1u.w}, b1u[4] = {B1u.x, B1u.y, B1u.z, B1u.w};
+  const float w2l4[4] = {w2l, W2.x, W2.y, W2.z}, b2l4[4] = {b2l, B2.x, B2.y, B2.z};
+  const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
+  float out[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const float lap = (up[t] + dn[t]) + (lf[t] + rt[t]) - 4.f * x[t];
+    const float dv = ((b1[t] - w1[t]) - (b1u[t] - w1u[t])) + ((b2[t] - w2[t]) - (b2l4[t] - w2l4[t]));
+    float force = m.mu * (dv + lap);
+    if (in_band(x[t], m)) {
+      const float wn = sqrtf(w1[t] * w1[t] + w2[t] * w2[t]);
+      force += -m.gamma * gg[t] * wn * dpeps(x[t], m.eps) + m.alpha * gg[t] * deps(x[t], m.eps) +
+               2.f * m.beta * band_hp(x[t], m) * (w1[t] * v1[t] + w2[t] * v2[t]);
+    }
+    out[t] = m.tau * force;
+  }
+  st4(a.G + o, make_float4(out[0], out[1], out[2], out[3]));
+}
+
+// w and b update (Eqs. (41), (42), (40), (23)) with the window sum fused in.
+// Soft threshold then projection: w = B/|B| if |B| > t, else 0.
+template <int R>
+__global__ void __launch_bounds__(kTN, 4) k_wb_update(const WBArgs a) {
+  using TL = Tile<R>;
+  extern __shared__ __align__(16) float smem_f[];
+  const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
+  const int M = a.geo.M, N = a.geo.N;
+  const Model& m = a.mod;
+  const int any = stage4<R, true>(smem_f, a.phi1, a.geo, i0, j0, m);
+  const bool band = __syncthreads_or(any) != 0;
+  float v1[4], v2[4];
+  tile_window<R>(smem_f, a.geo, m, a.w1, a.w2, i0, j0, band, v1, v2);
+  const int i = i0 + threadIdx.y, j = j0 + 4 * threadIdx.x;
   double part[2] = {0.0, 0.0};
   if (i < M && j < N) {
     const size_t o = (size_t)i * N + j;
-    const float x = a.phi1[o];
-    const float d1 = a.phi1[(size_t)(i == M - 1 ? 0 : i + 1) * N + j] - x;
-    const float d2 = a.phi1[(size_t)i * N + (j == N - 1 ? 0 : j + 1)] - x;
-    float B1 = d1 + a.b1[o];
-    float B2 = d2 + a.b2[o];
-    float thr = 0.f;
-    if (fabsf(x) < m.band_l + m.eps) {
-      const float h = band_h(x, m);
-      B1 = fmaf(m.beta2_mu * h, v1, B1);
-      B2 = fmaf(m.beta2_mu * h, v2, B2);
-      thr = m.gamma_mu * a.g[o] * deps(x, m.eps);
+    const float4 B1 = ld4(a.b1 + o), B2 = ld4(a.b2 + o), G4 = ld4(a.g + o);
+    const float* t_psi = smem_f;
+    const int q = (threadIdx.y + TL::HY) * TL::SW + 4 * threadIdx.x + TL::HX;
+    const float4 X = *reinterpret_cast<const float4*>(t_psi + q);
+    const float4 DN = i < M - 1 ? *reinterpret_cast<const float4*>(t_psi + q + TL::SW)
+                                : ld4(a.phi1 + j);
+    const float RT = j + 4 < N ? t_psi[q + 4] : __ldg(a.phi1 + (size_t)i * N);
+    const float x[4] = {X.x, X.y, X.z, X.w};
+    const float dn[4] = {DN.x, DN.y, DN.z, DN.w}, rt[4] = {X.y, X.z, X.w, RT};
+    const float b1[4] = {B1.x, B1.y, B1.z, B1.w}, b2[4] = {B2.x, B2.y, B2.z, B2.w};
+    const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
+    float wo1[4], wo2[4], bo1[4], bo2[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float d1 = dn[t] - x[t];
+      const float d2 = rt[t] - x[t];
+      float Bv1 = d1 + b1[t];
+      float Bv2 = d2 + b2[t];
+      float thr = 0.f;
+      if (in_band(x[t], m)) {
+        const float h = band_h(x[t], m);
+        Bv1 = fmaf(m.beta2_mu * h, v1[t], Bv1);
+        Bv2 = fmaf(m.beta2_mu * h, v2[t], Bv2);
+        thr = m.gamma_mu * gg[t] * deps(x[t], m.eps);
+      }
+      const float nB = sqrtf(Bv1 * Bv1 + Bv2 * Bv2);
+      float W1 = 0.f, W2 = 0.f;
+      if (nB > thr) {
+        W1 = Bv1 / nB;
+        W2 = Bv2 / nB;
+      }
+      wo1[t] = W1;
+      wo2[t] = W2;
+      bo1[t] = (b1[t] + d1) - W1;
+      bo2[t] = (b2[t] + d2) - W2;
     }
-    const float nB = sqrtf(B1 * B1 + B2 * B2);
-    float W1 = 0.f, W2 = 0.f;
-    if (nB > thr) {
-      W1 = B1 / nB;
-      W2 = B2 / nB;
-    }
-    a.w1o[o] = W1;
-    a.w2o[o] = W2;
-    a.b1o[o] = (a.b1[o] + d1) - W1;
-    a.b2o[o] = (a.b2[o] + d2) - W2;
+    st4(a.w1o + o, make_float4(wo1[0], wo1[1], wo1[2], wo1[3]));
+    st4(a.w2o + o, make_float4(wo2[0], wo2[1], wo2[2], wo2[3]));
+    st4(a.b1o + o, make_float4(bo1[0], bo1[1], bo1[2], bo1[3]));
+    st4(a.b2o + o, make_float4(bo2[0], bo2[1], bo2[2], bo2[3]));
     if (a.phi_old) {
-      const double po = a.phi_old[o];
-      const double df = (double)x - po;
-      part[0] = df * df;
-      part[1] = po * po;
+      const float4 P = ld4(a.phi_old + o);
+      const float po[4] = {P.x, P.y, P.z, P.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const double df = (double)x[t] - (double)po[t];
+        part[0] += df * df;
+        part[1] += (double)po[t] * (double)po[t];
+      }
     }
   }
   if (a.phi_old) block_sum_store<2>(part, a.partials + 2 * (blockIdx.y * gridDim.x + blockIdx.x));
@@ -753,19 +982,34 @@ int tile_blocks(const Geo& geo) {
   return ((geo.N + kTileX - 1) / kTileX) * ((geo.M + kTileY - 1) / kTileY);
 }
 
+// Allow each kernel the largest dynamic shared memory the device grants on
+// top of its own static shared memory.
+template <class K>
+static cudaError_t allow_big_smem(K kernel) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+
 cudaError_t configure_kernels() {
-  const int big = 227 * 1024;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_rowfwd<kRowRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_rowfwd<kRowLOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_colsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_rowinv<kInvADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_rowinv<kInvSTORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
-    return e;
+  if ((e = allow_big_smem(k_rowfwd<kRowRHS>))) return e;
+  if ((e = allow_big_smem(k_rowfwd<kRowLOAD>))) return e;
+  if ((e = allow_big_smem(k_colsolve))) return e;
+  if ((e = allow_big_smem(k_rowinv<kInvADD>))) return e;
+  if ((e = allow_big_smem(k_rowinv<kInvSTORE>))) return e;
+#define SR_CASE(r)                                                 \
+  if ((e = allow_big_smem(k_prep<r>)) != cudaSuccess) return e;    \
+  if ((e = allow_big_smem(k_wb_update<r>)) != cudaSuccess) return e;
+  SR_FOR_R(SR_CASE)
+#undef SR_CASE
   return cudaSuccess;
 }
 
@@ -796,8 +1040,33 @@ static dim3 tile_grid(const Geo& geo) {
   return dim3((geo.N + kTileX - 1) / kTileX, (geo.M + kTileY - 1) / kTileY);
 }
 
+static dim3 tile32_grid(const Geo& geo) { return dim3((geo.N + kT - 1) / kT, (geo.M + kT - 1) / kT); }
+
+int tile32_blocks(const Geo& geo) { return ((geo.N + kT - 1) / kT) * ((geo.M + kT - 1) / kT); }
+
 cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s) {
-  k_wb_update<<<tile_grid(a.geo), dim3(kTileX, kTileY), 0, s>>>(a);
+  const dim3 g = tile32_grid(a.geo), b(kTBX, kTBY);
+  const size_t sm = tile32_smem(a.mod.R);
+  switch (a.mod.R) {
+#define SR_CASE(r) \
+  case r: k_wb_update<r><<<g, b, sm, s>>>(a); break;
+    SR_FOR_R(SR_CASE)
+#undef SR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
+  const dim3 g = tile32_grid(a.geo), b(kTBX, kTBY);
+  const size_t sm = tile32_smem(a.mod.R);
+  switch (a.mod.R) {
+#define SR_CASE(r) \
+  case r: k_prep<r><<<g, b, sm, s>>>(a); break;
+    SR_FOR_R(SR_CASE)
+#undef SR_CASE
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

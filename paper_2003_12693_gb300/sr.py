@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "sr.h")
 
 SR_OK, SR_EINVAL, SR_ENOMEM, SR_ECUDA, SR_ENONFINITE = 0, 1, 2, 3, 4
 SR_ENOTCONVERGED, SR_ETIMEOUT, SR_EUNSUPPORTED = 5, 6, 7
-KCLASS = {"rhs_rowfft": 0, "colsolve": 1, "rowifft": 2, "wb_update": 3, "reduce": 4}
+KCLASS = {"rowfft": 0, "colsolve": 1, "rowifft": 2, "wb_update": 3, "reduce": 4, "prep": 5}
 
 
 class SRError(RuntimeError):
@@ -35,6 +35,11 @@ class sr_params(C.Structure):
                 ("band_l", C.c_float), ("d", C.c_float), ("win_radius", C.c_int),
                 ("inner_S", C.c_int), ("inner_tol", C.c_float), ("rho", C.c_float),
                 ("sigma", C.c_float), ("s_pow", C.c_int), ("check_every", C.c_int)]
+
+
+class sr_schedule(C.Structure):
+    _fields_ = [("row_values_per_thread", C.c_int), ("row_threads", C.c_int),
+                ("col_schedule", C.c_int), ("tuned_us", C.c_float)]
 
 
 _lib = None
@@ -98,6 +103,10 @@ def lib() -> C.CDLL:
     L.sr_profile_enable.argtypes = [_P, C.c_int]
     L.sr_kernel_times.restype = st
     L.sr_kernel_times.argtypes = [_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.sr_get_schedule.restype = st
+    L.sr_get_schedule.argtypes = [_P, C.POINTER(sr_schedule)]
+    L.sr_set_schedule.restype = st
+    L.sr_set_schedule.argtypes = [_P, C.POINTER(sr_schedule)]
     L.sr_phi_step_noalloc.restype = st
     L.sr_phi_step_noalloc.argtypes = [C.c_int, C.c_int, C.POINTER(sr_params)] + [_P] * 7 + [_P]
     L.sr_segment_host.restype = st
@@ -246,6 +255,15 @@ class Context:
         args = [self._dev(t) for t in (phi1, w1, w2, b1, b2, *outs)]
         _check(lib().sr_w_b_update(self.handle, *args), self)
         return tuple(outs)
+
+    def get_schedule(self) -> dict:
+        sc = sr_schedule()
+        _check(lib().sr_get_schedule(self.handle, C.byref(sc)), self)
+        return {f: getattr(sc, f) for f, _ in sr_schedule._fields_}
+
+    def set_schedule(self, row_values_per_thread: int, row_threads: int, col_schedule: int):
+        sc = sr_schedule(row_values_per_thread, row_threads, col_schedule, 0.0)
+        _check(lib().sr_set_schedule(self.handle, C.byref(sc)), self)
 
     def kernel_launches(self, reset: bool = False) -> int:
         return int(lib().sr_kernel_launches(self.handle, int(reset)))

@@ -52,6 +52,38 @@ def test_fft_solve_eigenfunctions():
     ctx.close()
 
 
+@pytest.mark.parametrize("shape", [(64, 32), (128, 256), (512, 512), (256, 2048), (4096, 64)])
+def test_every_fft_schedule_matches_oracle(shape):
+    """The autotuner may pick any schedule; each one must compute the same solve."""
+    H, W = shape
+    rng = np.random.default_rng(H + W)
+    rhs = f32(rng.normal(size=shape) * 3.0)
+    ref = oracle.solve(rhs, 0.1, 8.0)
+    phi, w1, w2, b1, b2, g = (f32(a) for a in synth.random_state(H, W, seed=W))
+    ref_step = oracle.phi_step(phi, g, w1, w2, b1, b2, oparams())
+    ctx = context(H, W)
+    ctx.set_g(dev(g))
+    tuned = ctx.get_schedule()
+    assert tuned["tuned_us"] > 0
+    tried = 0
+    for vpt in (16, 8):
+        for threads in (32, 64, 128, 256, 512):
+            for col in (0, 1, 2):
+                try:
+                    ctx.set_schedule(vpt, threads, col)
+                except sr.SRError as e:
+                    assert e.status == sr.SR_EINVAL
+                    continue
+                tried += 1
+                out = host(ctx.fft_solve(dev(rhs)))
+                assert np.abs(out - ref).max() <= 4e-7 * math.log2(H * W) * np.abs(rhs).max()
+                step = host(ctx.phi_step(*[dev(a) for a in (phi, w1, w2, b1, b2)]))
+                assert np.abs(step - ref_step).max() <= PHI_TOL
+    assert tried >= 6
+    report("schedules", shape=f"{H}x{W}", tried=tried, tuned=str(tuned))
+    ctx.close()
+
+
 # ---------------------------------------------------------------- step (a) alone
 @pytest.mark.parametrize("shape", SHAPES[:5])
 @pytest.mark.parametrize("R,d", [(0, 1.0), (3, 3.0), (4, 4.0), (8, 8.0), (2, 5.0)])
@@ -254,7 +286,7 @@ def test_graph_and_direct_launches_agree():
         ctx.iterate(5)
         outs.append([host(t) for t in ctx.get_state()])
         if prof:
-            ms, n = ctx.kernel_times("rhs_rowfft")
+            ms, n = ctx.kernel_times("prep")
             assert n == 15 and ms > 0
         ctx.close()
     for x, y in zip(*outs):
