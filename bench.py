@@ -84,7 +84,8 @@ class ClockSampler:
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+              "clocks.mem")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -120,7 +121,7 @@ class ClockSampler:
             self.thread.join(timeout=2)
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        sm, mx, reasons, mem = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -134,8 +135,14 @@ class ClockSampler:
             for name, val in zip(names, parts[5:9]):
                 if val.lower() == "active":
                     reasons.add(name)
+            if len(parts) > 9:
+                try:
+                    mem.append(float(parts[9]))
+                except ValueError:
+                    pass
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "mem_mhz": statistics.median(mem) if mem else None}
 
 
 # ----------------------------------------------------------------------------
@@ -257,7 +264,15 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
     P = wl.H * wl.W
     schedule = ctx.get_schedule()
 
-    # warm-up (also builds the CUDA graphs)
+    # warm-up: the W counted steps (which also build the CUDA graphs), preceded by
+    # back-to-back steps for at least --prewarm-s seconds so that the GPU leaves
+    # its idle clock state before anything is timed
+    t_pre = time.perf_counter()
+    prewarm_steps = 0
+    while time.perf_counter() - t_pre < args.prewarm_s:
+        ctx.iterate(20)
+        torch.cuda.synchronize()
+        prewarm_steps += 20
     ctx.iterate(args.warmup)
     torch.cuda.synchronize()
 
@@ -366,8 +381,10 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
+        "prewarm": {"seconds": args.prewarm_s, "steps": prewarm_steps},
         "clocks": clk.summary(),
         "wall_s_timed_region": wall,
+        "step_ms_first_last": [[round(x, 4) for x in step_ms[:5]], [round(x, 4) for x in step_ms[-5:]]],
     }
     print(json.dumps(line), flush=True)
 
@@ -381,6 +398,8 @@ def main():
     ap.add_argument("--workload", default="ellipses_2048")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--prewarm-s", type=float, default=1.0,
+                    help="untimed back-to-back steps before the warm-up steps (clock ramp)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -40,7 +40,7 @@ typedef enum sr_status {
   SR_ECUDA = 3,           /* a CUDA runtime call failed (see sr_last_error) */
   SR_ENONFINITE = 4,      /* NaN or Inf met in the state or the stopping test */
   SR_ENOTCONVERGED = 5,   /* tol > 0 and max_outer reached before convergence */
-  SR_ETIMEOUT = 6,        /* reserved for bounded device-side waits */
+  SR_ETIMEOUT = 6,        /* a bounded device-side wait (TMA transfer) ran out of time */
   SR_EUNSUPPORTED = 7     /* size or option this build does not implement */
 } sr_status;
 
@@ -201,10 +201,15 @@ sr_status sr_phi_step_noalloc(int H, int W, const sr_params* p, const float* g,
  *   row_threads: threads per CTA of the row passes; rows per CTA =
  *                row_threads * row_values_per_thread / (W / 2)
  *   col_schedule: 0 = 4 columns per CTA, 16 values per thread (2 columns at
- *                 H = 4096); 1 = 2 columns, 8 values; 2 = 4 columns, 8 values
+ *                 H = 4096); 1 = 2 columns, 8 values; 2 = 4 columns, 8 values;
+ *                 3 = persistent CTAs fed by TMA (tensor-memory-accelerator
+ *                 box loads/stores, double buffered), 4 columns, 16 values
  *   tuned_us: measured microseconds of one row pair plus one column pass
  *             when the autotuner chose the schedule, else 0.
  * Sizes below W = 32 use fixed kernels and report row_threads = 0.
+ * The environment variable SR_FFT_SCHEDULE="row_values,row_threads,
+ * col_schedule" makes sr_create use that schedule (when valid for the size)
+ * instead of tuning, e.g. for reproducible profiling.
  * sr_set_schedule validates the fields (SR_EINVAL) and rebuilds the
  * iteration graphs. */
 typedef struct sr_schedule {

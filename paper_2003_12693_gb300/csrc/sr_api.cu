@@ -1,11 +1,15 @@
 // Host side of the C-ABI declared in include/sr.h: parameter checks, device
 // state, FFT plans and tables, CUDA-graph capture of the outer iteration, and
 // the FP64 stopping test.  The kernels live in sr_kernels.cu.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -33,6 +37,10 @@ struct sr_ctx {
   int row_T = 0, row_NT = 0, row_CW = 0;
   bool fft2 = false;  // register-resident FFT passes (sr_fft.cu) for this size
   sr_schedule sched{};  // schedule of the fft2 passes
+  CUtensorMap tm_X{};   // X as a float32 matrix, boxes for the TMA column pass
+  bool tm_X_ok = false;
+  int col_tma_grid = 0;
+  int* err_dev = nullptr;  // device error flag of the bounded waits
   int n_tile = 0;    // CTAs of the 32 x 8 tile kernels (energy)
   int n_tile32 = 0;  // CTAs of the 32 x 32 tile kernels (w/b update)
 
@@ -52,6 +60,7 @@ struct sr_ctx {
   float2* tw_row = nullptr;
   float2* tw_col = nullptr;
   float2* tw_n = nullptr;
+  float2* tws[4] = {nullptr, nullptr, nullptr, nullptr};  // stage twiddles: row16, row8, col16, col8
   float* aM = nullptr;
   float* aN = nullptr;
   double* partials = nullptr;
@@ -166,6 +175,27 @@ std::vector<float2> twiddles(int n, int len) {
   return t;
 }
 
+// Stage twiddles of the register FFT for a length-len transform with 2^logE
+// values per thread: stage q >= 1 has Ns = 2^(logE q) and radix 2^logE (the
+// last stage 2^(log2(len) mod logE) if that is not 1); its entries
+// exp(-2 pi i k t / (Ns R)) are stored at [t - 1][k].
+std::vector<float2> stage_twiddle_table(int len, int logE) {
+  const int logL = ilog2(len);
+  const int nst = (logL + logE - 1) / logE;
+  std::vector<float2> v;
+  for (int q = 1; q < nst; ++q) {
+    const int logR = q < logL / logE ? logE : logL % logE;
+    const int R = 1 << logR, Ns = 1 << (logE * q);
+    for (int t = 1; t < R; ++t)
+      for (int k = 0; k < Ns; ++k) {
+        const double ang = -2.0 * M_PI * (double)k * (double)t / ((double)Ns * (double)R);
+        v.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
+      }
+  }
+  if (v.empty()) v.push_back(make_float2(1.f, 0.f));  // keep the allocation non-empty
+  return v;
+}
+
 template <class T>
 sr_status upload(sr_ctx* c, T** dst, const std::vector<T>& v) {
   SR_CUDA(c, cudaMalloc((void**)dst, v.size() * sizeof(T)));
@@ -230,7 +260,8 @@ int sched_rows(const sr_ctx* c, const sr_schedule& sc) {
 bool sched_valid(const sr_ctx* c, const sr_schedule& sc) {
   if (!c->fft2) return false;
   if (sc.row_values_per_thread != 8 && sc.row_values_per_thread != 16) return false;
-  if (sc.col_schedule < 0 || sc.col_schedule > 2) return false;
+  if (sc.col_schedule < 0 || sc.col_schedule > 3) return false;
+  if (sc.col_schedule == 3 && !c->tm_X_ok) return false;
   if (srk::colsolve2_threads(c->H, sc.col_schedule) > 1024) return false;
   if (sc.row_threads < 1 || sc.row_threads > 512) return false;
   const long long prod = (long long)sc.row_threads * sc.row_values_per_thread;
@@ -238,7 +269,7 @@ bool sched_valid(const sr_ctx* c, const sr_schedule& sc) {
   const int T = (int)(prod / c->L);
   if (T < 1 || T > c->H) return false;
   if (sc.row_threads != T * c->L / sc.row_values_per_thread) return false;
-  return srk::rowfft2_smem(T, c->L) <= 200 * 1024;
+  return srk::rowfft2_smem(T, c->L, sc.row_values_per_thread == 8 ? 3 : 4) <= 200 * 1024;
 }
 
 // raise the shared-memory limits of the kernels a schedule uses
@@ -254,8 +285,47 @@ cudaError_t sched_configure(sr_ctx* c, const sr_schedule& sc) {
   const int le = sc.row_values_per_thread == 8 ? 3 : 4;
   cudaError_t e = srk::launch_rowfft2(fa, le, sc.row_threads, nullptr, true);
   if (e == cudaSuccess) e = srk::launch_rowifft2(ia, true, le, sc.row_threads, nullptr, true);
-  if (e == cudaSuccess) e = srk::launch_colsolve2(ca, sc.col_schedule, nullptr, true);
-  return e;
+  if (e != cudaSuccess) return e;
+  if (sc.col_schedule == 3) {
+    e = srk::launch_colsolve_tma(ca, c->tm_X, 0, nullptr, true);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = srk::colsolve_tma_occupancy(c->H, &per_sm);
+    if (e != cudaSuccess) return e;
+    const int nb = c->L / srk::colsolve_tma_cb(c->H);
+    c->col_tma_grid = std::max(1, std::min(nb, c->nsm * std::max(per_sm, 1)));
+    return cudaSuccess;
+  }
+  return srk::launch_colsolve2(ca, sc.col_schedule, nullptr, true);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D float32 tensor map: rows x cols (cols innermost), row pitch in floats,
+// box of box_cols x box_rows, zero fill outside the tensor.
+bool make_tensor_map_2d(CUtensorMap* map, const void* base, int rows, int cols, int pitch,
+                        int box_cols, int box_rows) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 std::mutex g_tune_mutex;
@@ -264,6 +334,18 @@ std::map<std::pair<int, int>, std::pair<int, sr_schedule>> g_tuned;  // (H, W) -
 // Time the candidate row and column schedules on the context's buffers and
 // keep the fastest (once per image size and device in the process).
 sr_status autotune(sr_ctx* c) {
+  // SR_FFT_SCHEDULE="row_values,row_threads,col_schedule" fixes the schedule
+  // (reproducible profiling); invalid values fall back to tuning
+  if (const char* env = std::getenv("SR_FFT_SCHEDULE")) {
+    sr_schedule sc{};
+    if (std::sscanf(env, "%d,%d,%d", &sc.row_values_per_thread, &sc.row_threads,
+                    &sc.col_schedule) == 3 &&
+        sched_valid(c, sc)) {
+      c->sched = sc;
+      SR_CUDA(c, sched_configure(c, sc));
+      return SR_OK;
+    }
+  }
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tuned.find({c->H, c->W});
@@ -285,7 +367,7 @@ sr_status autotune(sr_ctx* c) {
     cudaError_t e = launch();
     if (e != cudaSuccess) return e;
     if ((e = cudaEventRecord(e0, s)) != cudaSuccess) return e;
-    const int reps = 5;
+    const int reps = 10;
     for (int r = 0; r < reps; ++r)
       if ((e = launch()) != cudaSuccess) return e;
     if ((e = cudaEventRecord(e1, s)) != cudaSuccess) return e;
@@ -295,6 +377,29 @@ sr_status autotune(sr_ctx* c) {
     *us = 1000.f * ms / reps;
     return cudaSuccess;
   };
+  // bring clocks up before timing: ~20 ms of back-to-back launches
+  {
+    srk::ColArgs ca{};
+    ca.geo = c->geo;
+    ca.fft = c->fft_col;
+    ca.aM = c->aM;
+    ca.aN = c->aN;
+    ca.X = c->X;
+    sr_schedule sc{16, 0, 0, 0.f};
+    SR_CUDA(c, sched_configure(c, sc));
+    SR_CUDA(c, cudaEventRecord(e0, s));
+    for (int r = 0; r < 4000; ++r) {
+      SR_CUDA(c, srk::launch_colsolve2(ca, 0, s, false));
+      if (r % 200 == 199) {
+        SR_CUDA(c, cudaEventRecord(e1, s));
+        SR_CUDA(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        SR_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms > 20.f) break;
+      }
+    }
+    SR_CUDA(c, cudaStreamSynchronize(s));
+  }
   sr_schedule best{};
   float best_row = 1e30f;
   const int vpts[2] = {16, 8};
@@ -333,7 +438,7 @@ sr_status autotune(sr_ctx* c) {
       }
     }
   float best_col = 1e30f;
-  for (int cs = 0; cs < 3 && err == cudaSuccess; ++cs) {
+  for (int cs = 0; cs < 4 && err == cudaSuccess; ++cs) {
     sr_schedule sc = best;
     sc.col_schedule = cs;
     if (!sched_valid(c, sc)) continue;
@@ -344,8 +449,12 @@ sr_status autotune(sr_ctx* c) {
     ca.aM = c->aM;
     ca.aN = c->aN;
     ca.X = c->X;
+    ca.err = c->err_dev;
     float us = 0.f;
-    err = time_it([&] { return srk::launch_colsolve2(ca, cs, s, false); }, &us);
+    err = time_it([&] {
+      return cs == 3 ? srk::launch_colsolve_tma(ca, c->tm_X, c->col_tma_grid, s, false)
+                     : srk::launch_colsolve2(ca, cs, s, false);
+    }, &us);
     if (err == cudaSuccess && us < best_col) {
       best_col = us;
       best.col_schedule = cs;
@@ -406,9 +515,12 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
   ca.aM = c->aM;
   ca.aN = c->aN;
   ca.X = c->X;
+  ca.err = c->err_dev;
   st = run_kernel(c, SR_KCLASS_COLSOLVE, s, "k_colsolve", [&] {
-    return c->fft2 ? srk::launch_colsolve2(ca, c->sched.col_schedule, s, false)
-                   : srk::launch_colsolve(ca, s);
+    if (!c->fft2) return srk::launch_colsolve(ca, s);
+    if (c->sched.col_schedule == 3)
+      return srk::launch_colsolve_tma(ca, c->tm_X, c->col_tma_grid, s, false);
+    return srk::launch_colsolve2(ca, c->sched.col_schedule, s, false);
   });
   if (st != SR_OK) return st;
   srk::RowInvArgs ia{};
@@ -497,10 +609,24 @@ sr_status build_graphs(sr_ctx* c) {
   return SR_OK;
 }
 
+// Device-side bounded waits record timeouts in err_dev; read it at every sync.
+sr_status check_device_error(sr_ctx* c) {
+  int h = 0;
+  SR_CUDA(c, cudaMemcpyAsync(&h, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  SR_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (h) {
+    cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
+    return fail(c, SR_ETIMEOUT, "a device-side wait for a TMA transfer ran out of time");
+  }
+  return SR_OK;
+}
+
 sr_status read_residual(sr_ctx* c, double* rel) {
   SR_CUDA(c, cudaMemcpyAsync(c->red_host, c->red, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                              c->stream));
   SR_CUDA(c, cudaStreamSynchronize(c->stream));
+  sr_status es = check_device_error(c);
+  if (es != SR_OK) return es;
   const double num = c->red_host[0], den = c->red_host[1];
   const double r = std::sqrt(num) / (std::sqrt(den) + 1e-6);
   *rel = r;
@@ -558,7 +684,8 @@ void sr_destroy(sr_ctx* c) {
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   void* bufs[] = {c->phi[0], c->phi[1], c->w1[0], c->w1[1], c->w2[0], c->w2[1], c->b1, c->b2,
                   c->g, c->tmp1, c->tmp2, c->stage, c->G, c->mask_dev, c->X, c->tw_row, c->tw_col,
-                  c->tw_n, c->aM, c->aN, c->partials, c->red};
+                  c->tw_n, c->aM, c->aN, c->partials, c->red, c->err_dev,
+                  c->tws[0], c->tws[1], c->tws[2], c->tws[3]};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -671,8 +798,27 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   if (upload(c, &c->aN, aN) != SR_OK) return bail(SR_ECUDA);
   make_fft(c->fft_row, L, c->tw_row);
   make_fft(c->fft_col, H, c->tw_col);
+  {
+    const int lens[4] = {L, L, H, H}, loges[4] = {4, 3, 4, 3};
+    for (int q = 0; q < 4; ++q) {
+      std::vector<float2> tb = stage_twiddle_table(lens[q], loges[q]);
+      const int want = srk::stage_twiddles(lens[q], loges[q]);
+      if (want > 0 && (int)tb.size() != want) return bail(SR_ECUDA);
+      if (upload(c, &c->tws[q], tb) != SR_OK) return bail(SR_ECUDA);
+    }
+    c->fft_row.tws16 = c->tws[0];
+    c->fft_row.tws8 = c->tws[1];
+    c->fft_col.tws16 = c->tws[2];
+    c->fft_col.tws8 = c->tws[3];
+  }
+  CREATE_CUDA(cudaMalloc((void**)&c->err_dev, sizeof(int)));
+  CREATE_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
   c->fft2 = srk::fft2_supported(c->geo);
-  if (c->fft2 && autotune(c) != SR_OK) return bail(SR_ECUDA);
+  if (c->fft2) {
+    const int cb = srk::colsolve_tma_cb(H);
+    c->tm_X_ok = make_tensor_map_2d(&c->tm_X, c->X, H, W, W, 2 * cb, H < 256 ? H : 256);
+    if (autotune(c) != SR_OK) return bail(SR_ECUDA);
+  }
 
   // g = 1 until sr_edge_function is called
   std::vector<float> ones(P, 1.f);

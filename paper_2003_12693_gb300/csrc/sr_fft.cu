@@ -15,6 +15,7 @@
 //   k_rowifft<LOGL>   rows: rebuild the length-L sequence, inverse FFT_L,
 //                     interleave, add psi (increment form) or store
 #include "sr_internal.h"
+#include "sr_tma.cuh"
 
 namespace srk {
 namespace fft2 {
@@ -102,17 +103,43 @@ __device__ __forceinline__ void dft(float2* x) {
 // padded shared-memory position of sequence index a (1 pad per 16 values)
 __device__ __forceinline__ int pad(int a) { return a + (a >> 4); }
 
+// Twiddles of the Stockham stages, laid out per stage as [t - 1][k]
+// (t = 1..R-1, k = 0..Ns-1, value exp(-2 pi i k t / (Ns R))), so that the
+// threads of a warp, which hold consecutive k, read consecutive entries.
+// Stage s >= 1 has Ns = E^s; only the last stage may have a radix below E.
+template <int LOGL, int LOGE>
+struct TwPlan {
+  static constexpr int NST = (LOGL + LOGE - 1) / LOGE;
+  __host__ __device__ static constexpr int log_r(int s) {
+    return s < LOGL / LOGE ? LOGE : LOGL % LOGE;
+  }
+  __host__ __device__ static constexpr int offset(int s) {
+    int o = 0;
+    for (int q = 1; q < s; ++q) o += ((1 << log_r(q)) - 1) << (LOGE * q);
+    return o;
+  }
+  static constexpr int TOTAL = offset(NST);
+};
+
+// Copy a stage-twiddle table into shared memory (the caller synchronises).
+template <int N>
+__device__ __forceinline__ void stage_table(float2* dst, const float2* __restrict__ src) {
+  for (int q = threadIdx.x; q < N; q += blockDim.x) dst[q] = __ldg(src + q);
+}
+
 // Element a of the thread's sequence lives at smem[pad(a) * STRIDE] (STRIDE =
 // 1 for rows, CB for interleaved columns; `base` already includes the
 // sequence offset).  The thread holds E = 2^LOGE values x[m] = seq[u + (L/E) m];
 // stages use radix E, the last one radix 2^(LOGL mod LOGE) if that is not 1.
+// stw is the stage-twiddle table in shared memory.
 template <int LOGL, int LOGE, int S, bool INV, int STRIDE>
 __device__ __forceinline__ void stages(float2 (&x)[1 << LOGE], float2* base, int u,
-                                       const float2* __restrict__ tw) {
+                                       const float2* stw) {
+  using TP = TwPlan<LOGL, LOGE>;
   constexpr int E = 1 << LOGE;
-  constexpr int NST = (LOGL + LOGE - 1) / LOGE;
+  constexpr int NST = TP::NST;
   if constexpr (S < NST) {
-    constexpr int LOGR = (S < LOGL / LOGE) ? LOGE : (LOGL % LOGE);
+    constexpr int LOGR = TP::log_r(S);
     constexpr int R = 1 << LOGR, NB = E / R;
     constexpr int LOGNS = LOGE * S;
     constexpr int LOGTP = LOGL - LOGE;
@@ -124,10 +151,10 @@ __device__ __forceinline__ void stages(float2 (&x)[1 << LOGE], float2* base, int
       for (int t = 0; t < R; ++t) v[t] = x[b + t * NB];
       if constexpr (LOGNS > 0) {
         const int k = j & ((1 << LOGNS) - 1);
-        constexpr int TSH = LOGL - LOGNS - LOGR;
+        constexpr int OFF = TP::offset(S);
 #pragma unroll
         for (int t = 1; t < R; ++t) {
-          float2 w = __ldg(&tw[(k * t) << TSH]);
+          float2 w = stw[OFF + ((t - 1) << LOGNS) + k];
           if (INV) w.y = -w.y;
           v[t] = cmul(v[t], w);
         }
@@ -149,7 +176,7 @@ __device__ __forceinline__ void stages(float2 (&x)[1 << LOGE], float2* base, int
 #pragma unroll
       for (int m = 0; m < E; ++m) x[m] = base[pad(u + (m << LOGTP)) * STRIDE];
       __syncthreads();
-      stages<LOGL, LOGE, S + 1, INV, STRIDE>(x, base, u, tw);
+      stages<LOGL, LOGE, S + 1, INV, STRIDE>(x, base, u, stw);
     }
   }
 }
@@ -168,11 +195,13 @@ __global__ void __launch_bounds__(512) k_rowfft(const RowFwdArgs a) {
   const int i = blockIdx.x * a.T + t;
   const bool live = i < a.geo.M;
   float2* base = smem2 + t * S;
+  float2* stw = smem2 + a.T * S;
   float2 x[E];
   const float2* row = reinterpret_cast<const float2*>(a.src + (size_t)(live ? i : 0) * a.geo.N);
 #pragma unroll
   for (int m = 0; m < E; ++m) x[m] = live ? __ldg(row + u + (m << LOGTP)) : make_float2(0.f, 0.f);
-  stages<LOGL, LOGE, 0, false, 1>(x, base, u, a.fft.tw);
+  stage_table<TwPlan<LOGL, LOGE>::TOTAL>(stw, LOGE == 4 ? a.fft.tws16 : a.fft.tws8);
+  stages<LOGL, LOGE, 0, false, 1>(x, base, u, stw);
   // even/odd split needs Z_{L-k}: exchange through shared memory
 #pragma unroll
   for (int m = 0; m < E; ++m) base[pad(u + (m << LOGTP))] = x[m];
@@ -210,6 +239,8 @@ __global__ void __launch_bounds__(512) k_rowifft(const RowInvArgs a) {
   const bool live = i < a.geo.M;
   const int ii = live ? i : 0;
   float2* base = smem2 + t * S;
+  float2* stw = smem2 + a.T * S;
+  stage_table<TwPlan<LOGL, LOGE>::TOTAL>(stw, LOGE == 4 ? a.fft.tws16 : a.fft.tws8);
   float2 p[E];
   if (ADD) {
     const float2* prow = reinterpret_cast<const float2*>(a.psi_in + (size_t)ii * a.geo.N);
@@ -238,7 +269,7 @@ __global__ void __launch_bounds__(512) k_rowifft(const RowInvArgs a) {
     const float2 Xo = cmul(D, cconj(__ldg(&a.twN[k])));
     x[m] = make_float2(Xe.x - Xo.y, Xe.y + Xo.x);
   }
-  stages<LOGL, LOGE, 0, true, 1>(x, base, u, a.fft.tw);
+  stages<LOGL, LOGE, 0, true, 1>(x, base, u, stw);
   if (!live) return;
   float2* orow = reinterpret_cast<float2*>(a.out + (size_t)i * a.geo.N);
 #pragma unroll
@@ -253,9 +284,9 @@ __global__ void __launch_bounds__(512) k_rowifft(const RowInvArgs a) {
 // columns: CB adjacent columns of X per CTA, thread (u, c) with c fastest
 // ---------------------------------------------------------------------------
 template <int LOGM, int CB, int LOGE>
-constexpr int col_threads() { return CB * (1 << LOGM) / (1 << LOGE); }
+__host__ __device__ constexpr int col_threads() { return CB * (1 << LOGM) / (1 << LOGE); }
 template <int LOGM, int CB, int LOGE>
-constexpr int col_min_blocks() {
+__host__ __device__ constexpr int col_min_blocks() {
   return (LOGE == 3 && col_threads<LOGM, CB, LOGE>() <= 512) ? 3 : 1;
 }
 
@@ -271,10 +302,12 @@ __global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), col_min_blocks<
   const int c0 = blockIdx.x * CB;
   const int k = c0 + c;
   float2* base = smem2 + c;
+  float2* stw = smem2 + CB * (M + M / 16);
   float2 x[E];
 #pragma unroll
   for (int m = 0; m < E; ++m) x[m] = a.X[(size_t)(u + (m << LOGTP)) * L + k];
-  stages<LOGM, LOGE, 0, false, CB>(x, base, u, a.fft.tw);
+  stage_table<TwPlan<LOGM, LOGE>::TOTAL>(stw, LOGE == 4 ? a.fft.tws16 : a.fft.tws8);
+  stages<LOGM, LOGE, 0, false, CB>(x, base, u, stw);
   const float inv_mn = 1.f / ((float)M * (float)a.geo.N);
   if (c0 == 0) {
     // column 0 packs the DC and Nyquist columns of the row transforms: split
@@ -308,9 +341,136 @@ __global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), col_min_blocks<
       x[m] = make_float2(x[m].x * s, x[m].y * s);
     }
   }
-  stages<LOGM, LOGE, 0, true, CB>(x, base, u, a.fft.tw);
+  stages<LOGM, LOGE, 0, true, CB>(x, base, u, stw);
 #pragma unroll
   for (int m = 0; m < E; ++m) a.X[(size_t)(u + (m << LOGTP)) * L + k] = x[m];
+}
+
+// ---------------------------------------------------------------------------
+// columns, persistent with TMA: each CTA walks over column blocks; the block
+// it works on was brought into shared memory by a 2-D TMA load (boxes of
+// CB columns x up to 256 rows) while the previous block was computed, and
+// goes back by TMA store.  The shared buffer of a block doubles as the
+// exchange buffer of its FFT stages once the values are in registers.
+// ---------------------------------------------------------------------------
+// float2 per TMA column buffer: room for the padded exchange layout, rounded
+// up to 128 bytes so the second buffer and every box stay 128-byte aligned
+template <int LOGM, int CB>
+__host__ __device__ constexpr int col_tma_buf() {
+  return ((((1 << LOGM) + (1 << LOGM) / 16) * CB + 15) / 16) * 16;
+}
+template <int LOGM, int CB>
+__host__ __device__ constexpr size_t col_tma_smem() {
+  return 2 * (size_t)col_tma_buf<LOGM, CB>() * sizeof(float2) +
+         (size_t)TwPlan<LOGM, 4>::TOTAL * sizeof(float2) + (size_t)(1 << LOGM) * sizeof(float) + 128 +
+         2 * sizeof(uint64_t);
+}
+
+template <int LOGM, int CB, int LOGE>
+__global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), 1)
+    k_colsolve_tma(const ColArgs a, const __grid_constant__ CUtensorMap tmX) {
+  constexpr int E = 1 << LOGE, M = 1 << LOGM, LOGTP = LOGM - LOGE;
+  constexpr int BOXR = M < 256 ? M : 256;
+  constexpr int NBOX = M / BOXR;
+  constexpr int BUF = col_tma_buf<LOGM, CB>();
+  constexpr uint32_t BYTES = (uint32_t)M * CB * sizeof(float2);
+  // dynamic shared memory: [up to 128 B of alignment][buffer 0][buffer 1][2 mbarriers]
+  extern __shared__ __align__(16) unsigned char smem_tma[];
+  float2* smem2 = reinterpret_cast<float2*>(
+      (reinterpret_cast<uintptr_t>(smem_tma) + 127) & ~static_cast<uintptr_t>(127));
+  float2* stw = smem2 + 2 * BUF;
+  float* s_aM = reinterpret_cast<float*>(stw + TwPlan<LOGM, LOGE>::TOTAL);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_aM + M);
+  stage_table<TwPlan<LOGM, LOGE>::TOTAL>(stw, a.fft.tws16);
+  for (int q = threadIdx.x; q < M; q += blockDim.x) s_aM[q] = __ldg(a.aM + q);
+  const int tid = threadIdx.x;
+  const int c = tid % CB, u = tid / CB;
+  const int L = a.geo.L, nb = L / CB;
+  const float inv_mn = 1.f / ((float)M * (float)a.geo.N);
+  if (tid == 0) {
+    tma::mbar_init(&bar[0], 1);
+    tma::mbar_init(&bar[1], 1);
+    tma::mbar_init_fence();
+  }
+  __syncthreads();
+  int blk = blockIdx.x;
+  if (tid == 0 && blk < nb) {
+    tma::mbar_expect_tx(&bar[0], BYTES);
+#pragma unroll
+    for (int q = 0; q < NBOX; ++q)
+      tma::load_2d(smem2 + q * BOXR * CB, &tmX, 2 * CB * blk, q * BOXR, &bar[0]);
+  }
+  for (int it = 0; blk < nb; blk += gridDim.x, ++it) {
+    const int b = it & 1;
+    const uint32_t par = (it >> 1) & 1;
+    float2* B = smem2 + b * BUF;
+    const int nxt = blk + gridDim.x;
+    if (tid == 0 && nxt < nb) {
+      tma::store_wait_read();  // the other buffer's stores have read it
+      float2* Bn = smem2 + (1 - b) * BUF;
+      tma::mbar_expect_tx(&bar[1 - b], BYTES);
+#pragma unroll
+      for (int q = 0; q < NBOX; ++q)
+        tma::load_2d(Bn + q * BOXR * CB, &tmX, 2 * CB * nxt, q * BOXR, &bar[1 - b]);
+    }
+    const bool ok = tma::mbar_wait(&bar[b], par);
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) {
+        tma::on_timeout(&bar[b], par, a.err);
+        if (nxt < nb) tma::mbar_wait(&bar[1 - b], ((it + 1) >> 1) & 1);
+      }
+      return;
+    }
+    const int k = blk * CB + c;
+    float2 x[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = B[(u + (m << LOGTP)) * CB + c];
+    __syncthreads();  // B is now the exchange buffer
+    float2* base = B + c;
+    stages<LOGM, LOGE, 0, false, CB>(x, base, u, stw);
+    if (blk == 0) {
+      if (c == 0) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) base[pad(u + (m << LOGTP)) * CB] = x[m];
+      }
+      __syncthreads();
+      if (c == 0) {
+        const float aNy = a.aN[L];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+          const int l = u + (m << LOGTP);
+          const float2 Cl = x[m], Cm = base[pad((M - l) & (M - 1)) * CB];
+          const float sA = inv_mn / (1.f + s_aM[l] + a.aN[0]);
+          const float sB = inv_mn / (1.f + s_aM[l] + aNy);
+          const float2 A = make_float2(0.5f * (Cl.x + Cm.x) * sA, 0.5f * (Cl.y - Cm.y) * sA);
+          const float2 D = make_float2(0.5f * (Cl.x - Cm.x), 0.5f * (Cl.y + Cm.y));
+          const float2 Bq = make_float2(D.y * sB, -D.x * sB);
+          x[m] = make_float2(A.x - Bq.y, A.y + Bq.x);
+        }
+      }
+      __syncthreads();
+    }
+    if (k != 0) {
+      const float ak = a.aN[k];
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const float sc = inv_mn / (1.f + s_aM[u + (m << LOGTP)] + ak);
+        x[m] = make_float2(x[m].x * sc, x[m].y * sc);
+      }
+    }
+    stages<LOGM, LOGE, 0, true, CB>(x, base, u, stw);
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) B[(u + (m << LOGTP)) * CB + c] = x[m];
+    tma::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+      for (int q = 0; q < NBOX; ++q) tma::store_2d(&tmX, B + q * BOXR * CB, 2 * CB * blk, q * BOXR);
+      tma::store_commit();
+    }
+  }
+  if (tid == 0) tma::store_wait_all();
 }
 
 }  // namespace fft2
@@ -352,7 +512,7 @@ static cudaError_t rowifft_go(const RowInvArgs& a, bool add, int nthreads, size_
 template <int LOGM, int CB, int LOGE>
 static cudaError_t col_go(const ColArgs& a, cudaStream_t s, bool set_attr) {
   constexpr int M = 1 << LOGM;
-  const size_t smem = (size_t)CB * (M + M / 16) * sizeof(float2);
+  const size_t smem = ((size_t)CB * (M + M / 16) + TwPlan<LOGM, LOGE>::TOTAL) * sizeof(float2);
   if (set_attr) return set_smem(k_colsolve2<LOGM, CB, LOGE>, smem);
   k_colsolve2<LOGM, CB, LOGE><<<a.geo.L / CB, CB * M / (1 << LOGE), smem, s>>>(a);
   return cudaGetLastError();
@@ -360,7 +520,27 @@ static cudaError_t col_go(const ColArgs& a, cudaStream_t s, bool set_attr) {
 
 bool fft2_supported(const Geo& geo) { return geo.L >= 16 && geo.L <= 2048 && geo.M >= 16 && geo.M <= 4096; }
 
-size_t rowfft2_smem(int T, int L) { return (size_t)T * (L + L / 16) * sizeof(float2); }
+template <int LOGL>
+static int tw_total(int logE) { return logE == 3 ? TwPlan<LOGL, 3>::TOTAL : TwPlan<LOGL, 4>::TOTAL; }
+
+int stage_twiddles(int L, int logE) {
+  switch (L) {
+    case 16: return tw_total<4>(logE);
+    case 32: return tw_total<5>(logE);
+    case 64: return tw_total<6>(logE);
+    case 128: return tw_total<7>(logE);
+    case 256: return tw_total<8>(logE);
+    case 512: return tw_total<9>(logE);
+    case 1024: return tw_total<10>(logE);
+    case 2048: return tw_total<11>(logE);
+    case 4096: return tw_total<12>(logE);
+  }
+  return 0;
+}
+
+size_t rowfft2_smem(int T, int L, int logE) {
+  return ((size_t)T * (L + L / 16) + stage_twiddles(L, logE)) * sizeof(float2);
+}
 
 #define SR_ROW_SWITCH(CALL)                         \
   switch (a.geo.L) {                                \
@@ -372,7 +552,7 @@ size_t rowfft2_smem(int T, int L) { return (size_t)T * (L + L / 16) * sizeof(flo
 
 cudaError_t launch_rowfft2(const RowFwdArgs& a, int logE, int nthreads, cudaStream_t s,
                            bool set_attr) {
-  const size_t sm = rowfft2_smem(a.T, a.geo.L);
+  const size_t sm = rowfft2_smem(a.T, a.geo.L, logE);
 #define SR_CALL(l)                                                                   \
   return logE == 3 ? rowfft_go<l, 3>(a, nthreads, sm, s, set_attr)                  \
                    : rowfft_go<l, 4>(a, nthreads, sm, s, set_attr);
@@ -383,7 +563,7 @@ cudaError_t launch_rowfft2(const RowFwdArgs& a, int logE, int nthreads, cudaStre
 
 cudaError_t launch_rowifft2(const RowInvArgs& a, bool add, int logE, int nthreads, cudaStream_t s,
                             bool set_attr) {
-  const size_t sm = rowfft2_smem(a.T, a.geo.L);
+  const size_t sm = rowfft2_smem(a.T, a.geo.L, logE);
 #define SR_CALL(l)                                                                   \
   return logE == 3 ? rowifft_go<l, 3>(a, add, nthreads, sm, s, set_attr)            \
                    : rowifft_go<l, 4>(a, add, nthreads, sm, s, set_attr);
@@ -406,7 +586,51 @@ cudaError_t launch_colsolve2(const ColArgs& a, int sched, cudaStream_t s, bool s
   return cudaErrorInvalidValue;
 }
 
+template <int LOGM, int CB, int LOGE>
+static cudaError_t col_tma_go(const ColArgs& a, const CUtensorMap& tm, int grid, cudaStream_t s,
+                              bool set_attr) {
+  const size_t smem = col_tma_smem<LOGM, CB>();
+  if (set_attr) return set_smem(k_colsolve_tma<LOGM, CB, LOGE>, smem);
+  k_colsolve_tma<LOGM, CB, LOGE><<<grid, col_threads<LOGM, CB, LOGE>(), smem, s>>>(a, tm);
+  return cudaGetLastError();
+}
+
+// schedule 3: persistent TMA columns (4 columns x 16 values; 2 columns at H = 4096)
+cudaError_t launch_colsolve_tma(const ColArgs& a, const CUtensorMap& tm, int grid, cudaStream_t s,
+                                bool set_attr) {
+#define SR_COL(lm)                                                                  \
+  case (1 << lm):                                                                   \
+    return (lm == 12) ? col_tma_go<lm, 2, 4>(a, tm, grid, s, set_attr)              \
+                      : col_tma_go<lm, 4, 4>(a, tm, grid, s, set_attr);
+  switch (a.geo.M) {
+    SR_COL(4) SR_COL(5) SR_COL(6) SR_COL(7) SR_COL(8) SR_COL(9) SR_COL(10) SR_COL(11) SR_COL(12)
+  }
+#undef SR_COL
+  return cudaErrorInvalidValue;
+}
+
+int colsolve_tma_cb(int M) { return M == 4096 ? 2 : 4; }
+
+template <int LOGM, int CB, int LOGE>
+static cudaError_t col_tma_occ(int* blocks) {
+  const size_t smem = col_tma_smem<LOGM, CB>();
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_colsolve_tma<LOGM, CB, LOGE>,
+                                                       col_threads<LOGM, CB, LOGE>(), smem);
+}
+
+cudaError_t colsolve_tma_occupancy(int M, int* blocks_per_sm) {
+#define SR_COL(lm) \
+  case (1 << lm):  \
+    return (lm == 12) ? col_tma_occ<lm, 2, 4>(blocks_per_sm) : col_tma_occ<lm, 4, 4>(blocks_per_sm);
+  switch (M) {
+    SR_COL(4) SR_COL(5) SR_COL(6) SR_COL(7) SR_COL(8) SR_COL(9) SR_COL(10) SR_COL(11) SR_COL(12)
+  }
+#undef SR_COL
+  return cudaErrorInvalidValue;
+}
+
 int colsolve2_threads(int M, int sched) {
+  if (sched == 3) return colsolve_tma_cb(M) * M / 16;
   if (sched == 1) return 2 * M / 8;
   if (sched == 2) return 4 * M / 8;
   return M == 4096 ? 2 * M / 16 : 4 * M / 16;

@@ -2,6 +2,7 @@
 // (sr_kernels.cu).  Not part of the public C-ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,6 +32,8 @@ struct Fft {
   int n16;
   int tail;
   const float2* tw;       // tw[q] = exp(-2 pi i q / L), q in [0, L)
+  const float2* tws16;    // stage twiddles of the register FFT, 16 values per thread
+  const float2* tws8;     // stage twiddles of the register FFT, 8 values per thread
 };
 
 struct Geo {
@@ -65,6 +68,7 @@ struct ColArgs {
   const float* aM;         // tau mu 4 sin^2(pi l / M), l in [0, M)
   const float* aN;         // tau mu 4 sin^2(pi k / N), k in [0, L]
   float2* X;
+  int* err;                // device error flag (bounded waits), may be null
 };
 
 // Row pass, inverse: half spectrum to real rows; ADD mode adds psi_in.
@@ -169,13 +173,20 @@ cudaError_t configure_kernels();   // raise dynamic shared-memory limits once
 // values per thread; 2 columns at H = 4096), 1 (2 columns, 8 values),
 // 2 (4 columns, 8 values).
 bool fft2_supported(const Geo& geo);
-size_t rowfft2_smem(int T, int L);
+size_t rowfft2_smem(int T, int L, int logE);
+int stage_twiddles(int L, int logE);  // entries of the stage-twiddle table
 cudaError_t launch_rowfft2(const RowFwdArgs& a, int logE, int nthreads, cudaStream_t s,
                            bool set_attr);
 cudaError_t launch_rowifft2(const RowInvArgs& a, bool add, int logE, int nthreads, cudaStream_t s,
                             bool set_attr);
 cudaError_t launch_colsolve2(const ColArgs& a, int sched, cudaStream_t s, bool set_attr);
 int colsolve2_threads(int M, int sched);
+// Persistent TMA column pass (schedule 3); tm maps X as a float32 matrix of
+// H rows by W floats with boxes of 2 * colsolve_tma_cb(H) x min(H, 256).
+cudaError_t launch_colsolve_tma(const ColArgs& a, const CUtensorMap& tm, int grid, cudaStream_t s,
+                                bool set_attr);
+int colsolve_tma_cb(int M);
+cudaError_t colsolve_tma_occupancy(int M, int* blocks_per_sm);  // after set_attr
 int tile_blocks(const Geo& geo);   // CTAs of the 2-D tile kernels
 
 }  // namespace srk
