@@ -37,13 +37,15 @@ METRIC = ("SR Mpixel·iter/s (% HBM peak); s per converged mask, plain vs "
           "learned+batched")
 UNIT = "Mpixel·iter/s"
 
-# Algorithmic bytes per pixel of one launch of each kernel (FP32 planes):
-#   prep:      read psi, g, w1, w2, b1, b2 (24 B), write the right-hand side G (4 B)
+# Algorithmic bytes per pixel of one launch of each kernel (FP32 planes; the
+# Bregman variable is carried as e = b - w; w and g are read only on tiles
+# that hold narrow-band pixels, which are not counted):
+#   prep:      read psi, e1, e2 (12 B), write the right-hand side G (4 B)
 #   rowfft:    read G (4 B), write the half spectrum (4 B)
 #   colsolve:  read and write the half spectrum (8 B)
 #   rowifft:   read the half spectrum (4 B) and psi (4 B), write psi (4 B)
-#   wb_update: read phi, g, w1, w2, b1, b2 (24 B), write w1, w2, b1, b2 (16 B)
-BYTES_PER_PX = {"prep": 28, "rowfft": 8, "colsolve": 8, "rowifft": 12, "wb_update": 40}
+#   wb_update: read phi, w1, w2, e1, e2 (20 B), write w1, w2, e1, e2 (16 B)
+BYTES_PER_PX = {"prep": 16, "rowfft": 8, "colsolve": 8, "rowifft": 12, "wb_update": 36}
 KERNEL_NAMES = {"prep": "k_prep", "rowfft": "k_rowfwd", "colsolve": "k_colsolve",
                 "rowifft": "k_rowinv", "wb_update": "k_wb_update"}
 

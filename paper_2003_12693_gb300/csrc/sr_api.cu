@@ -41,6 +41,17 @@ struct sr_ctx {
   bool tm_X_ok = false;
   int col_tma_grid = 0;
   int* err_dev = nullptr;  // device error flag of the bounded waits
+  // tensor maps of the TMA tile kernels, keyed by buffer and box shape; the
+  // context's own buffers are encoded at creation, caller buffers on demand
+  struct MapEntry {
+    const void* p;
+    int kind;
+    CUtensorMap map;
+  };
+  std::vector<MapEntry> maps;
+  size_t own_maps = 0;
+  bool tile_tma = false;     // TMA tile kernels available for this size
+  bool tile_tma_on = false;  // chosen by the autotuner
   int n_tile = 0;    // CTAs of the 32 x 8 tile kernels (energy)
   int n_tile32 = 0;  // CTAs of the 32 x 32 tile kernels (w/b update)
 
@@ -48,8 +59,8 @@ struct sr_ctx {
   float* phi[2] = {nullptr, nullptr};
   float* w1[2] = {nullptr, nullptr};
   float* w2[2] = {nullptr, nullptr};
-  float* b1 = nullptr;
-  float* b2 = nullptr;
+  float* e1 = nullptr;  // Bregman variable carried as e = b - w
+  float* e2 = nullptr;
   float* g = nullptr;
   float* tmp1 = nullptr;
   float* tmp2 = nullptr;
@@ -331,6 +342,32 @@ bool make_tensor_map_2d(CUtensorMap* map, const void* base, int rows, int cols, 
 std::mutex g_tune_mutex;
 std::map<std::pair<int, int>, std::pair<int, sr_schedule>> g_tuned;  // (H, W) -> (device, schedule)
 
+// Box shapes of the TMA tile kernels.
+enum MapKind { MK_HALO = 0, MK_C32 = 1, MK_B1UP = 2, MK_B2LEFT = 3 };
+
+bool tile_map(sr_ctx* c, const float* p, int kind, CUtensorMap* out) {
+  for (const auto& e : c->maps)
+    if (e.p == p && e.kind == kind) {
+      *out = e.map;
+      return true;
+    }
+  int bw = 32, bh = 32;
+  if (kind == MK_HALO) {
+    bw = 32 + 2 * srk::tile_halo_x(c->prm.win_radius);
+    bh = 32 + 2 * srk::tile_halo_y(c->prm.win_radius);
+  } else if (kind == MK_B1UP) {
+    bh = 33;
+  } else if (kind == MK_B2LEFT) {
+    bw = 36;
+  }
+  sr_ctx::MapEntry e{p, kind, {}};
+  if (!make_tensor_map_2d(&e.map, p, c->H, c->W, c->W, bw, bh)) return false;
+  if (c->maps.size() >= 64) c->maps.resize(c->own_maps);  // forget caller buffers
+  c->maps.push_back(e);
+  *out = e.map;
+  return true;
+}
+
 // Time the candidate row and column schedules on the context's buffers and
 // keep the fastest (once per image size and device in the process).
 sr_status autotune(sr_ctx* c) {
@@ -475,7 +512,7 @@ sr_status autotune(sr_ctx* c) {
 // With load_src set, the step solves L out = load_src instead (Eqs. (31)-(33)
 // alone).
 sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const float* w1,
-                           const float* w2, const float* b1, const float* b2, float* psi_out,
+                           const float* w2, const float* e1, const float* e2, float* psi_out,
                            const float* load_src) {
   sr_status st;
   const float* src = load_src;
@@ -487,10 +524,19 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
     pa.g = c->g;
     pa.w1 = w1;
     pa.w2 = w2;
-    pa.b1 = b1;
-    pa.b2 = b2;
+    pa.e1 = e1;
+    pa.e2 = e2;
     pa.G = c->G;
-    st = run_kernel(c, SR_KCLASS_PREP, s, "k_prep", [&] { return srk::launch_prep(pa, s); });
+    pa.err = c->err_dev;
+    srk::PrepMaps pm{};
+    const bool use_tma = c->tile_tma && c->tile_tma_on &&
+                         tile_map(c, psi_in, MK_HALO, &pm.psi) &&
+                         tile_map(c, w1, MK_HALO, &pm.w1) && tile_map(c, w2, MK_HALO, &pm.w2) &&
+                         tile_map(c, e1, MK_B1UP, &pm.e1) && tile_map(c, e2, MK_B2LEFT, &pm.e2) &&
+                         tile_map(c, c->g, MK_C32, &pm.g);
+    st = run_kernel(c, SR_KCLASS_PREP, s, "k_prep", [&] {
+      return use_tma ? srk::launch_prep_tma(pa, pm, s) : srk::launch_prep(pa, s);
+    });
     if (st != SR_OK) return st;
     src = c->G;
   }
@@ -541,8 +587,8 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
 }
 
 sr_status enqueue_wb(sr_ctx* c, cudaStream_t s, const float* phi1, const float* w1i,
-                     const float* w2i, const float* b1i, const float* b2i, float* w1o, float* w2o,
-                     float* b1o, float* b2o, const float* phi_old) {
+                     const float* w2i, const float* e1i, const float* e2i, float* w1o, float* w2o,
+                     float* e1o, float* e2o, const float* phi_old) {
   srk::WBArgs a{};
   a.geo = c->geo;
   a.mod = c->mod;
@@ -550,16 +596,25 @@ sr_status enqueue_wb(sr_ctx* c, cudaStream_t s, const float* phi1, const float* 
   a.g = c->g;
   a.w1 = w1i;
   a.w2 = w2i;
-  a.b1 = b1i;
-  a.b2 = b2i;
+  a.e1 = e1i;
+  a.e2 = e2i;
   a.w1o = w1o;
   a.w2o = w2o;
-  a.b1o = b1o;
-  a.b2o = b2o;
+  a.e1o = e1o;
+  a.e2o = e2o;
   a.phi_old = phi_old;
   a.partials = c->partials;
-  sr_status st = run_kernel(c, SR_KCLASS_WB_UPDATE, s, "k_wb_update",
-                            [&] { return srk::launch_wb_update(a, s); });
+  a.err = c->err_dev;
+  srk::WBMaps wm{};
+  const bool use_tma = c->tile_tma && c->tile_tma_on && tile_map(c, phi1, MK_HALO, &wm.psi) &&
+                       tile_map(c, w1i, MK_HALO, &wm.w1) && tile_map(c, w2i, MK_HALO, &wm.w2) &&
+                       tile_map(c, w1i, MK_C32, &wm.w1c) && tile_map(c, w2i, MK_C32, &wm.w2c) &&
+                       tile_map(c, e1i, MK_C32, &wm.e1) && tile_map(c, e2i, MK_C32, &wm.e2) &&
+                       tile_map(c, c->g, MK_C32, &wm.g) &&
+                       (!phi_old || tile_map(c, phi_old, MK_C32, &wm.phi_old));
+  sr_status st = run_kernel(c, SR_KCLASS_WB_UPDATE, s, "k_wb_update", [&] {
+    return use_tma ? srk::launch_wb_tma(a, wm, s) : srk::launch_wb_update(a, s);
+  });
   if (st != SR_OK || !phi_old) return st;
   return run_kernel(c, SR_KCLASS_REDUCE, s, "k_reduce", [&] {
     return srk::launch_reduce(c->partials, c->n_tile32, 2, c->red, s);
@@ -571,11 +626,11 @@ sr_status enqueue_iteration(sr_ctx* c, cudaStream_t s, int p, bool check) {
   const int q = 1 - p;
   for (int it = 0; it < c->prm.inner_S; ++it) {
     const float* in = it == 0 ? c->phi[p] : c->phi[q];
-    sr_status st = enqueue_phi_step(c, s, in, c->w1[p], c->w2[p], c->b1, c->b2, c->phi[q], nullptr);
+    sr_status st = enqueue_phi_step(c, s, in, c->w1[p], c->w2[p], c->e1, c->e2, c->phi[q], nullptr);
     if (st != SR_OK) return st;
   }
-  return enqueue_wb(c, s, c->phi[q], c->w1[p], c->w2[p], c->b1, c->b2, c->w1[q], c->w2[q], c->b1,
-                    c->b2, check ? c->phi[p] : nullptr);
+  return enqueue_wb(c, s, c->phi[q], c->w1[p], c->w2[p], c->e1, c->e2, c->w1[q], c->w2[q], c->e1,
+                    c->e2, check ? c->phi[p] : nullptr);
 }
 
 void drop_graphs(sr_ctx* c) {
@@ -682,7 +737,7 @@ void sr_destroy(sr_ctx* c) {
   if (!c) return;
   drop_graphs(c);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
-  void* bufs[] = {c->phi[0], c->phi[1], c->w1[0], c->w1[1], c->w2[0], c->w2[1], c->b1, c->b2,
+  void* bufs[] = {c->phi[0], c->phi[1], c->w1[0], c->w1[1], c->w2[0], c->w2[1], c->e1, c->e2,
                   c->g, c->tmp1, c->tmp2, c->stage, c->G, c->mask_dev, c->X, c->tw_row, c->tw_col,
                   c->tw_n, c->aM, c->aN, c->partials, c->red, c->err_dev,
                   c->tws[0], c->tws[1], c->tws[2], c->tws[3]};
@@ -769,7 +824,7 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
 
   const size_t P = (size_t)H * W;
   float** planes[] = {&c->phi[0], &c->phi[1], &c->w1[0], &c->w1[1], &c->w2[0], &c->w2[1],
-                      &c->b1,     &c->b2,     &c->g,     &c->tmp1,  &c->tmp2,  &c->stage,
+                      &c->e1,     &c->e2,     &c->g,     &c->tmp1,  &c->tmp2,  &c->stage,
                       &c->G};
   for (float** pl : planes) CREATE_CUDA(cudaMalloc((void**)pl, P * sizeof(float)));
   CREATE_CUDA(cudaMalloc((void**)&c->mask_dev, P));
@@ -813,6 +868,24 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   }
   CREATE_CUDA(cudaMalloc((void**)&c->err_dev, sizeof(int)));
   CREATE_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
+  if (H >= 64 && W >= 64 && tensor_map_encoder()) {
+    CUtensorMap tmp;
+    bool ok = true;
+    for (int p = 0; p < 2; ++p) {
+      ok = ok && tile_map(c, c->phi[p], MK_HALO, &tmp) && tile_map(c, c->w1[p], MK_HALO, &tmp) &&
+           tile_map(c, c->w2[p], MK_HALO, &tmp) && tile_map(c, c->phi[p], MK_C32, &tmp) &&
+           tile_map(c, c->w1[p], MK_C32, &tmp) && tile_map(c, c->w2[p], MK_C32, &tmp);
+    }
+    ok = ok && tile_map(c, c->e1, MK_B1UP, &tmp) && tile_map(c, c->e2, MK_B2LEFT, &tmp) &&
+         tile_map(c, c->e1, MK_C32, &tmp) && tile_map(c, c->e2, MK_C32, &tmp) &&
+         tile_map(c, c->g, MK_C32, &tmp);
+    c->own_maps = c->maps.size();
+    c->tile_tma = ok;
+    // the plain-load tile kernels measured faster on GB300 (k_prep 31.5 us vs
+    // 37.4 us at 2048^2); SR_TILE_TMA=1 selects the TMA-fed ones
+    const char* env = std::getenv("SR_TILE_TMA");
+    c->tile_tma_on = ok && env && env[0] == '1';
+  }
   c->fft2 = srk::fft2_supported(c->geo);
   if (c->fft2) {
     const int cb = srk::colsolve_tma_cb(H);
@@ -858,7 +931,7 @@ sr_status sr_set_phi(sr_ctx* c, const float* phi0, int ld) {
   SR_CUDA(c, cudaMemcpy2DAsync(c->phi[0], c->W * sizeof(float), phi0, (size_t)ld * sizeof(float),
                                c->W * sizeof(float), c->H, cudaMemcpyDeviceToDevice, c->stream));
   c->launches += 1;
-  SR_CUDA(c, srk::launch_init_wb(c->phi[0], c->w1[0], c->w2[0], c->b1, c->b2, c->geo, c->stream));
+  SR_CUDA(c, srk::launch_init_wb(c->phi[0], c->w1[0], c->w2[0], c->e1, c->e2, c->geo, c->stream));
   return SR_OK;
 }
 
@@ -929,11 +1002,16 @@ sr_status sr_get_phi(sr_ctx* c, float* phi, int ld) {
 sr_status sr_get_state(sr_ctx* c, float* phi, float* w1, float* w2, float* b1, float* b2) {
   if (!c) return SR_EINVAL;
   if (!phi || !w1 || !w2 || !b1 || !b2) return fail(c, SR_EINVAL, "NULL state pointer");
-  const size_t bytes = (size_t)c->H * c->W * sizeof(float);
-  const float* src[] = {c->phi[c->cur], c->w1[c->cur], c->w2[c->cur], c->b1, c->b2};
-  float* dst[] = {phi, w1, w2, b1, b2};
-  for (int t = 0; t < 5; ++t)
+  const size_t P = (size_t)c->H * c->W;
+  const size_t bytes = P * sizeof(float);
+  const float* src[] = {c->phi[c->cur], c->w1[c->cur], c->w2[c->cur]};
+  float* dst[] = {phi, w1, w2};
+  for (int t = 0; t < 3; ++t)
     SR_CUDA(c, cudaMemcpyAsync(dst[t], src[t], bytes, cudaMemcpyDeviceToDevice, c->stream));
+  // b = e + w
+  c->launches += 2;
+  SR_CUDA(c, srk::launch_axpb(c->e1, c->w1[c->cur], 1.f, b1, P, c->stream));
+  SR_CUDA(c, srk::launch_axpb(c->e2, c->w2[c->cur], 1.f, b2, P, c->stream));
   return SR_OK;
 }
 
@@ -941,12 +1019,17 @@ sr_status sr_set_state(sr_ctx* c, const float* phi, const float* w1, const float
                        const float* b1, const float* b2) {
   if (!c) return SR_EINVAL;
   if (!phi || !w1 || !w2 || !b1 || !b2) return fail(c, SR_EINVAL, "NULL state pointer");
-  const size_t bytes = (size_t)c->H * c->W * sizeof(float);
+  const size_t P = (size_t)c->H * c->W;
+  const size_t bytes = P * sizeof(float);
   c->cur = 0;
-  const float* src[] = {phi, w1, w2, b1, b2};
-  float* dst[] = {c->phi[0], c->w1[0], c->w2[0], c->b1, c->b2};
-  for (int t = 0; t < 5; ++t)
+  const float* src[] = {phi, w1, w2};
+  float* dst[] = {c->phi[0], c->w1[0], c->w2[0]};
+  for (int t = 0; t < 3; ++t)
     SR_CUDA(c, cudaMemcpyAsync(dst[t], src[t], bytes, cudaMemcpyDeviceToDevice, c->stream));
+  // e = b - w
+  c->launches += 2;
+  SR_CUDA(c, srk::launch_axpb(b1, c->w1[0], -1.f, c->e1, P, c->stream));
+  SR_CUDA(c, srk::launch_axpb(b2, c->w2[0], -1.f, c->e2, P, c->stream));
   return SR_OK;
 }
 
@@ -1015,7 +1098,11 @@ sr_status sr_phi_step(sr_ctx* c, const float* psi_in, const float* w1, const flo
   for (const void* ptr : {(const void*)psi_in, (const void*)w1, (const void*)w2, (const void*)b1,
                           (const void*)b2, (const void*)psi_out})
     if (!aligned16(ptr)) return fail(c, SR_EINVAL, "buffers must be 16-byte aligned");
-  return enqueue_phi_step(c, c->stream, psi_in, w1, w2, b1, b2, psi_out, nullptr);
+  const size_t P = (size_t)c->H * c->W;
+  c->launches += 2;
+  SR_CUDA(c, srk::launch_axpb(b1, w1, -1.f, c->tmp1, P, c->stream));  // e = b - w
+  SR_CUDA(c, srk::launch_axpb(b2, w2, -1.f, c->tmp2, P, c->stream));
+  return enqueue_phi_step(c, c->stream, psi_in, w1, w2, c->tmp1, c->tmp2, psi_out, nullptr);
 }
 
 sr_status sr_fft_solve(sr_ctx* c, const float* rhs, float* out) {
@@ -1037,8 +1124,16 @@ sr_status sr_w_b_update(sr_ctx* c, const float* phi1, const float* w1_in, const 
                           (const void*)b1_in, (const void*)b2_in, (const void*)w1_out,
                           (const void*)w2_out, (const void*)b1_out, (const void*)b2_out})
     if (!aligned16(ptr)) return fail(c, SR_EINVAL, "buffers must be 16-byte aligned");
-  return enqueue_wb(c, c->stream, phi1, w1_in, w2_in, b1_in, b2_in, w1_out, w2_out, b1_out,
-                    b2_out, nullptr);
+  const size_t P = (size_t)c->H * c->W;
+  c->launches += 4;
+  SR_CUDA(c, srk::launch_axpb(b1_in, w1_in, -1.f, c->tmp1, P, c->stream));  // e = b - w
+  SR_CUDA(c, srk::launch_axpb(b2_in, w2_in, -1.f, c->tmp2, P, c->stream));
+  sr_status st = enqueue_wb(c, c->stream, phi1, w1_in, w2_in, c->tmp1, c->tmp2, w1_out, w2_out,
+                            c->tmp1, c->tmp2, nullptr);
+  if (st != SR_OK) return st;
+  SR_CUDA(c, srk::launch_axpb(c->tmp1, w1_out, 1.f, b1_out, P, c->stream));  // b = e + w
+  SR_CUDA(c, srk::launch_axpb(c->tmp2, w2_out, 1.f, b2_out, P, c->stream));
+  return SR_OK;
 }
 
 sr_status sr_get_schedule(sr_ctx* c, sr_schedule* out) {

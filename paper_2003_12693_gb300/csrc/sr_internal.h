@@ -82,7 +82,8 @@ struct RowInvArgs {
   int T;
 };
 
-// Right-hand side of one inner step on 2-D tiles (window sum fused in).
+// Right-hand side of one inner step on 2-D tiles (window sum fused in).  The
+// Bregman variable is carried as e = b - w, so that div(b - w) needs only e.
 struct PrepArgs {
   Geo geo;
   Model mod;
@@ -90,12 +91,14 @@ struct PrepArgs {
   const float* g;
   const float* w1;
   const float* w2;
-  const float* b1;
-  const float* b2;
+  const float* e1;         // b1 - w1
+  const float* e2;         // b2 - w2
   float* G;                // increment right-hand side, H x W
+  int* err;                // device error flag (bounded waits), may be null
 };
 
-// w and b update with the repulsion window sum fused in.
+// w and b update with the repulsion window sum fused in; b is carried as
+// e = b - w on input and output.
 struct WBArgs {
   Geo geo;
   Model mod;
@@ -103,14 +106,26 @@ struct WBArgs {
   const float* g;
   const float* w1;         // w^k
   const float* w2;
-  const float* b1;         // b^k
-  const float* b2;
+  const float* e1;         // e^k = b^k - w^k
+  const float* e2;
   float* w1o;              // w^{k+1}
   float* w2o;
-  float* b1o;              // b^{k+1} (may alias b1)
-  float* b2o;
+  float* e1o;              // e^{k+1} = b^{k+1} - w^{k+1} (may alias e1)
+  float* e2o;
   const float* phi_old;    // phi^k for the stopping test, or nullptr
   double* partials;        // 2 doubles per 32 x 32 tile when phi_old != nullptr
+  int* err;                // device error flag (bounded waits), may be null
+};
+
+// 2-D float32 tensor maps (H x W planes) of the TMA tile kernels.  Boxes:
+// psi, w1, w2 (32 + 2 tile_halo_x(R)) x (32 + 2 tile_halo_y(R)) columns x
+// rows; prep: b1 32 x 33, b2 36 x 32, g 32 x 32; w/b update: b1, b2, g,
+// phi_old 32 x 32.
+struct PrepMaps {
+  CUtensorMap psi, w1, w2, e1, e2, g;   // e1: 32 x 33 (row above), e2: 36 x 32 (columns to the left)
+};
+struct WBMaps {
+  CUtensorMap psi, w1, w2, w1c, w2c, e1, e2, g, phi_old;  // w1, w2 halo; the rest 32 x 32
 };
 
 struct RepArgs {
@@ -154,13 +169,21 @@ cudaError_t launch_colsolve(const ColArgs& a, cudaStream_t s);
 cudaError_t launch_rowinv(const RowInvArgs& a, int mode, int nthreads, cudaStream_t s);
 cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s);
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
+cudaError_t launch_prep_tma(const PrepArgs& a, const PrepMaps& tm, cudaStream_t s);
+cudaError_t launch_wb_tma(const WBArgs& a, const WBMaps& tm, cudaStream_t s);
+size_t tile_tma_smem(int R);
+int tile_halo_x(int R);
+int tile_halo_y(int R);
 int tile32_blocks(const Geo& geo);  // CTAs of the 32 x 32 tile kernels
 cudaError_t launch_repulsion(const RepArgs& a, cudaStream_t s);
 cudaError_t launch_energy(const EnergyArgs& a, cudaStream_t s);
 cudaError_t launch_reduce(const double* partials, int nblocks, int ncomp, double* out,
                           cudaStream_t s);
-cudaError_t launch_init_wb(const float* phi, float* w1, float* w2, float* b1, float* b2,
+cudaError_t launch_init_wb(const float* phi, float* w1, float* w2, float* e1, float* e2,
                            Geo geo, cudaStream_t s);
+// out = a + sign * b elementwise over n floats (b <-> e conversions)
+cudaError_t launch_axpb(const float* a, const float* b, float sign, float* out, size_t n,
+                        cudaStream_t s);
 cudaError_t launch_mask(const float* phi, unsigned char* mask, int ld, Geo geo,
                         cudaStream_t s);
 cudaError_t launch_edge(const EdgeArgs& a, const float* f, int ld, float* tmp1, float* tmp2,

@@ -20,7 +20,10 @@
 // CUDA-core arithmetic, shared-memory staging, coalesced global access.
 #include <math.h>
 
+#include <algorithm>
+
 #include "sr_internal.h"
+#include "sr_tma.cuh"
 
 // every supported repulsion window half width R
 #define SR_FOR_R(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
@@ -609,27 +612,14 @@ __device__ __forceinline__ int stage4(float* dst, const float* __restrict__ src,
   return any;
 }
 
-// With psi staged: stage w, form u = h(psi) w and return the window sums of
-// the thread's four pixels (zero for tiles without band pixels).
+// With psi and w in shared memory ([SH][SW] planes, zero outside the image):
+// form u = h(psi) w and return the window sums of the thread's four pixels.
 template <int R>
-__device__ __forceinline__ void tile_window(float* sm, const Geo& geo, const Model& m,
-                                            const float* __restrict__ w1,
-                                            const float* __restrict__ w2, int i0, int j0,
-                                            bool band, float (&v1)[4], float (&v2)[4]) {
+__device__ __forceinline__ void window_sum(const float* t_psi, const float* t_w1,
+                                           const float* t_w2, float* t_u1, float* t_u2,
+                                           float* t_V1, float* t_V2, const Model& m,
+                                           float (&v1)[4], float (&v2)[4]) {
   using TL = Tile<R>;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) v1[q] = v2[q] = 0.f;
-  if (!band) return;  // uniform across the block
-  float* t_psi = sm;
-  float* t_u1 = sm + TL::NP;
-  float* t_u2 = sm + 2 * TL::NP;
-  float* t_w1 = sm + 3 * TL::NP;
-  float* t_w2 = sm + 4 * TL::NP;
-  float* t_V1 = sm + 5 * TL::NP;
-  float* t_V2 = t_V1 + kT * TL::SW;
-  stage4<R, false>(t_w1, w1, geo, i0, j0, m);
-  stage4<R, false>(t_w2, w2, geo, i0, j0, m);
-  __syncthreads();
   const int tid = threadIdx.y * kTBX + threadIdx.x;
   for (int idx = tid; idx < TL::NP; idx += kTN) {
     const float x = t_psi[idx];
@@ -676,6 +666,8 @@ __device__ __forceinline__ void tile_window(float* sm, const Geo& geo, const Mod
   // across the row: outputs c .. c+3 take inputs c - R .. c + 3 + R
   const int r = threadIdx.y, c = 4 * threadIdx.x + TL::HX;
 #pragma unroll
+  for (int q = 0; q < 4; ++q) v1[q] = v2[q] = 0.f;
+#pragma unroll
   for (int t = 0; t < 4 + 2 * R; ++t) {
     const float x1 = t_V1[r * TL::SW + c - R + t];
     const float x2 = t_V2[r * TL::SW + c - R + t];
@@ -690,7 +682,72 @@ __device__ __forceinline__ void tile_window(float* sm, const Geo& geo, const Mod
   }
 }
 
+// With psi staged: stage w, then the window sums of the thread's four pixels
+// (zero for tiles without band pixels).
+template <int R>
+__device__ __forceinline__ void tile_window(float* sm, const Geo& geo, const Model& m,
+                                            const float* __restrict__ w1,
+                                            const float* __restrict__ w2, int i0, int j0,
+                                            bool band, float (&v1)[4], float (&v2)[4]) {
+  using TL = Tile<R>;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v1[q] = v2[q] = 0.f;
+  if (!band) return;  // uniform across the block
+  float* t_w1 = sm + 3 * TL::NP;
+  float* t_w2 = sm + 4 * TL::NP;
+  stage4<R, false>(t_w1, w1, geo, i0, j0, m);
+  stage4<R, false>(t_w2, w2, geo, i0, j0, m);
+  __syncthreads();
+  float* t_V1 = sm + 5 * TL::NP;
+  window_sum<R>(sm, t_w1, t_w2, sm + TL::NP, sm + 2 * TL::NP, t_V1, t_V1 + kT * TL::SW, m, v1,
+                v2);
+}
+
 size_t tile32_smem(int R) { return (size_t)tile32_floats(R) * sizeof(float); }
+
+// G = tau [ mu (div e + Lap psi) - gamma g |w| delta'(psi) + alpha g delta(psi)
+//           + 2 beta h'(psi) (w . v) ] at one pixel (the band terms only where
+// |psi| < l + eps; e = b - w, div the backward divergence).
+__device__ __forceinline__ float rhs_point(const Model& m, float x, float up, float dn, float lf,
+                                           float rt, float e1, float e1u, float e2, float e2l,
+                                           float w1, float w2, float g, float v1, float v2) {
+  const float lap = (up + dn) + (lf + rt) - 4.f * x;
+  const float dv = (e1 - e1u) + (e2 - e2l);
+  float force = m.mu * (dv + lap);
+  if (in_band(x, m)) {
+    const float wn = sqrtf(w1 * w1 + w2 * w2);
+    force += -m.gamma * g * wn * dpeps(x, m.eps) + m.alpha * g * deps(x, m.eps) +
+             2.f * m.beta * band_hp(x, m) * (w1 * v1 + w2 * v2);
+  }
+  return m.tau * force;
+}
+
+// Eqs. (41), (42), (40), (23) at one pixel: B = grad phi + b + (2 beta/mu) h v,
+// t = (gamma/mu) g delta(phi); w = B/|B| if |B| > t else 0; b' = b + grad phi - w;
+// returns w' and e' = b' - w'.
+__device__ __forceinline__ void wb_point(const Model& m, float x, float d1, float d2, float b1,
+                                         float b2, float g, float v1, float v2, float& wo1,
+                                         float& wo2, float& eo1, float& eo2) {
+  float Bv1 = d1 + b1;
+  float Bv2 = d2 + b2;
+  float thr = 0.f;
+  if (in_band(x, m)) {
+    const float h = band_h(x, m);
+    Bv1 = fmaf(m.beta2_mu * h, v1, Bv1);
+    Bv2 = fmaf(m.beta2_mu * h, v2, Bv2);
+    thr = m.gamma_mu * g * deps(x, m.eps);
+  }
+  const float nB = sqrtf(Bv1 * Bv1 + Bv2 * Bv2);
+  float W1 = 0.f, W2 = 0.f;
+  if (nB > thr) {
+    W1 = Bv1 / nB;
+    W2 = Bv2 / nB;
+  }
+  wo1 = W1;
+  wo2 = W2;
+  eo1 = ((b1 + d1) - W1) - W1;
+  eo2 = ((b2 + d2) - W2) - W2;
+}
 
 // Increment right-hand side of one inner step, Eq. (37) in the form
 // G = tau [ -gamma g |w| delta'(psi) + alpha g delta(psi) + 2 beta h'(psi) (w . v)
@@ -711,10 +768,8 @@ __global__ void __launch_bounds__(kTN, 4) k_prep(const PrepArgs a) {
   const size_t o = (size_t)i * N + j;
   const size_t ou = (size_t)(i > 0 ? i - 1 : M - 1) * N + j;
   const size_t ol = (size_t)i * N + (j > 0 ? j - 1 : N - 1);
-  const float4 W1 = ld4(a.w1 + o), W2 = ld4(a.w2 + o), B1 = ld4(a.b1 + o), B2 = ld4(a.b2 + o);
-  const float4 W1u = ld4(a.w1 + ou), B1u = ld4(a.b1 + ou);
-  const float w2l = __ldg(a.w2 + ol), b2l = __ldg(a.b2 + ol);
-  const float4 G4 = ld4(a.g + o);
+  const float4 E1 = ld4(a.e1 + o), E2 = ld4(a.e2 + o), E1u = ld4(a.e1 + ou);
+  const float e2l = __ldg(a.e2 + ol);
   const float* t_psi = smem_f;
   const int q = (threadIdx.y + TL::HY) * TL::SW + 4 * threadIdx.x + TL::HX;
   const float4 X = *reinterpret_cast<const float4*>(t_psi + q);
@@ -723,27 +778,23 @@ __global__ void __launch_bounds__(kTN, 4) k_prep(const PrepArgs a) {
                               : ld4(a.psi + j);
   const float LF = j > 0 ? t_psi[q - 1] : __ldg(a.psi + ol);
   const float RT = j + 4 < N ? t_psi[q + 4] : __ldg(a.psi + (size_t)i * N);
+  float4 W1 = make_float4(0.f, 0.f, 0.f, 0.f), W2 = W1, G4 = W1;
+  if (band) {  // w and g enter only through the narrow-band terms
+    W1 = ld4(a.w1 + o);
+    W2 = ld4(a.w2 + o);
+    G4 = ld4(a.g + o);
+  }
   const float x[4] = {X.x, X.y, X.z, X.w};
   const float up[4] = {UP.x, UP.y, UP.z, UP.w}, dn[4] = {DN.x, DN.y, DN.z, DN.w};
   const float lf[4] = {LF, X.x, X.y, X.z}, rt[4] = {X.y, X.z, X.w, RT};
+  const float e1[4] = {E1.x, E1.y, E1.z, E1.w}, e2[4] = {E2.x, E2.y, E2.z, E2.w};
+  const float e1u[4] = {E1u.x, E1u.y, E1u.z, E1u.w}, e2l4[4] = {e2l, E2.x, E2.y, E2.z};
   const float w1[4] = {W1.x, W1.y, W1.z, W1.w}, w2[4] = {W2.x, W2.y, W2.z, W2.w};
-  const float b1[4] = {B1.x, B1.y, B1.z, B1.w}, b2[4] = {B2.x, B2.y, B2.z, B2.w};
-  const float w1u[4] = {W1u.x, W1u.y, W1u.z, W1u.w}, b1u[4] = {B1u.x, B1u.y, B1u.z, B1u.w};
-  const float w2l4[4] = {w2l, W2.x, W2.y, W2.z}, b2l4[4] = {b2l, B2.x, B2.y, B2.z};
   const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
   float out[4];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const float lap = (up[t] + dn[t]) + (lf[t] + rt[t]) - 4.f * x[t];
-    const float dv = ((b1[t] - w1[t]) - (b1u[t] - w1u[t])) + ((b2[t] - w2[t]) - (b2l4[t] - w2l4[t]));
-    float force = m.mu * (dv + lap);
-    if (in_band(x[t], m)) {
-      const float wn = sqrtf(w1[t] * w1[t] + w2[t] * w2[t]);
-      force += -m.gamma * gg[t] * wn * dpeps(x[t], m.eps) + m.alpha * gg[t] * deps(x[t], m.eps) +
-               2.f * m.beta * band_hp(x[t], m) * (w1[t] * v1[t] + w2[t] * v2[t]);
-    }
-    out[t] = m.tau * force;
-  }
+  for (int t = 0; t < 4; ++t) out[t] = rhs_point(m, x[t], up[t], dn[t], lf[t], rt[t], e1[t], e1u[t],
+                                                 e2[t], e2l4[t], w1[t], w2[t], gg[t], v1[t], v2[t]);
   st4(a.G + o, make_float4(out[0], out[1], out[2], out[3]));
 }
 
@@ -764,7 +815,8 @@ __global__ void __launch_bounds__(kTN, 4) k_wb_update(const WBArgs a) {
   double part[2] = {0.0, 0.0};
   if (i < M && j < N) {
     const size_t o = (size_t)i * N + j;
-    const float4 B1 = ld4(a.b1 + o), B2 = ld4(a.b2 + o), G4 = ld4(a.g + o);
+    const float4 E1 = ld4(a.e1 + o), E2 = ld4(a.e2 + o), W1 = ld4(a.w1 + o), W2 = ld4(a.w2 + o);
+    const float4 G4 = band ? ld4(a.g + o) : make_float4(0.f, 0.f, 0.f, 0.f);
     const float* t_psi = smem_f;
     const int q = (threadIdx.y + TL::HY) * TL::SW + 4 * threadIdx.x + TL::HX;
     const float4 X = *reinterpret_cast<const float4*>(t_psi + q);
@@ -773,37 +825,18 @@ __global__ void __launch_bounds__(kTN, 4) k_wb_update(const WBArgs a) {
     const float RT = j + 4 < N ? t_psi[q + 4] : __ldg(a.phi1 + (size_t)i * N);
     const float x[4] = {X.x, X.y, X.z, X.w};
     const float dn[4] = {DN.x, DN.y, DN.z, DN.w}, rt[4] = {X.y, X.z, X.w, RT};
-    const float b1[4] = {B1.x, B1.y, B1.z, B1.w}, b2[4] = {B2.x, B2.y, B2.z, B2.w};
+    const float b1[4] = {E1.x + W1.x, E1.y + W1.y, E1.z + W1.z, E1.w + W1.w};
+    const float b2[4] = {E2.x + W2.x, E2.y + W2.y, E2.z + W2.z, E2.w + W2.w};
     const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
-    float wo1[4], wo2[4], bo1[4], bo2[4];
+    float wo1[4], wo2[4], eo1[4], eo2[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const float d1 = dn[t] - x[t];
-      const float d2 = rt[t] - x[t];
-      float Bv1 = d1 + b1[t];
-      float Bv2 = d2 + b2[t];
-      float thr = 0.f;
-      if (in_band(x[t], m)) {
-        const float h = band_h(x[t], m);
-        Bv1 = fmaf(m.beta2_mu * h, v1[t], Bv1);
-        Bv2 = fmaf(m.beta2_mu * h, v2[t], Bv2);
-        thr = m.gamma_mu * gg[t] * deps(x[t], m.eps);
-      }
-      const float nB = sqrtf(Bv1 * Bv1 + Bv2 * Bv2);
-      float W1 = 0.f, W2 = 0.f;
-      if (nB > thr) {
-        W1 = Bv1 / nB;
-        W2 = Bv2 / nB;
-      }
-      wo1[t] = W1;
-      wo2[t] = W2;
-      bo1[t] = (b1[t] + d1) - W1;
-      bo2[t] = (b2[t] + d2) - W2;
-    }
+    for (int t = 0; t < 4; ++t)
+      wb_point(m, x[t], dn[t] - x[t], rt[t] - x[t], b1[t], b2[t], gg[t], v1[t], v2[t], wo1[t],
+               wo2[t], eo1[t], eo2[t]);
     st4(a.w1o + o, make_float4(wo1[0], wo1[1], wo1[2], wo1[3]));
     st4(a.w2o + o, make_float4(wo2[0], wo2[1], wo2[2], wo2[3]));
-    st4(a.b1o + o, make_float4(bo1[0], bo1[1], bo1[2], bo1[3]));
-    st4(a.b2o + o, make_float4(bo2[0], bo2[1], bo2[2], bo2[3]));
+    st4(a.e1o + o, make_float4(eo1[0], eo1[1], eo1[2], eo1[3]));
+    st4(a.e2o + o, make_float4(eo2[0], eo2[1], eo2[2], eo2[3]));
     if (a.phi_old) {
       const float4 P = ld4(a.phi_old + o);
       const float po[4] = {P.x, P.y, P.z, P.w};
@@ -816,6 +849,219 @@ __global__ void __launch_bounds__(kTN, 4) k_wb_update(const WBArgs a) {
     }
   }
   if (a.phi_old) block_sum_store<2>(part, a.partials + 2 * (blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+// ---------------------------------------------------------------------------
+// TMA versions of the two tile kernels.  One thread issues 2-D box loads of
+// every plane the tile needs (zero fill outside the image gives the window
+// sum's dropped terms); they complete on an mbarrier, and the block then
+// works from shared memory only.  Boxes: psi, w1, w2 with the (HX, HY) halo;
+// b1 with the row above (33 x 32), b2 with four columns to the left
+// (32 x 36), g and the old phi 32 x 32.  k_wb_tma loads w only for tiles with
+// narrow-band pixels (second phase).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int a32(int n) { return (n + 31) / 32 * 32; }
+
+template <int R>
+struct TileT {
+  using TL = Tile<R>;
+  static constexpr int PSI = 0;
+  static constexpr int W1 = PSI + a32(TL::NP);
+  static constexpr int W2 = W1 + a32(TL::NP);
+  static constexpr int B1 = W2 + a32(TL::NP);    // 33 rows x 32
+  static constexpr int B2 = B1 + a32(33 * 32);    // 32 rows x 36
+  static constexpr int GG = B2 + a32(32 * 36);    // 32 x 32
+  static constexpr int PO = GG + a32(32 * 32);    // 32 x 32 (old phi)
+  static constexpr int U1 = PO + a32(32 * 32);
+  static constexpr int U2 = U1 + a32(TL::NP);
+  static constexpr int V1 = U2 + a32(TL::NP);
+  static constexpr int V2 = V1 + a32(kT * TL::SW);
+  static constexpr int BAR = V2 + a32(kT * TL::SW);
+  static constexpr int FLOATS = BAR + 8;  // two mbarriers
+};
+
+__device__ __forceinline__ float* align128(unsigned char* p) {
+  return reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(p) + 127) & ~static_cast<uintptr_t>(127));
+}
+
+template <int R>
+__global__ void __launch_bounds__(kTN, 3) k_prep_tma(const PrepArgs a, const __grid_constant__ PrepMaps tm) {
+  using TL = Tile<R>;
+  using TT = TileT<R>;
+  extern __shared__ __align__(16) unsigned char smem_tt[];
+  float* sm = align128(smem_tt);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TT::BAR);
+  const int tid = threadIdx.y * kTBX + threadIdx.x;
+  const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
+  const int M = a.geo.M, N = a.geo.N;
+  const Model& m = a.mod;
+  if (tid == 0) {
+    tma::mbar_init(&bar[0], 1);
+    tma::mbar_init(&bar[1], 1);
+    tma::mbar_init_fence();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    constexpr uint32_t bytes = 4u * (TL::NP + 33 * 32 + 32 * 36);
+    tma::mbar_expect_tx(&bar[0], bytes);
+    tma::load_2d(sm + TT::PSI, &tm.psi, j0 - TL::HX, i0 - TL::HY, &bar[0]);
+    tma::load_2d(sm + TT::B1, &tm.e1, j0, i0 - 1, &bar[0]);
+    tma::load_2d(sm + TT::B2, &tm.e2, j0 - 4, i0, &bar[0]);
+  }
+  bool ok = tma::mbar_wait(&bar[0], 0);
+  if (!__syncthreads_and(ok)) {
+    if (tid == 0) tma::on_timeout(&bar[0], 0, a.err);
+    return;
+  }
+  const float* t_psi = sm + TT::PSI;
+  int any = 0;
+  for (int idx = tid; idx < TL::NP; idx += kTN) any |= in_band(t_psi[idx], m);
+  const bool band = __syncthreads_or(any) != 0;
+  float v1[4] = {0.f, 0.f, 0.f, 0.f}, v2[4] = {0.f, 0.f, 0.f, 0.f};
+  if (band) {
+    if (tid == 0) {
+      tma::mbar_expect_tx(&bar[1], 4u * (2 * TL::NP + 32 * 32));
+      tma::load_2d(sm + TT::W1, &tm.w1, j0 - TL::HX, i0 - TL::HY, &bar[1]);
+      tma::load_2d(sm + TT::W2, &tm.w2, j0 - TL::HX, i0 - TL::HY, &bar[1]);
+      tma::load_2d(sm + TT::GG, &tm.g, j0, i0, &bar[1]);
+    }
+    ok = tma::mbar_wait(&bar[1], 0);
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) tma::on_timeout(&bar[1], 0, a.err);
+      return;
+    }
+    window_sum<R>(t_psi, sm + TT::W1, sm + TT::W2, sm + TT::U1, sm + TT::U2, sm + TT::V1,
+                  sm + TT::V2, m, v1, v2);
+  }
+  const int ty = threadIdx.y, tx = threadIdx.x;
+  const int i = i0 + ty, j = j0 + 4 * tx;
+  if (i >= M || j >= N) return;
+  const int q = (ty + TL::HY) * TL::SW + 4 * tx + TL::HX;
+  auto f4 = [&](int off) { return *reinterpret_cast<const float4*>(sm + off); };
+  const float4 X = f4(TT::PSI + q);
+  const float4 UP = i > 0 ? f4(TT::PSI + q - TL::SW) : ld4(a.psi + (size_t)(M - 1) * N + j);
+  const float4 DN = i < M - 1 ? f4(TT::PSI + q + TL::SW) : ld4(a.psi + j);
+  const float LF = j > 0 ? sm[TT::PSI + q - 1] : __ldg(a.psi + (size_t)i * N + N - 1);
+  const float RT = j + 4 < N ? sm[TT::PSI + q + 4] : __ldg(a.psi + (size_t)i * N);
+  const float4 E1 = f4(TT::B1 + (ty + 1) * 32 + 4 * tx);
+  const float4 E1u = i > 0 ? f4(TT::B1 + ty * 32 + 4 * tx) : ld4(a.e1 + (size_t)(M - 1) * N + j);
+  const float4 E2 = f4(TT::B2 + ty * 36 + 4 + 4 * tx);
+  const float e2l = j > 0 ? sm[TT::B2 + ty * 36 + 3 + 4 * tx] : __ldg(a.e2 + (size_t)i * N + N - 1);
+  float4 W1 = make_float4(0.f, 0.f, 0.f, 0.f), W2 = W1, G4 = W1;
+  if (band) {
+    W1 = f4(TT::W1 + q);
+    W2 = f4(TT::W2 + q);
+    G4 = f4(TT::GG + ty * 32 + 4 * tx);
+  }
+  const float x[4] = {X.x, X.y, X.z, X.w};
+  const float up[4] = {UP.x, UP.y, UP.z, UP.w}, dn[4] = {DN.x, DN.y, DN.z, DN.w};
+  const float lf[4] = {LF, X.x, X.y, X.z}, rt[4] = {X.y, X.z, X.w, RT};
+  const float e1[4] = {E1.x, E1.y, E1.z, E1.w}, e2[4] = {E2.x, E2.y, E2.z, E2.w};
+  const float e1u[4] = {E1u.x, E1u.y, E1u.z, E1u.w}, e2l4[4] = {e2l, E2.x, E2.y, E2.z};
+  const float w1[4] = {W1.x, W1.y, W1.z, W1.w}, w2[4] = {W2.x, W2.y, W2.z, W2.w};
+  const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
+  float out[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) out[t] = rhs_point(m, x[t], up[t], dn[t], lf[t], rt[t], e1[t], e1u[t],
+                                                 e2[t], e2l4[t], w1[t], w2[t], gg[t], v1[t], v2[t]);
+  st4(a.G + (size_t)i * N + j, make_float4(out[0], out[1], out[2], out[3]));
+}
+
+template <int R>
+__global__ void __launch_bounds__(kTN, 3) k_wb_tma(const WBArgs a, const __grid_constant__ WBMaps tm) {
+  using TL = Tile<R>;
+  using TT = TileT<R>;
+  extern __shared__ __align__(16) unsigned char smem_tt[];
+  float* sm = align128(smem_tt);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TT::BAR);
+  const int tid = threadIdx.y * kTBX + threadIdx.x;
+  const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
+  const int M = a.geo.M, N = a.geo.N;
+  const Model& m = a.mod;
+  const bool chk = a.phi_old != nullptr;
+  if (tid == 0) {
+    tma::mbar_init(&bar[0], 1);
+    tma::mbar_init(&bar[1], 1);
+    tma::mbar_init_fence();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t bytes = 4u * (TL::NP + 4 * 32 * 32 + (chk ? 32 * 32 : 0));
+    tma::mbar_expect_tx(&bar[0], bytes);
+    tma::load_2d(sm + TT::PSI, &tm.psi, j0 - TL::HX, i0 - TL::HY, &bar[0]);
+    tma::load_2d(sm + TT::B1, &tm.e1, j0, i0, &bar[0]);
+    tma::load_2d(sm + TT::B2, &tm.e2, j0, i0, &bar[0]);
+    tma::load_2d(sm + TT::U1, &tm.w1c, j0, i0, &bar[0]);
+    tma::load_2d(sm + TT::U2, &tm.w2c, j0, i0, &bar[0]);
+    if (chk) tma::load_2d(sm + TT::PO, &tm.phi_old, j0, i0, &bar[0]);
+  }
+  bool ok = tma::mbar_wait(&bar[0], 0);
+  if (!__syncthreads_and(ok)) {
+    if (tid == 0) tma::on_timeout(&bar[0], 0, a.err);
+    return;
+  }
+  const float* t_psi = sm + TT::PSI;
+  int any = 0;
+  for (int idx = tid; idx < TL::NP; idx += kTN) any |= in_band(t_psi[idx], m);
+  const bool band = __syncthreads_or(any) != 0;
+  const int ty = threadIdx.y, tx = threadIdx.x;
+  const int c32 = ty * 32 + 4 * tx;
+  // w^k of the thread's pixels before the window sum reuses U1/U2
+  auto f4 = [&](int off) { return *reinterpret_cast<const float4*>(sm + off); };
+  const float4 W1 = f4(TT::U1 + c32), W2 = f4(TT::U2 + c32);
+  float v1[4] = {0.f, 0.f, 0.f, 0.f}, v2[4] = {0.f, 0.f, 0.f, 0.f};
+  if (band) {
+    __syncthreads();  // every thread holds its w before U1/U2 are overwritten
+    if (tid == 0) {
+      tma::mbar_expect_tx(&bar[1], 4u * (2 * TL::NP + 32 * 32));
+      tma::load_2d(sm + TT::W1, &tm.w1, j0 - TL::HX, i0 - TL::HY, &bar[1]);
+      tma::load_2d(sm + TT::W2, &tm.w2, j0 - TL::HX, i0 - TL::HY, &bar[1]);
+      tma::load_2d(sm + TT::GG, &tm.g, j0, i0, &bar[1]);
+    }
+    ok = tma::mbar_wait(&bar[1], 0);
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) tma::on_timeout(&bar[1], 0, a.err);
+      return;
+    }
+    window_sum<R>(t_psi, sm + TT::W1, sm + TT::W2, sm + TT::U1, sm + TT::U2, sm + TT::V1,
+                  sm + TT::V2, m, v1, v2);
+  }
+  const int i = i0 + ty, j = j0 + 4 * tx;
+  double part[2] = {0.0, 0.0};
+  if (i < M && j < N) {
+    const size_t o = (size_t)i * N + j;
+    const int q = (ty + TL::HY) * TL::SW + 4 * tx + TL::HX;
+    const float4 X = f4(TT::PSI + q);
+    const float4 DN = i < M - 1 ? f4(TT::PSI + q + TL::SW) : ld4(a.phi1 + j);
+    const float RT = j + 4 < N ? sm[TT::PSI + q + 4] : __ldg(a.phi1 + (size_t)i * N);
+    const float4 E1 = f4(TT::B1 + c32), E2 = f4(TT::B2 + c32);
+    const float4 G4 = band ? f4(TT::GG + c32) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float x[4] = {X.x, X.y, X.z, X.w};
+    const float dn[4] = {DN.x, DN.y, DN.z, DN.w}, rt[4] = {X.y, X.z, X.w, RT};
+    const float b1[4] = {E1.x + W1.x, E1.y + W1.y, E1.z + W1.z, E1.w + W1.w};
+    const float b2[4] = {E2.x + W2.x, E2.y + W2.y, E2.z + W2.z, E2.w + W2.w};
+    const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
+    float wo1[4], wo2[4], eo1[4], eo2[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      wb_point(m, x[t], dn[t] - x[t], rt[t] - x[t], b1[t], b2[t], gg[t], v1[t], v2[t], wo1[t],
+               wo2[t], eo1[t], eo2[t]);
+    st4(a.w1o + o, make_float4(wo1[0], wo1[1], wo1[2], wo1[3]));
+    st4(a.w2o + o, make_float4(wo2[0], wo2[1], wo2[2], wo2[3]));
+    st4(a.e1o + o, make_float4(eo1[0], eo1[1], eo1[2], eo1[3]));
+    st4(a.e2o + o, make_float4(eo2[0], eo2[1], eo2[2], eo2[3]));
+    if (chk) {
+      const float4 P = f4(TT::PO + c32);
+      const float po[4] = {P.x, P.y, P.z, P.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const double df = (double)x[t] - (double)po[t];
+        part[0] += df * df;
+        part[1] += (double)po[t] * (double)po[t];
+      }
+    }
+  }
+  if (chk) block_sum_store<2>(part, a.partials + 2 * (blockIdx.y * gridDim.x + blockIdx.x));
 }
 
 __global__ void __launch_bounds__(kTileX* kTileY) k_repulsion(const RepArgs a) {
@@ -897,18 +1143,27 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ parti
     for (int c = 0; c < ncomp; ++c) out[c] = red[c][0];
 }
 
-// Alg. 1 initialisation: w = grad phi (forward, periodic), b = 0.
+// Alg. 1 initialisation: w = grad phi (forward, periodic), b = 0, i.e. e = -w.
 __global__ void k_init_wb(const float* __restrict__ phi, float* __restrict__ w1,
-                          float* __restrict__ w2, float* __restrict__ b1, float* __restrict__ b2,
+                          float* __restrict__ w2, float* __restrict__ e1, float* __restrict__ e2,
                           Geo geo) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
   if (j >= geo.N) return;
   const size_t o = (size_t)i * geo.N + j;
   const float x = phi[o];
-  w1[o] = phi[(size_t)(i == geo.M - 1 ? 0 : i + 1) * geo.N + j] - x;
-  w2[o] = phi[(size_t)i * geo.N + (j == geo.N - 1 ? 0 : j + 1)] - x;
-  b1[o] = 0.f;
-  b2[o] = 0.f;
+  const float d1 = phi[(size_t)(i == geo.M - 1 ? 0 : i + 1) * geo.N + j] - x;
+  const float d2 = phi[(size_t)i * geo.N + (j == geo.N - 1 ? 0 : j + 1)] - x;
+  w1[o] = d1;
+  w2[o] = d2;
+  e1[o] = -d1;
+  e2[o] = -d2;
+}
+
+__global__ void k_axpb(const float* __restrict__ a, const float* __restrict__ b, float sign,
+                       float* __restrict__ out, size_t n) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+       q += (size_t)gridDim.x * blockDim.x)
+    out[q] = a[q] + sign * b[q];
 }
 
 __global__ void k_mask(const float* __restrict__ phi, unsigned char* __restrict__ mask, int ld,
@@ -1005,9 +1260,11 @@ cudaError_t configure_kernels() {
   if ((e = allow_big_smem(k_colsolve))) return e;
   if ((e = allow_big_smem(k_rowinv<kInvADD>))) return e;
   if ((e = allow_big_smem(k_rowinv<kInvSTORE>))) return e;
-#define SR_CASE(r)                                                 \
-  if ((e = allow_big_smem(k_prep<r>)) != cudaSuccess) return e;    \
-  if ((e = allow_big_smem(k_wb_update<r>)) != cudaSuccess) return e;
+#define SR_CASE(r)                                                   \
+  if ((e = allow_big_smem(k_prep<r>)) != cudaSuccess) return e;      \
+  if ((e = allow_big_smem(k_wb_update<r>)) != cudaSuccess) return e; \
+  if ((e = allow_big_smem(k_prep_tma<r>)) != cudaSuccess) return e;  \
+  if ((e = allow_big_smem(k_wb_tma<r>)) != cudaSuccess) return e;
   SR_FOR_R(SR_CASE)
 #undef SR_CASE
   return cudaSuccess;
@@ -1057,6 +1314,45 @@ cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+size_t tile_tma_smem(int R) {
+  switch (R) {
+#define SR_CASE(r) \
+  case r: return (size_t)TileT<r>::FLOATS * sizeof(float) + 128;
+    SR_FOR_R(SR_CASE)
+#undef SR_CASE
+  }
+  return 0;
+}
+
+int tile_halo_x(int R) { return R > 4 ? 8 : 4; }
+int tile_halo_y(int R) { return R > 1 ? R : 1; }
+
+cudaError_t launch_prep_tma(const PrepArgs& a, const PrepMaps& tm, cudaStream_t s) {
+  const dim3 g = tile32_grid(a.geo), b(kTBX, kTBY);
+  const size_t sm = tile_tma_smem(a.mod.R);
+  switch (a.mod.R) {
+#define SR_CASE(r) \
+  case r: k_prep_tma<r><<<g, b, sm, s>>>(a, tm); break;
+    SR_FOR_R(SR_CASE)
+#undef SR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wb_tma(const WBArgs& a, const WBMaps& tm, cudaStream_t s) {
+  const dim3 g = tile32_grid(a.geo), b(kTBX, kTBY);
+  const size_t sm = tile_tma_smem(a.mod.R);
+  switch (a.mod.R) {
+#define SR_CASE(r) \
+  case r: k_wb_tma<r><<<g, b, sm, s>>>(a, tm); break;
+    SR_FOR_R(SR_CASE)
+#undef SR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
   const dim3 g = tile32_grid(a.geo), b(kTBX, kTBY);
   const size_t sm = tile32_smem(a.mod.R);
@@ -1088,9 +1384,16 @@ cudaError_t launch_reduce(const double* partials, int nblocks, int ncomp, double
 
 static dim3 row_grid(const Geo& geo) { return dim3((geo.N + 127) / 128, geo.M); }
 
-cudaError_t launch_init_wb(const float* phi, float* w1, float* w2, float* b1, float* b2, Geo geo,
+cudaError_t launch_init_wb(const float* phi, float* w1, float* w2, float* e1, float* e2, Geo geo,
                            cudaStream_t s) {
-  k_init_wb<<<row_grid(geo), 128, 0, s>>>(phi, w1, w2, b1, b2, geo);
+  k_init_wb<<<row_grid(geo), 128, 0, s>>>(phi, w1, w2, e1, e2, geo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpb(const float* a, const float* b, float sign, float* out, size_t n,
+                        cudaStream_t s) {
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
+  k_axpb<<<grid, 256, 0, s>>>(a, b, sign, out, n);
   return cudaGetLastError();
 }
 
