@@ -61,7 +61,7 @@ def _peaks():
 
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("sr_kernels.cu", "sr_internal.h"):
+    for name in ("sr_kernels.cu", "sr_fft.cu", "sr_tma.cuh", "sr_internal.h"):
         with open(os.path.join(ROOT, "paper_2003_12693_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
