@@ -46,8 +46,8 @@ UNIT = "Mpixel·iter/s"
 #   rowifft:   read the half spectrum (4 B) and psi (4 B), write psi (4 B)
 #   wb_update: read phi, w1, w2, e1, e2 (20 B), write w1, w2, e1, e2 (16 B)
 BYTES_PER_PX = {"prep": 16, "rowfft": 8, "colsolve": 8, "rowifft": 12, "wb_update": 36}
-KERNEL_NAMES = {"prep": "k_prep", "rowfft": "k_rowfwd", "colsolve": "k_colsolve",
-                "rowifft": "k_rowinv", "wb_update": "k_wb_update"}
+KERNEL_NAMES = {"prep": "k_prep", "rowfft": "k_rowfft", "colsolve": "k_colsolve2",
+                "rowifft": "k_rowifft", "wb_update": "k_wb_update"}
 
 
 def _peaks():

@@ -799,6 +799,9 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   m.band_l = p->band_l;
   m.beta2_mu = (float)(2.0 * (double)p->beta / (double)p->mu);
   m.gamma_mu = (float)((double)p->gamma / (double)p->mu);
+  m.inv_eps = (float)(1.0 / (double)p->eps);
+  m.half_inv_eps = (float)(0.5 / (double)p->eps);
+  m.dp_scale = (float)(1.57079632679489661923 / ((double)p->eps * (double)p->eps));
   m.R = p->win_radius;
   for (int t = -m.R; t <= m.R; ++t)
     m.kw[t + m.R] = (float)std::exp(-(double)(t * t) / ((double)p->d * (double)p->d));

@@ -20,6 +20,9 @@ struct Model {
   float alpha, beta, gamma, mu, tau, eps, band_l;
   float beta2_mu;   // 2 beta / mu       (Eq. (41))
   float gamma_mu;   // gamma / mu        (Eq. (42))
+  float inv_eps;    // 1 / eps
+  float half_inv_eps;  // 1 / (2 eps), the scale of delta_eps (Eq. (6))
+  float dp_scale;   // pi / (2 eps^2), the scale of delta'_eps (Eq. (29))
   int R;            // window half width
   float kw[2 * kMaxR + 1];  // k(p) = exp(-p^2 / d^2), p = -R..R at index p + R
 };
@@ -171,7 +174,7 @@ cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s);
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 cudaError_t launch_prep_tma(const PrepArgs& a, const PrepMaps& tm, cudaStream_t s);
 cudaError_t launch_wb_tma(const WBArgs& a, const WBMaps& tm, cudaStream_t s);
-size_t tile_tma_smem(int R);
+size_t tile_tma_smem(int R, bool wb);
 int tile_halo_x(int R);
 int tile_halo_y(int R);
 int tile32_blocks(const Geo& geo);  // CTAs of the 32 x 32 tile kernels

@@ -203,28 +203,56 @@ __device__ void fft_run(float2* buf, const Lay& lay, const Fft& f) {
 // ---------------------------------------------------------------------------
 // Regularised functions, Eqs. (5), (6), (11), (28), (29), in FP32
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float heps(float x, float eps) {
-  if (x > eps) return 1.f;
-  if (x < -eps) return 0.f;
-  const float y = x / eps;
-  return 0.5f * (1.f + y + sinpif(y) * 0.318309886183790671538f);
+// Arguments are scaled once, y = x / eps (as x times the host-computed 1/eps);
+// each branch boundary |y| = 1 is a point of continuity of the function.
+constexpr float kInvPi = 0.318309886183790671538f;
+
+__device__ __forceinline__ float heps(float x, const Model& m) {
+  const float y = x * m.inv_eps;
+  if (y > 1.f) return 1.f;
+  if (y < -1.f) return 0.f;
+  return 0.5f * (1.f + y + sinpif(y) * kInvPi);
 }
-__device__ __forceinline__ float deps(float x, float eps) {
-  if (fabsf(x) > eps) return 0.f;
-  return (1.f + cospif(x / eps)) * (0.5f / eps);
+__device__ __forceinline__ float deps(float x, const Model& m) {
+  const float y = x * m.inv_eps;
+  if (fabsf(y) > 1.f) return 0.f;
+  return (1.f + cospif(y)) * m.half_inv_eps;
 }
-__device__ __forceinline__ float dpeps(float x, float eps) {
-  if (fabsf(x) > eps) return 0.f;
-  return -(1.57079632679489661923f / (eps * eps)) * sinpif(x / eps);
+// H_eps and delta_eps of one argument from one sincospif
+__device__ __forceinline__ void hd_eps(float x, const Model& m, float& h, float& d) {
+  const float y = x * m.inv_eps;
+  if (fabsf(y) > 1.f) {
+    h = y > 0.f ? 1.f : 0.f;
+    d = 0.f;
+    return;
+  }
+  float sn, cs;
+  sincospif(y, &sn, &cs);
+  h = 0.5f * (1.f + y + sn * kInvPi);
+  d = (1.f + cs) * m.half_inv_eps;
+}
+// delta_eps and delta'_eps (Eq. (29)) of one argument
+__device__ __forceinline__ void dd_eps(float x, const Model& m, float& d, float& dp) {
+  const float y = x * m.inv_eps;
+  if (fabsf(y) > 1.f) {
+    d = dp = 0.f;
+    return;
+  }
+  float sn, cs;
+  sincospif(y, &sn, &cs);
+  d = (1.f + cs) * m.half_inv_eps;
+  dp = -m.dp_scale * sn;
 }
 __device__ __forceinline__ float band_h(float x, const Model& m) {
   if (fabsf(x) >= m.band_l + m.eps) return 0.f;
-  return heps(x + m.band_l, m.eps) * (1.f - heps(x - m.band_l, m.eps));
+  return heps(x + m.band_l, m) * (1.f - heps(x - m.band_l, m));
 }
 __device__ __forceinline__ float band_hp(float x, const Model& m) {
   if (fabsf(x) >= m.band_l + m.eps) return 0.f;
-  return deps(x + m.band_l, m.eps) * (1.f - heps(x - m.band_l, m.eps)) -
-         heps(x + m.band_l, m.eps) * deps(x - m.band_l, m.eps);
+  float hA, dA, hB, dB;
+  hd_eps(x + m.band_l, m, hA, dA);
+  hd_eps(x - m.band_l, m, hB, dB);
+  return dA * (1.f - hB) - hA * dB;
 }
 
 // ---------------------------------------------------------------------------
@@ -254,7 +282,9 @@ __device__ __forceinline__ float rhs_increment(const RowFwdArgs& a, int i, int j
   if (fabsf(x) < m.band_l + m.eps) {
     const float gg = a.g[o];
     const float wn = sqrtf(W1 * W1 + W2 * W2);
-    force += -m.gamma * gg * wn * dpeps(x, m.eps) + m.alpha * gg * deps(x, m.eps) +
+    float dl, dpl;
+    dd_eps(x, m, dl, dpl);
+    force += -m.gamma * gg * wn * dpl + m.alpha * gg * dl +
              2.f * m.beta * band_hp(x, m) * (W1 * v1 + W2 * v2);
   }
   return m.tau * force;
@@ -621,46 +651,48 @@ __device__ __forceinline__ void window_sum(const float* t_psi, const float* t_w1
                                            float (&v1)[4], float (&v2)[4]) {
   using TL = Tile<R>;
   const int tid = threadIdx.y * kTBX + threadIdx.x;
-  for (int idx = tid; idx < TL::NP; idx += kTN) {
-    const float x = t_psi[idx];
-    const float hh = in_band(x, m) ? band_h(x, m) : 0.f;
-    t_u1[idx] = hh * t_w1[idx];  // w = 0 outside the image
-    t_u2[idx] = hh * t_w2[idx];
+  for (int idx = tid; idx < TL::NP / 4; idx += kTN) {
+    const float4 x = *reinterpret_cast<const float4*>(t_psi + 4 * idx);
+    const float4 a1 = *reinterpret_cast<const float4*>(t_w1 + 4 * idx);  // w = 0 outside the image
+    const float4 a2 = *reinterpret_cast<const float4*>(t_w2 + 4 * idx);
+    float4 h;
+    h.x = in_band(x.x, m) ? band_h(x.x, m) : 0.f;
+    h.y = in_band(x.y, m) ? band_h(x.y, m) : 0.f;
+    h.z = in_band(x.z, m) ? band_h(x.z, m) : 0.f;
+    h.w = in_band(x.w, m) ? band_h(x.w, m) : 0.f;
+    st4(t_u1 + 4 * idx, make_float4(h.x * a1.x, h.y * a1.y, h.z * a1.z, h.w * a1.w));
+    st4(t_u2 + 4 * idx, make_float4(h.x * a2.x, h.y * a2.y, h.z * a2.z, h.w * a2.w));
   }
   __syncthreads();
-  // sum down the columns: a task is 4 rows x 4 columns, sliding over 4 + 2R rows
-  constexpr int NTASK = (kT / 4) * TL::SW4;
+  // sum down the columns: a task is one plane, 4 rows x 4 columns, sliding
+  // over 4 + 2R input rows
+  constexpr int NTASK = 2 * (kT / 4) * TL::SW4;
+  static_assert(NTASK <= kTN, "one column task per thread");
   if (tid < NTASK) {
-    const int r0 = (tid / TL::SW4) * 4, c = 4 * (tid % TL::SW4);
-    float4 a1[4], a2[4];
+    const int c4 = tid % TL::SW4, rest = tid / TL::SW4;
+    const int r0 = (rest >> 1) * 4, c = 4 * c4;
+    const float* src = (rest & 1) ? t_u2 : t_u1;
+    float* dst = (rest & 1) ? t_V2 : t_V1;
+    float4 acc[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) a1[q] = a2[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < 4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int t = 0; t < 4 + 2 * R; ++t) {
-      const int row = r0 + TL::HY - R + t;
-      const float4 x1 = *reinterpret_cast<const float4*>(t_u1 + row * TL::SW + c);
-      const float4 x2 = *reinterpret_cast<const float4*>(t_u2 + row * TL::SW + c);
+      const float4 x = *reinterpret_cast<const float4*>(src + (r0 + TL::HY - R + t) * TL::SW + c);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int p = t - q;  // output row r0 + q takes input rows r0 + q - R .. r0 + q + R
         if (p >= 0 && p <= 2 * R) {
           const float kw = m.kw[p];
-          a1[q].x = fmaf(kw, x1.x, a1[q].x);
-          a1[q].y = fmaf(kw, x1.y, a1[q].y);
-          a1[q].z = fmaf(kw, x1.z, a1[q].z);
-          a1[q].w = fmaf(kw, x1.w, a1[q].w);
-          a2[q].x = fmaf(kw, x2.x, a2[q].x);
-          a2[q].y = fmaf(kw, x2.y, a2[q].y);
-          a2[q].z = fmaf(kw, x2.z, a2[q].z);
-          a2[q].w = fmaf(kw, x2.w, a2[q].w);
+          acc[q].x = fmaf(kw, x.x, acc[q].x);
+          acc[q].y = fmaf(kw, x.y, acc[q].y);
+          acc[q].z = fmaf(kw, x.z, acc[q].z);
+          acc[q].w = fmaf(kw, x.w, acc[q].w);
         }
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      st4(t_V1 + (r0 + q) * TL::SW + c, a1[q]);
-      st4(t_V2 + (r0 + q) * TL::SW + c, a2[q]);
-    }
+    for (int q = 0; q < 4; ++q) st4(dst + (r0 + q) * TL::SW + c, acc[q]);
   }
   __syncthreads();
   // across the row: outputs c .. c+3 take inputs c - R .. c + 3 + R
@@ -708,15 +740,20 @@ size_t tile32_smem(int R) { return (size_t)tile32_floats(R) * sizeof(float); }
 // G = tau [ mu (div e + Lap psi) - gamma g |w| delta'(psi) + alpha g delta(psi)
 //           + 2 beta h'(psi) (w . v) ] at one pixel (the band terms only where
 // |psi| < l + eps; e = b - w, div the backward divergence).
+// BAND = false is the form for tiles without narrow-band pixels: the band
+// terms are not evaluated at all (rather than predicated off per pixel).
+template <bool BAND>
 __device__ __forceinline__ float rhs_point(const Model& m, float x, float up, float dn, float lf,
                                            float rt, float e1, float e1u, float e2, float e2l,
                                            float w1, float w2, float g, float v1, float v2) {
   const float lap = (up + dn) + (lf + rt) - 4.f * x;
   const float dv = (e1 - e1u) + (e2 - e2l);
   float force = m.mu * (dv + lap);
-  if (in_band(x, m)) {
+  if (BAND && in_band(x, m)) {
     const float wn = sqrtf(w1 * w1 + w2 * w2);
-    force += -m.gamma * g * wn * dpeps(x, m.eps) + m.alpha * g * deps(x, m.eps) +
+    float dl, dpl;
+    dd_eps(x, m, dl, dpl);
+    force += -m.gamma * g * wn * dpl + m.alpha * g * dl +
              2.f * m.beta * band_hp(x, m) * (w1 * v1 + w2 * v2);
   }
   return m.tau * force;
@@ -725,23 +762,27 @@ __device__ __forceinline__ float rhs_point(const Model& m, float x, float up, fl
 // Eqs. (41), (42), (40), (23) at one pixel: B = grad phi + b + (2 beta/mu) h v,
 // t = (gamma/mu) g delta(phi); w = B/|B| if |B| > t else 0; b' = b + grad phi - w;
 // returns w' and e' = b' - w'.
+template <bool BAND>
 __device__ __forceinline__ void wb_point(const Model& m, float x, float d1, float d2, float b1,
                                          float b2, float g, float v1, float v2, float& wo1,
                                          float& wo2, float& eo1, float& eo2) {
   float Bv1 = d1 + b1;
   float Bv2 = d2 + b2;
   float thr = 0.f;
-  if (in_band(x, m)) {
+  if (BAND && in_band(x, m)) {
     const float h = band_h(x, m);
     Bv1 = fmaf(m.beta2_mu * h, v1, Bv1);
     Bv2 = fmaf(m.beta2_mu * h, v2, Bv2);
-    thr = m.gamma_mu * g * deps(x, m.eps);
+    thr = m.gamma_mu * g * deps(x, m);
   }
-  const float nB = sqrtf(Bv1 * Bv1 + Bv2 * Bv2);
+  // |B| and B/|B| from one reciprocal square root (a few ulp, against a
+  // correctly rounded sqrt and two divisions)
+  const float nB2 = Bv1 * Bv1 + Bv2 * Bv2;
+  const float r = rsqrtf(nB2);
   float W1 = 0.f, W2 = 0.f;
-  if (nB > thr) {
-    W1 = Bv1 / nB;
-    W2 = Bv2 / nB;
+  if (nB2 > 0.f && nB2 * r > thr) {
+    W1 = Bv1 * r;
+    W2 = Bv2 * r;
   }
   wo1 = W1;
   wo2 = W2;
@@ -749,41 +790,97 @@ __device__ __forceinline__ void wb_point(const Model& m, float x, float d1, floa
   eo2 = ((b2 + d2) - W2) - W2;
 }
 
+// Four-pixel neighbourhood of one thread of a 32 x 32 tile (block 8 x 32,
+// thread (tx, ty) owns pixels (i, j .. j+3), a warp owns four rows).
+// Neighbours that another lane of the warp holds come by shuffle; only the
+// warp's edge lanes read their periodic neighbours from global memory.
+struct Quad {
+  int i, j, iu, id, jl, jr;
+  bool live, up_g, dn_g, lf_g, rt_g;
+  size_t o;
+  __device__ __forceinline__ Quad(const Geo& geo) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    i = blockIdx.y * kT + ty;
+    j = blockIdx.x * kT + 4 * tx;
+    live = i < geo.M && j < geo.N;
+    iu = i > 0 ? i - 1 : geo.M - 1;
+    id = i < geo.M - 1 ? i + 1 : 0;
+    jl = j > 0 ? j - 1 : geo.N - 1;
+    jr = j + 4 < geo.N ? j + 4 : 0;
+    // a warp holds rows 4w .. 4w+3 of the tile, whole (M is a multiple of 16)
+    up_g = (ty & 3) == 0;
+    dn_g = (ty & 3) == 3;
+    lf_g = tx == 0;
+    rt_g = tx == kTBX - 1 || j + 4 >= geo.N;
+    o = (size_t)i * geo.N + j;
+  }
+};
+
+__device__ __forceinline__ float4 shfl_up4(float4 v, int d) {
+  return make_float4(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d),
+                     __shfl_up_sync(0xffffffffu, v.z, d), __shfl_up_sync(0xffffffffu, v.w, d));
+}
+__device__ __forceinline__ float4 shfl_down4(float4 v, int d) {
+  return make_float4(__shfl_down_sync(0xffffffffu, v.x, d),
+                     __shfl_down_sync(0xffffffffu, v.y, d),
+                     __shfl_down_sync(0xffffffffu, v.z, d),
+                     __shfl_down_sync(0xffffffffu, v.w, d));
+}
+__device__ __forceinline__ float4 ld4_if(bool p, const float* ptr) {
+  return p ? ld4(ptr) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ float ld_if(bool p, const float* ptr) { return p ? __ldg(ptr) : 0.f; }
+__device__ __forceinline__ int any_band4(float4 v, const Model& m) {
+  return in_band(v.x, m) | in_band(v.y, m) | in_band(v.z, m) | in_band(v.w, m);
+}
+
 // Increment right-hand side of one inner step, Eq. (37) in the form
 // G = tau [ -gamma g |w| delta'(psi) + alpha g delta(psi) + 2 beta h'(psi) (w . v)
 //           + mu (div(b - w) + Lap psi) ], so that phi^{k+1,s+1} = psi + L^{-1} G.
+// Every plane of the bulk path is requested before the block decides whether
+// its tile holds narrow-band pixels; only such tiles stage psi and w with a
+// halo for the window sum v (which enters only at band pixels, so the test
+// over the tile's own pixels is exact).
 template <int R>
 __global__ void __launch_bounds__(kTN, 4) k_prep(const PrepArgs a) {
-  using TL = Tile<R>;
   extern __shared__ __align__(16) float smem_f[];
-  const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
-  const int M = a.geo.M, N = a.geo.N;
   const Model& m = a.mod;
-  const int any = stage4<R, true>(smem_f, a.psi, a.geo, i0, j0, m);
-  const bool band = __syncthreads_or(any) != 0;
-  float v1[4], v2[4];
-  tile_window<R>(smem_f, a.geo, m, a.w1, a.w2, i0, j0, band, v1, v2);
-  const int i = i0 + threadIdx.y, j = j0 + 4 * threadIdx.x;
-  if (i >= M || j >= N) return;
-  const size_t o = (size_t)i * N + j;
-  const size_t ou = (size_t)(i > 0 ? i - 1 : M - 1) * N + j;
-  const size_t ol = (size_t)i * N + (j > 0 ? j - 1 : N - 1);
-  const float4 E1 = ld4(a.e1 + o), E2 = ld4(a.e2 + o), E1u = ld4(a.e1 + ou);
-  const float e2l = __ldg(a.e2 + ol);
-  const float* t_psi = smem_f;
-  const int q = (threadIdx.y + TL::HY) * TL::SW + 4 * threadIdx.x + TL::HX;
-  const float4 X = *reinterpret_cast<const float4*>(t_psi + q);
-  const float4 UP = i > 0 ? *reinterpret_cast<const float4*>(t_psi + q - TL::SW) : ld4(a.psi + ou);
-  const float4 DN = i < M - 1 ? *reinterpret_cast<const float4*>(t_psi + q + TL::SW)
-                              : ld4(a.psi + j);
-  const float LF = j > 0 ? t_psi[q - 1] : __ldg(a.psi + ol);
-  const float RT = j + 4 < N ? t_psi[q + 4] : __ldg(a.psi + (size_t)i * N);
-  float4 W1 = make_float4(0.f, 0.f, 0.f, 0.f), W2 = W1, G4 = W1;
-  if (band) {  // w and g enter only through the narrow-band terms
-    W1 = ld4(a.w1 + o);
-    W2 = ld4(a.w2 + o);
-    G4 = ld4(a.g + o);
+  const int N = a.geo.N;
+  const Quad q(a.geo);
+  const float* psi = a.psi;
+  const float4 X = ld4_if(q.live, psi + q.o);
+  const float4 E1 = ld4_if(q.live, a.e1 + q.o), E2 = ld4_if(q.live, a.e2 + q.o);
+  float4 UP = ld4_if(q.live && q.up_g, psi + (size_t)q.iu * N + q.j);
+  float4 DN = ld4_if(q.live && q.dn_g, psi + (size_t)q.id * N + q.j);
+  float4 E1u = ld4_if(q.live && q.up_g, a.e1 + (size_t)q.iu * N + q.j);
+  float LF = ld_if(q.live && q.lf_g, psi + (size_t)q.i * N + q.jl);
+  float RT = ld_if(q.live && q.rt_g, psi + (size_t)q.i * N + q.jr);
+  float e2l = ld_if(q.live && q.lf_g, a.e2 + (size_t)q.i * N + q.jl);
+  const bool band = __syncthreads_or(q.live && any_band4(X, m)) != 0;
+  {
+    const float4 su = shfl_up4(X, kTBX), sd = shfl_down4(X, kTBX), se = shfl_up4(E1, kTBX);
+    const float sl = __shfl_up_sync(0xffffffffu, X.w, 1);
+    const float sr = __shfl_down_sync(0xffffffffu, X.x, 1);
+    const float sel = __shfl_up_sync(0xffffffffu, E2.w, 1);
+    if (!q.up_g) UP = su, E1u = se;
+    if (!q.dn_g) DN = sd;
+    if (!q.lf_g) LF = sl, e2l = sel;
+    if (!q.rt_g) RT = sr;
   }
+  float v1[4], v2[4];
+  float4 W1 = make_float4(0.f, 0.f, 0.f, 0.f), W2 = W1, G4 = W1;
+  if (band) {  // uniform across the block
+    const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
+    stage4<R, false>(smem_f, psi, a.geo, i0, j0, m);
+    tile_window<R>(smem_f, a.geo, m, a.w1, a.w2, i0, j0, true, v1, v2);
+    W1 = ld4_if(q.live, a.w1 + q.o);
+    W2 = ld4_if(q.live, a.w2 + q.o);
+    G4 = ld4_if(q.live, a.g + q.o);
+  } else {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) v1[t] = v2[t] = 0.f;
+  }
+  if (!q.live) return;
   const float x[4] = {X.x, X.y, X.z, X.w};
   const float up[4] = {UP.x, UP.y, UP.z, UP.w}, dn[4] = {DN.x, DN.y, DN.z, DN.w};
   const float lf[4] = {LF, X.x, X.y, X.z}, rt[4] = {X.y, X.z, X.w, RT};
@@ -792,53 +889,79 @@ __global__ void __launch_bounds__(kTN, 4) k_prep(const PrepArgs a) {
   const float w1[4] = {W1.x, W1.y, W1.z, W1.w}, w2[4] = {W2.x, W2.y, W2.z, W2.w};
   const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
   float out[4];
+  if (band) {
 #pragma unroll
-  for (int t = 0; t < 4; ++t) out[t] = rhs_point(m, x[t], up[t], dn[t], lf[t], rt[t], e1[t], e1u[t],
-                                                 e2[t], e2l4[t], w1[t], w2[t], gg[t], v1[t], v2[t]);
-  st4(a.G + o, make_float4(out[0], out[1], out[2], out[3]));
+    for (int t = 0; t < 4; ++t)
+      out[t] = rhs_point<true>(m, x[t], up[t], dn[t], lf[t], rt[t], e1[t], e1u[t], e2[t], e2l4[t],
+                               w1[t], w2[t], gg[t], v1[t], v2[t]);
+  } else {
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      out[t] = rhs_point<false>(m, x[t], up[t], dn[t], lf[t], rt[t], e1[t], e1u[t], e2[t], e2l4[t],
+                                w1[t], w2[t], gg[t], v1[t], v2[t]);
+  }
+  st4(a.G + q.o, make_float4(out[0], out[1], out[2], out[3]));
 }
 
 // w and b update (Eqs. (41), (42), (40), (23)) with the window sum fused in.
-// Soft threshold then projection: w = B/|B| if |B| > t, else 0.
+// Soft threshold then projection: w = B/|B| if |B| > t, else 0.  Same
+// structure as k_prep: all bulk loads issued up front, window sum and g only
+// on tiles with narrow-band pixels.
 template <int R>
 __global__ void __launch_bounds__(kTN, 4) k_wb_update(const WBArgs a) {
-  using TL = Tile<R>;
   extern __shared__ __align__(16) float smem_f[];
-  const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
-  const int M = a.geo.M, N = a.geo.N;
   const Model& m = a.mod;
-  const int any = stage4<R, true>(smem_f, a.phi1, a.geo, i0, j0, m);
-  const bool band = __syncthreads_or(any) != 0;
+  const int N = a.geo.N;
+  const Quad q(a.geo);
+  const float* phi = a.phi1;
+  const float4 X = ld4_if(q.live, phi + q.o);
+  const float4 E1 = ld4_if(q.live, a.e1 + q.o), E2 = ld4_if(q.live, a.e2 + q.o);
+  const float4 W1 = ld4_if(q.live, a.w1 + q.o), W2 = ld4_if(q.live, a.w2 + q.o);
+  float4 DN = ld4_if(q.live && q.dn_g, phi + (size_t)q.id * N + q.j);
+  float RT = ld_if(q.live && q.rt_g, phi + (size_t)q.i * N + q.jr);
+  const float4 P = ld4_if(q.live && a.phi_old != nullptr, a.phi_old + q.o);
+  const bool band = __syncthreads_or(q.live && any_band4(X, m)) != 0;
+  {
+    const float4 sd = shfl_down4(X, kTBX);
+    const float sr = __shfl_down_sync(0xffffffffu, X.x, 1);
+    if (!q.dn_g) DN = sd;
+    if (!q.rt_g) RT = sr;
+  }
   float v1[4], v2[4];
-  tile_window<R>(smem_f, a.geo, m, a.w1, a.w2, i0, j0, band, v1, v2);
-  const int i = i0 + threadIdx.y, j = j0 + 4 * threadIdx.x;
+  float4 G4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (band) {  // uniform across the block
+    const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
+    stage4<R, false>(smem_f, phi, a.geo, i0, j0, m);
+    tile_window<R>(smem_f, a.geo, m, a.w1, a.w2, i0, j0, true, v1, v2);
+    G4 = ld4_if(q.live, a.g + q.o);
+  } else {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) v1[t] = v2[t] = 0.f;
+  }
   double part[2] = {0.0, 0.0};
-  if (i < M && j < N) {
-    const size_t o = (size_t)i * N + j;
-    const float4 E1 = ld4(a.e1 + o), E2 = ld4(a.e2 + o), W1 = ld4(a.w1 + o), W2 = ld4(a.w2 + o);
-    const float4 G4 = band ? ld4(a.g + o) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float* t_psi = smem_f;
-    const int q = (threadIdx.y + TL::HY) * TL::SW + 4 * threadIdx.x + TL::HX;
-    const float4 X = *reinterpret_cast<const float4*>(t_psi + q);
-    const float4 DN = i < M - 1 ? *reinterpret_cast<const float4*>(t_psi + q + TL::SW)
-                                : ld4(a.phi1 + j);
-    const float RT = j + 4 < N ? t_psi[q + 4] : __ldg(a.phi1 + (size_t)i * N);
+  if (q.live) {
     const float x[4] = {X.x, X.y, X.z, X.w};
     const float dn[4] = {DN.x, DN.y, DN.z, DN.w}, rt[4] = {X.y, X.z, X.w, RT};
     const float b1[4] = {E1.x + W1.x, E1.y + W1.y, E1.z + W1.z, E1.w + W1.w};
     const float b2[4] = {E2.x + W2.x, E2.y + W2.y, E2.z + W2.z, E2.w + W2.w};
     const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
     float wo1[4], wo2[4], eo1[4], eo2[4];
+    if (band) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t)
-      wb_point(m, x[t], dn[t] - x[t], rt[t] - x[t], b1[t], b2[t], gg[t], v1[t], v2[t], wo1[t],
-               wo2[t], eo1[t], eo2[t]);
-    st4(a.w1o + o, make_float4(wo1[0], wo1[1], wo1[2], wo1[3]));
-    st4(a.w2o + o, make_float4(wo2[0], wo2[1], wo2[2], wo2[3]));
-    st4(a.e1o + o, make_float4(eo1[0], eo1[1], eo1[2], eo1[3]));
-    st4(a.e2o + o, make_float4(eo2[0], eo2[1], eo2[2], eo2[3]));
+      for (int t = 0; t < 4; ++t)
+        wb_point<true>(m, x[t], dn[t] - x[t], rt[t] - x[t], b1[t], b2[t], gg[t], v1[t], v2[t],
+                       wo1[t], wo2[t], eo1[t], eo2[t]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        wb_point<false>(m, x[t], dn[t] - x[t], rt[t] - x[t], b1[t], b2[t], gg[t], v1[t], v2[t],
+                        wo1[t], wo2[t], eo1[t], eo2[t]);
+    }
+    st4(a.w1o + q.o, make_float4(wo1[0], wo1[1], wo1[2], wo1[3]));
+    st4(a.w2o + q.o, make_float4(wo2[0], wo2[1], wo2[2], wo2[3]));
+    st4(a.e1o + q.o, make_float4(eo1[0], eo1[1], eo1[2], eo1[3]));
+    st4(a.e2o + q.o, make_float4(eo2[0], eo2[1], eo2[2], eo2[3]));
     if (a.phi_old) {
-      const float4 P = ld4(a.phi_old + o);
       const float po[4] = {P.x, P.y, P.z, P.w};
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
@@ -852,216 +975,312 @@ __global__ void __launch_bounds__(kTN, 4) k_wb_update(const WBArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// TMA versions of the two tile kernels.  One thread issues 2-D box loads of
-// every plane the tile needs (zero fill outside the image gives the window
-// sum's dropped terms); they complete on an mbarrier, and the block then
-// works from shared memory only.  Boxes: psi, w1, w2 with the (HX, HY) halo;
-// b1 with the row above (33 x 32), b2 with four columns to the left
-// (32 x 36), g and the old phi 32 x 32.  k_wb_tma loads w only for tiles with
-// narrow-band pixels (second phase).
+// Pipelined TMA versions of the two tile kernels.  A persistent CTA walks the
+// tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; thread 0 keeps the 2-D
+// box loads of the next NS tiles in flight (one mbarrier per stage), so HBM
+// sees a steady stream instead of one load burst per CTA lifetime.  Boxes
+// per stage: psi with the (HX, HY) halo (zero fill outside the image gives
+// the window sum's dropped terms), and for k_prep e1 with the row above
+// (32 x 33) and e2 with four columns to the left (36 x 32); for k_wb_update
+// e1, e2, w1, w2 and the old phi, 32 x 32.  Tiles with narrow-band pixels
+// load w1, w2 with the halo and g on a separate barrier.  Periodic
+// neighbours across the image edge come from global memory.  Every wait is
+// bounded; on a timeout the block records the error, drains its own loads
+// in flight (bounded again) and returns.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int a32(int n) { return (n + 31) / 32 * 32; }
 
 template <int R>
-struct TileT {
+struct PipeP {  // k_prep stage, floats; every box 128-B aligned
   using TL = Tile<R>;
   static constexpr int PSI = 0;
-  static constexpr int W1 = PSI + a32(TL::NP);
-  static constexpr int W2 = W1 + a32(TL::NP);
-  static constexpr int B1 = W2 + a32(TL::NP);    // 33 rows x 32
-  static constexpr int B2 = B1 + a32(33 * 32);    // 32 rows x 36
-  static constexpr int GG = B2 + a32(32 * 36);    // 32 x 32
-  static constexpr int PO = GG + a32(32 * 32);    // 32 x 32 (old phi)
-  static constexpr int U1 = PO + a32(32 * 32);
-  static constexpr int U2 = U1 + a32(TL::NP);
-  static constexpr int V1 = U2 + a32(TL::NP);
-  static constexpr int V2 = V1 + a32(kT * TL::SW);
-  static constexpr int BAR = V2 + a32(kT * TL::SW);
-  static constexpr int FLOATS = BAR + 8;  // two mbarriers
+  static constexpr int E1 = PSI + a32(TL::NP);   // 33 rows x 32
+  static constexpr int E2 = E1 + a32(33 * 32);   // 32 rows x 36
+  static constexpr int STAGE = E2 + a32(32 * 36);
+  static constexpr uint32_t BYTES = 4u * (TL::NP + 33 * 32 + 32 * 36);
 };
+
+template <int R>
+struct PipeW {  // k_wb_update stage
+  using TL = Tile<R>;
+  static constexpr int PSI = 0;
+  static constexpr int E1 = PSI + a32(TL::NP);
+  static constexpr int E2 = E1 + 1024;
+  static constexpr int W1 = E2 + 1024;
+  static constexpr int W2 = W1 + 1024;
+  static constexpr int PO = W2 + 1024;
+  static constexpr int STAGE = PO + 1024;
+  static constexpr uint32_t BYTES = 4u * (TL::NP + 4 * 1024);  // + 4096 with the old phi
+};
+
+template <int R>
+struct PipeBand {  // band-tile buffers; u = h(psi) w is formed in place of w
+  using TL = Tile<R>;
+  static constexpr int W1 = 0;
+  static constexpr int W2 = W1 + a32(TL::NP);
+  static constexpr int V1 = W2 + a32(TL::NP);
+  static constexpr int V2 = V1 + a32(kT * TL::SW);
+  static constexpr int GG = V2 + a32(kT * TL::SW);
+  static constexpr int FLOATS = GG + 1024;
+  static constexpr uint32_t BYTES = 4u * (2 * TL::NP + 1024);
+};
+
+constexpr int kPrepStages = 3, kWbStages = 3;
+
+template <class P, class B, int NS>
+__host__ __device__ constexpr int pipe_floats() {
+  return NS * P::STAGE + B::FLOATS + 2 * (NS + 1) + 2;  // + mbarriers and an error word
+}
 
 __device__ __forceinline__ float* align128(unsigned char* p) {
   return reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(p) + 127) & ~static_cast<uintptr_t>(127));
 }
 
-template <int R>
-__global__ void __launch_bounds__(kTN, 3) k_prep_tma(const PrepArgs a, const __grid_constant__ PrepMaps tm) {
-  using TL = Tile<R>;
-  using TT = TileT<R>;
-  extern __shared__ __align__(16) unsigned char smem_tt[];
-  float* sm = align128(smem_tt);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TT::BAR);
-  const int tid = threadIdx.y * kTBX + threadIdx.x;
-  const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
-  const int M = a.geo.M, N = a.geo.N;
-  const Model& m = a.mod;
-  if (tid == 0) {
-    tma::mbar_init(&bar[0], 1);
-    tma::mbar_init(&bar[1], 1);
-    tma::mbar_init_fence();
-  }
-  __syncthreads();
-  if (tid == 0) {
-    constexpr uint32_t bytes = 4u * (TL::NP + 33 * 32 + 32 * 36);
-    tma::mbar_expect_tx(&bar[0], bytes);
-    tma::load_2d(sm + TT::PSI, &tm.psi, j0 - TL::HX, i0 - TL::HY, &bar[0]);
-    tma::load_2d(sm + TT::B1, &tm.e1, j0, i0 - 1, &bar[0]);
-    tma::load_2d(sm + TT::B2, &tm.e2, j0 - 4, i0, &bar[0]);
-  }
-  bool ok = tma::mbar_wait(&bar[0], 0);
-  if (!__syncthreads_and(ok)) {
-    if (tid == 0) tma::on_timeout(&bar[0], 0, a.err);
-    return;
-  }
-  const float* t_psi = sm + TT::PSI;
-  int any = 0;
-  for (int idx = tid; idx < TL::NP; idx += kTN) any |= in_band(t_psi[idx], m);
-  const bool band = __syncthreads_or(any) != 0;
-  float v1[4] = {0.f, 0.f, 0.f, 0.f}, v2[4] = {0.f, 0.f, 0.f, 0.f};
-  if (band) {
-    if (tid == 0) {
-      tma::mbar_expect_tx(&bar[1], 4u * (2 * TL::NP + 32 * 32));
-      tma::load_2d(sm + TT::W1, &tm.w1, j0 - TL::HX, i0 - TL::HY, &bar[1]);
-      tma::load_2d(sm + TT::W2, &tm.w2, j0 - TL::HX, i0 - TL::HY, &bar[1]);
-      tma::load_2d(sm + TT::GG, &tm.g, j0, i0, &bar[1]);
-    }
-    ok = tma::mbar_wait(&bar[1], 0);
-    if (!__syncthreads_and(ok)) {
-      if (tid == 0) tma::on_timeout(&bar[1], 0, a.err);
-      return;
-    }
-    window_sum<R>(t_psi, sm + TT::W1, sm + TT::W2, sm + TT::U1, sm + TT::U2, sm + TT::V1,
-                  sm + TT::V2, m, v1, v2);
-  }
-  const int ty = threadIdx.y, tx = threadIdx.x;
-  const int i = i0 + ty, j = j0 + 4 * tx;
-  if (i >= M || j >= N) return;
-  const int q = (ty + TL::HY) * TL::SW + 4 * tx + TL::HX;
-  auto f4 = [&](int off) { return *reinterpret_cast<const float4*>(sm + off); };
-  const float4 X = f4(TT::PSI + q);
-  const float4 UP = i > 0 ? f4(TT::PSI + q - TL::SW) : ld4(a.psi + (size_t)(M - 1) * N + j);
-  const float4 DN = i < M - 1 ? f4(TT::PSI + q + TL::SW) : ld4(a.psi + j);
-  const float LF = j > 0 ? sm[TT::PSI + q - 1] : __ldg(a.psi + (size_t)i * N + N - 1);
-  const float RT = j + 4 < N ? sm[TT::PSI + q + 4] : __ldg(a.psi + (size_t)i * N);
-  const float4 E1 = f4(TT::B1 + (ty + 1) * 32 + 4 * tx);
-  const float4 E1u = i > 0 ? f4(TT::B1 + ty * 32 + 4 * tx) : ld4(a.e1 + (size_t)(M - 1) * N + j);
-  const float4 E2 = f4(TT::B2 + ty * 36 + 4 + 4 * tx);
-  const float e2l = j > 0 ? sm[TT::B2 + ty * 36 + 3 + 4 * tx] : __ldg(a.e2 + (size_t)i * N + N - 1);
-  float4 W1 = make_float4(0.f, 0.f, 0.f, 0.f), W2 = W1, G4 = W1;
-  if (band) {
-    W1 = f4(TT::W1 + q);
-    W2 = f4(TT::W2 + q);
-    G4 = f4(TT::GG + ty * 32 + 4 * tx);
-  }
-  const float x[4] = {X.x, X.y, X.z, X.w};
-  const float up[4] = {UP.x, UP.y, UP.z, UP.w}, dn[4] = {DN.x, DN.y, DN.z, DN.w};
-  const float lf[4] = {LF, X.x, X.y, X.z}, rt[4] = {X.y, X.z, X.w, RT};
-  const float e1[4] = {E1.x, E1.y, E1.z, E1.w}, e2[4] = {E2.x, E2.y, E2.z, E2.w};
-  const float e1u[4] = {E1u.x, E1u.y, E1u.z, E1u.w}, e2l4[4] = {e2l, E2.x, E2.y, E2.z};
-  const float w1[4] = {W1.x, W1.y, W1.z, W1.w}, w2[4] = {W2.x, W2.y, W2.z, W2.w};
-  const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
-  float out[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) out[t] = rhs_point(m, x[t], up[t], dn[t], lf[t], rt[t], e1[t], e1u[t],
-                                                 e2[t], e2l4[t], w1[t], w2[t], gg[t], v1[t], v2[t]);
-  st4(a.G + (size_t)i * N + j, make_float4(out[0], out[1], out[2], out[3]));
+// After a timeout: record it, then wait (bounded) for the loads this block
+// still has in flight so that none lands after the block has exited.
+__device__ __forceinline__ void pipe_drain(uint64_t* bar, int NS, int it, int tile, int stride,
+                                           int ntiles, bool band_pending, uint32_t band_par,
+                                           int* err) {
+  if (err) atomicCAS(err, 0, tma::kErrTimeout);
+  for (int k = 0; k < NS && tile + k * stride < ntiles; ++k)
+    tma::mbar_wait(&bar[(it + k) % NS], (uint32_t)((it + k) / NS) & 1u);
+  if (band_pending) tma::mbar_wait(&bar[NS], band_par);
 }
 
 template <int R>
-__global__ void __launch_bounds__(kTN, 3) k_wb_tma(const WBArgs a, const __grid_constant__ WBMaps tm) {
+__global__ void __launch_bounds__(kTN, 3) k_prep_tma(const PrepArgs a, const __grid_constant__ PrepMaps tm) {
   using TL = Tile<R>;
-  using TT = TileT<R>;
+  using PP = PipeP<R>;
+  using PB = PipeBand<R>;
+  constexpr int NS = kPrepStages;
   extern __shared__ __align__(16) unsigned char smem_tt[];
   float* sm = align128(smem_tt);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TT::BAR);
+  float* bs = sm + NS * PP::STAGE;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(bs + PB::FLOATS);
+  volatile int* s_err = reinterpret_cast<volatile int*>(bar + NS + 1);
   const int tid = threadIdx.y * kTBX + threadIdx.x;
-  const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
   const int M = a.geo.M, N = a.geo.N;
+  const int tiles_x = (N + kT - 1) / kT, ntiles = tiles_x * ((M + kT - 1) / kT);
   const Model& m = a.mod;
-  const bool chk = a.phi_old != nullptr;
+  auto issue = [&](int tile, int s) {
+    const int i0 = (tile / tiles_x) * kT, j0 = (tile % tiles_x) * kT;
+    float* st = sm + s * PP::STAGE;
+    tma::mbar_expect_tx(&bar[s], PP::BYTES);
+    tma::load_2d(st + PP::PSI, &tm.psi, j0 - TL::HX, i0 - TL::HY, &bar[s]);
+    tma::load_2d(st + PP::E1, &tm.e1, j0, i0 - 1, &bar[s]);
+    tma::load_2d(st + PP::E2, &tm.e2, j0 - 4, i0, &bar[s]);
+  };
   if (tid == 0) {
-    tma::mbar_init(&bar[0], 1);
-    tma::mbar_init(&bar[1], 1);
+    for (int s = 0; s <= NS; ++s) tma::mbar_init(&bar[s], 1);
+    *s_err = 0;
     tma::mbar_init_fence();
+    for (int s = 0; s < NS; ++s)
+      if (blockIdx.x + s * gridDim.x < ntiles) issue(blockIdx.x + s * gridDim.x, s);
   }
   __syncthreads();
-  if (tid == 0) {
-    const uint32_t bytes = 4u * (TL::NP + 4 * 32 * 32 + (chk ? 32 * 32 : 0));
-    tma::mbar_expect_tx(&bar[0], bytes);
-    tma::load_2d(sm + TT::PSI, &tm.psi, j0 - TL::HX, i0 - TL::HY, &bar[0]);
-    tma::load_2d(sm + TT::B1, &tm.e1, j0, i0, &bar[0]);
-    tma::load_2d(sm + TT::B2, &tm.e2, j0, i0, &bar[0]);
-    tma::load_2d(sm + TT::U1, &tm.w1c, j0, i0, &bar[0]);
-    tma::load_2d(sm + TT::U2, &tm.w2c, j0, i0, &bar[0]);
-    if (chk) tma::load_2d(sm + TT::PO, &tm.phi_old, j0, i0, &bar[0]);
-  }
-  bool ok = tma::mbar_wait(&bar[0], 0);
-  if (!__syncthreads_and(ok)) {
-    if (tid == 0) tma::on_timeout(&bar[0], 0, a.err);
-    return;
-  }
-  const float* t_psi = sm + TT::PSI;
-  int any = 0;
-  for (int idx = tid; idx < TL::NP; idx += kTN) any |= in_band(t_psi[idx], m);
-  const bool band = __syncthreads_or(any) != 0;
   const int ty = threadIdx.y, tx = threadIdx.x;
-  const int c32 = ty * 32 + 4 * tx;
-  // w^k of the thread's pixels before the window sum reuses U1/U2
-  auto f4 = [&](int off) { return *reinterpret_cast<const float4*>(sm + off); };
-  const float4 W1 = f4(TT::U1 + c32), W2 = f4(TT::U2 + c32);
-  float v1[4] = {0.f, 0.f, 0.f, 0.f}, v2[4] = {0.f, 0.f, 0.f, 0.f};
-  if (band) {
-    __syncthreads();  // every thread holds its w before U1/U2 are overwritten
-    if (tid == 0) {
-      tma::mbar_expect_tx(&bar[1], 4u * (2 * TL::NP + 32 * 32));
-      tma::load_2d(sm + TT::W1, &tm.w1, j0 - TL::HX, i0 - TL::HY, &bar[1]);
-      tma::load_2d(sm + TT::W2, &tm.w2, j0 - TL::HX, i0 - TL::HY, &bar[1]);
-      tma::load_2d(sm + TT::GG, &tm.g, j0, i0, &bar[1]);
-    }
-    ok = tma::mbar_wait(&bar[1], 0);
-    if (!__syncthreads_and(ok)) {
-      if (tid == 0) tma::on_timeout(&bar[1], 0, a.err);
+  const int q = (ty + TL::HY) * TL::SW + 4 * tx + TL::HX;
+  auto f4 = [](const float* p) { return *reinterpret_cast<const float4*>(p); };
+  uint32_t band_par = 0;
+  int it = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int s = it % NS;
+    const int i0 = (tile / tiles_x) * kT, j0 = (tile % tiles_x) * kT;
+    const int i = i0 + ty, j = j0 + 4 * tx;
+    const bool live = i < M && j < N;
+    const size_t o = (size_t)i * N + j;
+    if (!tma::mbar_wait(&bar[s], (uint32_t)(it / NS) & 1u)) *s_err = 1;
+    const float* st = sm + s * PP::STAGE;
+    const float4 X = f4(st + PP::PSI + q);
+    const bool band = __syncthreads_or(live && any_band4(X, m)) != 0;
+    if (*s_err) {
+      if (tid == 0) pipe_drain(bar, NS, it, tile, gridDim.x, ntiles, false, 0, a.err);
       return;
     }
-    window_sum<R>(t_psi, sm + TT::W1, sm + TT::W2, sm + TT::U1, sm + TT::U2, sm + TT::V1,
-                  sm + TT::V2, m, v1, v2);
-  }
-  const int i = i0 + ty, j = j0 + 4 * tx;
-  double part[2] = {0.0, 0.0};
-  if (i < M && j < N) {
-    const size_t o = (size_t)i * N + j;
-    const int q = (ty + TL::HY) * TL::SW + 4 * tx + TL::HX;
-    const float4 X = f4(TT::PSI + q);
-    const float4 DN = i < M - 1 ? f4(TT::PSI + q + TL::SW) : ld4(a.phi1 + j);
-    const float RT = j + 4 < N ? sm[TT::PSI + q + 4] : __ldg(a.phi1 + (size_t)i * N);
-    const float4 E1 = f4(TT::B1 + c32), E2 = f4(TT::B2 + c32);
-    const float4 G4 = band ? f4(TT::GG + c32) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float x[4] = {X.x, X.y, X.z, X.w};
-    const float dn[4] = {DN.x, DN.y, DN.z, DN.w}, rt[4] = {X.y, X.z, X.w, RT};
-    const float b1[4] = {E1.x + W1.x, E1.y + W1.y, E1.z + W1.z, E1.w + W1.w};
-    const float b2[4] = {E2.x + W2.x, E2.y + W2.y, E2.z + W2.z, E2.w + W2.w};
-    const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
-    float wo1[4], wo2[4], eo1[4], eo2[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      wb_point(m, x[t], dn[t] - x[t], rt[t] - x[t], b1[t], b2[t], gg[t], v1[t], v2[t], wo1[t],
-               wo2[t], eo1[t], eo2[t]);
-    st4(a.w1o + o, make_float4(wo1[0], wo1[1], wo1[2], wo1[3]));
-    st4(a.w2o + o, make_float4(wo2[0], wo2[1], wo2[2], wo2[3]));
-    st4(a.e1o + o, make_float4(eo1[0], eo1[1], eo1[2], eo1[3]));
-    st4(a.e2o + o, make_float4(eo2[0], eo2[1], eo2[2], eo2[3]));
-    if (chk) {
-      const float4 P = f4(TT::PO + c32);
-      const float po[4] = {P.x, P.y, P.z, P.w};
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const double df = (double)x[t] - (double)po[t];
-        part[0] += df * df;
-        part[1] += (double)po[t] * (double)po[t];
+    float v1[4] = {0.f, 0.f, 0.f, 0.f}, v2[4] = {0.f, 0.f, 0.f, 0.f};
+    float4 W1 = make_float4(0.f, 0.f, 0.f, 0.f), W2 = W1, G4 = W1;
+    if (band) {  // uniform across the block
+      if (tid == 0) {
+        tma::fence_async_smem();
+        tma::mbar_expect_tx(&bar[NS], PB::BYTES);
+        tma::load_2d(bs + PB::W1, &tm.w1, j0 - TL::HX, i0 - TL::HY, &bar[NS]);
+        tma::load_2d(bs + PB::W2, &tm.w2, j0 - TL::HX, i0 - TL::HY, &bar[NS]);
+        tma::load_2d(bs + PB::GG, &tm.g, j0, i0, &bar[NS]);
       }
+      if (live) {
+        W1 = ld4(a.w1 + o);
+        W2 = ld4(a.w2 + o);
+      }
+      const bool ok = tma::mbar_wait(&bar[NS], band_par);
+      if (!__syncthreads_and(ok)) {
+        if (tid == 0) pipe_drain(bar, NS, it, tile, gridDim.x, ntiles, true, band_par, a.err);
+        return;
+      }
+      band_par ^= 1u;
+      G4 = f4(bs + PB::GG + ty * 32 + 4 * tx);
+      window_sum<R>(st + PP::PSI, bs + PB::W1, bs + PB::W2, bs + PB::W1, bs + PB::W2,
+                    bs + PB::V1, bs + PB::V2, m, v1, v2);
+    }
+    if (live) {
+      const float4 UP = i > 0 ? f4(st + PP::PSI + q - TL::SW) : ld4(a.psi + (size_t)(M - 1) * N + j);
+      const float4 DN = i < M - 1 ? f4(st + PP::PSI + q + TL::SW) : ld4(a.psi + j);
+      const float LF = j > 0 ? st[PP::PSI + q - 1] : __ldg(a.psi + (size_t)i * N + N - 1);
+      const float RT = j + 4 < N ? st[PP::PSI + q + 4] : __ldg(a.psi + (size_t)i * N);
+      const float4 E1 = f4(st + PP::E1 + (ty + 1) * 32 + 4 * tx);
+      const float4 E1u =
+          i > 0 ? f4(st + PP::E1 + ty * 32 + 4 * tx) : ld4(a.e1 + (size_t)(M - 1) * N + j);
+      const float4 E2 = f4(st + PP::E2 + ty * 36 + 4 + 4 * tx);
+      const float e2l =
+          j > 0 ? st[PP::E2 + ty * 36 + 3 + 4 * tx] : __ldg(a.e2 + (size_t)i * N + N - 1);
+      const float x[4] = {X.x, X.y, X.z, X.w};
+      const float up[4] = {UP.x, UP.y, UP.z, UP.w}, dn[4] = {DN.x, DN.y, DN.z, DN.w};
+      const float lf[4] = {LF, X.x, X.y, X.z}, rt[4] = {X.y, X.z, X.w, RT};
+      const float e1[4] = {E1.x, E1.y, E1.z, E1.w}, e2[4] = {E2.x, E2.y, E2.z, E2.w};
+      const float e1u[4] = {E1u.x, E1u.y, E1u.z, E1u.w}, e2l4[4] = {e2l, E2.x, E2.y, E2.z};
+      const float w1[4] = {W1.x, W1.y, W1.z, W1.w}, w2[4] = {W2.x, W2.y, W2.z, W2.w};
+      const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
+      float out[4];
+      if (band) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          out[t] = rhs_point<true>(m, x[t], up[t], dn[t], lf[t], rt[t], e1[t], e1u[t], e2[t],
+                                   e2l4[t], w1[t], w2[t], gg[t], v1[t], v2[t]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          out[t] = rhs_point<false>(m, x[t], up[t], dn[t], lf[t], rt[t], e1[t], e1u[t], e2[t],
+                                    e2l4[t], w1[t], w2[t], gg[t], v1[t], v2[t]);
+      }
+      st4(a.G + o, make_float4(out[0], out[1], out[2], out[3]));
+    }
+    __syncthreads();  // stage s and the band buffers are free again
+    if (tid == 0 && tile + NS * (int)gridDim.x < ntiles) {
+      tma::fence_async_smem();
+      issue(tile + NS * gridDim.x, s);
     }
   }
-  if (chk) block_sum_store<2>(part, a.partials + 2 * (blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+template <int R>
+__global__ void __launch_bounds__(kTN, 2) k_wb_tma(const WBArgs a, const __grid_constant__ WBMaps tm) {
+  using TL = Tile<R>;
+  using PW = PipeW<R>;
+  using PB = PipeBand<R>;
+  constexpr int NS = kWbStages;
+  extern __shared__ __align__(16) unsigned char smem_tt[];
+  float* sm = align128(smem_tt);
+  float* bs = sm + NS * PW::STAGE;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(bs + PB::FLOATS);
+  volatile int* s_err = reinterpret_cast<volatile int*>(bar + NS + 1);
+  const int tid = threadIdx.y * kTBX + threadIdx.x;
+  const int M = a.geo.M, N = a.geo.N;
+  const int tiles_x = (N + kT - 1) / kT, ntiles = tiles_x * ((M + kT - 1) / kT);
+  const Model& m = a.mod;
+  const bool chk = a.phi_old != nullptr;
+  auto issue = [&](int tile, int s) {
+    const int i0 = (tile / tiles_x) * kT, j0 = (tile % tiles_x) * kT;
+    float* st = sm + s * PW::STAGE;
+    tma::mbar_expect_tx(&bar[s], PW::BYTES + (chk ? 4096u : 0u));
+    tma::load_2d(st + PW::PSI, &tm.psi, j0 - TL::HX, i0 - TL::HY, &bar[s]);
+    tma::load_2d(st + PW::E1, &tm.e1, j0, i0, &bar[s]);
+    tma::load_2d(st + PW::E2, &tm.e2, j0, i0, &bar[s]);
+    tma::load_2d(st + PW::W1, &tm.w1c, j0, i0, &bar[s]);
+    tma::load_2d(st + PW::W2, &tm.w2c, j0, i0, &bar[s]);
+    if (chk) tma::load_2d(st + PW::PO, &tm.phi_old, j0, i0, &bar[s]);
+  };
+  if (tid == 0) {
+    for (int s = 0; s <= NS; ++s) tma::mbar_init(&bar[s], 1);
+    *s_err = 0;
+    tma::mbar_init_fence();
+    for (int s = 0; s < NS; ++s)
+      if (blockIdx.x + s * gridDim.x < ntiles) issue(blockIdx.x + s * gridDim.x, s);
+  }
+  __syncthreads();
+  const int ty = threadIdx.y, tx = threadIdx.x;
+  const int q = (ty + TL::HY) * TL::SW + 4 * tx + TL::HX;
+  const int c32 = ty * 32 + 4 * tx;
+  auto f4 = [](const float* p) { return *reinterpret_cast<const float4*>(p); };
+  uint32_t band_par = 0;
+  int it = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int s = it % NS;
+    const int i0 = (tile / tiles_x) * kT, j0 = (tile % tiles_x) * kT;
+    const int i = i0 + ty, j = j0 + 4 * tx;
+    const bool live = i < M && j < N;
+    const size_t o = (size_t)i * N + j;
+    if (!tma::mbar_wait(&bar[s], (uint32_t)(it / NS) & 1u)) *s_err = 1;
+    const float* st = sm + s * PW::STAGE;
+    const float4 X = f4(st + PW::PSI + q);
+    const bool band = __syncthreads_or(live && any_band4(X, m)) != 0;
+    if (*s_err) {
+      if (tid == 0) pipe_drain(bar, NS, it, tile, gridDim.x, ntiles, false, 0, a.err);
+      return;
+    }
+    float v1[4] = {0.f, 0.f, 0.f, 0.f}, v2[4] = {0.f, 0.f, 0.f, 0.f};
+    float4 G4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (band) {  // uniform across the block
+      if (tid == 0) {
+        tma::fence_async_smem();
+        tma::mbar_expect_tx(&bar[NS], PB::BYTES);
+        tma::load_2d(bs + PB::W1, &tm.w1, j0 - TL::HX, i0 - TL::HY, &bar[NS]);
+        tma::load_2d(bs + PB::W2, &tm.w2, j0 - TL::HX, i0 - TL::HY, &bar[NS]);
+        tma::load_2d(bs + PB::GG, &tm.g, j0, i0, &bar[NS]);
+      }
+      const bool ok = tma::mbar_wait(&bar[NS], band_par);
+      if (!__syncthreads_and(ok)) {
+        if (tid == 0) pipe_drain(bar, NS, it, tile, gridDim.x, ntiles, true, band_par, a.err);
+        return;
+      }
+      band_par ^= 1u;
+      G4 = f4(bs + PB::GG + c32);
+      window_sum<R>(st + PW::PSI, bs + PB::W1, bs + PB::W2, bs + PB::W1, bs + PB::W2,
+                    bs + PB::V1, bs + PB::V2, m, v1, v2);
+    }
+    double part[2] = {0.0, 0.0};
+    if (live) {
+      const float4 DN = i < M - 1 ? f4(st + PW::PSI + q + TL::SW) : ld4(a.phi1 + j);
+      const float RT = j + 4 < N ? st[PW::PSI + q + 4] : __ldg(a.phi1 + (size_t)i * N);
+      const float4 E1 = f4(st + PW::E1 + c32), E2 = f4(st + PW::E2 + c32);
+      const float4 W1 = f4(st + PW::W1 + c32), W2 = f4(st + PW::W2 + c32);
+      const float x[4] = {X.x, X.y, X.z, X.w};
+      const float dn[4] = {DN.x, DN.y, DN.z, DN.w}, rt[4] = {X.y, X.z, X.w, RT};
+      const float b1[4] = {E1.x + W1.x, E1.y + W1.y, E1.z + W1.z, E1.w + W1.w};
+      const float b2[4] = {E2.x + W2.x, E2.y + W2.y, E2.z + W2.z, E2.w + W2.w};
+      const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
+      float wo1[4], wo2[4], eo1[4], eo2[4];
+      if (band) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          wb_point<true>(m, x[t], dn[t] - x[t], rt[t] - x[t], b1[t], b2[t], gg[t], v1[t], v2[t],
+                         wo1[t], wo2[t], eo1[t], eo2[t]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          wb_point<false>(m, x[t], dn[t] - x[t], rt[t] - x[t], b1[t], b2[t], gg[t], v1[t], v2[t],
+                          wo1[t], wo2[t], eo1[t], eo2[t]);
+      }
+      st4(a.w1o + o, make_float4(wo1[0], wo1[1], wo1[2], wo1[3]));
+      st4(a.w2o + o, make_float4(wo2[0], wo2[1], wo2[2], wo2[3]));
+      st4(a.e1o + o, make_float4(eo1[0], eo1[1], eo1[2], eo1[3]));
+      st4(a.e2o + o, make_float4(eo2[0], eo2[1], eo2[2], eo2[3]));
+      if (chk) {
+        const float4 P = f4(st + PW::PO + c32);
+        const float po[4] = {P.x, P.y, P.z, P.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const double df = (double)x[t] - (double)po[t];
+          part[0] += df * df;
+          part[1] += (double)po[t] * (double)po[t];
+        }
+      }
+    }
+    if (chk) block_sum_store<2>(part, a.partials + 2 * tile);
+    __syncthreads();  // stage s and the band buffers are free again
+    if (tid == 0 && tile + NS * (int)gridDim.x < ntiles) {
+      tma::fence_async_smem();
+      issue(tile + NS * gridDim.x, s);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kTileX* kTileY) k_repulsion(const RepArgs a) {
@@ -1117,8 +1336,8 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_energy(const EnergyArgs a) {
     float d1, d2;
     grad(i, j, d1, d2);
     const double gg = a.g[o];
-    part[0] = gg * (double)sqrtf(d1 * d1 + d2 * d2) * (double)deps(x, m.eps);
-    part[1] = gg * (1.0 - (double)heps(x, m.eps));
+    part[0] = gg * (double)sqrtf(d1 * d1 + d2 * d2) * (double)deps(x, m);
+    part[1] = gg * (1.0 - (double)heps(x, m));
     part[2] = -(double)band_h(x, m) * ((double)d1 * v1 + (double)d2 * v2);
   }
   block_sum_store<3>(part, a.partials + 3 * (blockIdx.y * gridDim.x + blockIdx.x));
@@ -1314,25 +1533,43 @@ cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-size_t tile_tma_smem(int R) {
+size_t tile_tma_smem(int R, bool wb) {
   switch (R) {
-#define SR_CASE(r) \
-  case r: return (size_t)TileT<r>::FLOATS * sizeof(float) + 128;
+#define SR_CASE(r)                                                                            \
+  case r:                                                                                     \
+    return (size_t)(wb ? pipe_floats<PipeW<r>, PipeBand<r>, kWbStages>()                      \
+                       : pipe_floats<PipeP<r>, PipeBand<r>, kPrepStages>()) * sizeof(float) + \
+           128;
     SR_FOR_R(SR_CASE)
 #undef SR_CASE
   }
   return 0;
 }
 
+// Persistent grid: SMs x resident CTAs, capped by the number of tiles.
+template <class K>
+static int tile_pipe_grid(K kernel, size_t smem, int ntiles) {
+  int dev = 0, nsm = 1, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kTN, smem) != cudaSuccess ||
+      per < 1)
+    per = 1;
+  return ntiles < nsm * per ? ntiles : nsm * per;
+}
+
 int tile_halo_x(int R) { return R > 4 ? 8 : 4; }
 int tile_halo_y(int R) { return R > 1 ? R : 1; }
 
 cudaError_t launch_prep_tma(const PrepArgs& a, const PrepMaps& tm, cudaStream_t s) {
-  const dim3 g = tile32_grid(a.geo), b(kTBX, kTBY);
-  const size_t sm = tile_tma_smem(a.mod.R);
+  const dim3 b(kTBX, kTBY);
+  const size_t sm = tile_tma_smem(a.mod.R, false);
+  const int nt = tile32_blocks(a.geo);
   switch (a.mod.R) {
-#define SR_CASE(r) \
-  case r: k_prep_tma<r><<<g, b, sm, s>>>(a, tm); break;
+#define SR_CASE(r)                                                                 \
+  case r:                                                                          \
+    k_prep_tma<r><<<tile_pipe_grid(k_prep_tma<r>, sm, nt), b, sm, s>>>(a, tm); \
+    break;
     SR_FOR_R(SR_CASE)
 #undef SR_CASE
     default: return cudaErrorInvalidValue;
@@ -1341,11 +1578,14 @@ cudaError_t launch_prep_tma(const PrepArgs& a, const PrepMaps& tm, cudaStream_t 
 }
 
 cudaError_t launch_wb_tma(const WBArgs& a, const WBMaps& tm, cudaStream_t s) {
-  const dim3 g = tile32_grid(a.geo), b(kTBX, kTBY);
-  const size_t sm = tile_tma_smem(a.mod.R);
+  const dim3 b(kTBX, kTBY);
+  const size_t sm = tile_tma_smem(a.mod.R, true);
+  const int nt = tile32_blocks(a.geo);
   switch (a.mod.R) {
-#define SR_CASE(r) \
-  case r: k_wb_tma<r><<<g, b, sm, s>>>(a, tm); break;
+#define SR_CASE(r)                                                               \
+  case r:                                                                        \
+    k_wb_tma<r><<<tile_pipe_grid(k_wb_tma<r>, sm, nt), b, sm, s>>>(a, tm); \
+    break;
     SR_FOR_R(SR_CASE)
 #undef SR_CASE
     default: return cudaErrorInvalidValue;
