@@ -287,7 +287,9 @@ template <int LOGM, int CB, int LOGE>
 __host__ __device__ constexpr int col_threads() { return CB * (1 << LOGM) / (1 << LOGE); }
 template <int LOGM, int CB, int LOGE>
 __host__ __device__ constexpr int col_min_blocks() {
-  return (LOGE == 3 && col_threads<LOGM, CB, LOGE>() <= 512) ? 3 : 1;
+  return (LOGE == 3 && col_threads<LOGM, CB, LOGE>() <= 512) ? 3
+         : (col_threads<LOGM, CB, LOGE>() <= 256)            ? 2
+                                                              : 1;
 }
 
 template <int LOGM, int CB, int LOGE>
@@ -303,10 +305,17 @@ __global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), col_min_blocks<
   const int k = c0 + c;
   float2* base = smem2 + c;
   float2* stw = smem2 + CB * (M + M / 16);
+  float* sM = reinterpret_cast<float*>(stw + TwPlan<LOGM, LOGE>::TOTAL);
   float2 x[E];
 #pragma unroll
   for (int m = 0; m < E; ++m) x[m] = a.X[(size_t)(u + (m << LOGTP)) * L + k];
+  // the symbol's row part and this column's part are fetched with the data,
+  // so that the scaling between the two transforms waits on shared memory only
+  const float ak = a.aN[k];
+  const float a0 = a.aN[0], aNy = a.aN[L];
+  for (int q = threadIdx.x; q < M; q += blockDim.x) sM[q] = __ldg(a.aM + q);
   stage_table<TwPlan<LOGM, LOGE>::TOTAL>(stw, LOGE == 4 ? a.fft.tws16 : a.fft.tws8);
+  if constexpr (TwPlan<LOGM, LOGE>::NST == 1) __syncthreads();  // no exchange barrier before use
   stages<LOGM, LOGE, 0, false, CB>(x, base, u, stw);
   const float inv_mn = 1.f / ((float)M * (float)a.geo.N);
   if (c0 == 0) {
@@ -318,13 +327,12 @@ __global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), col_min_blocks<
     }
     __syncthreads();
     if (c == 0) {
-      const float aNy = a.aN[L];
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         const int l = u + (m << LOGTP);
         const float2 Cl = x[m], Cm = base[pad((M - l) & (M - 1)) * CB];
-        const float sA = inv_mn / (1.f + a.aM[l] + a.aN[0]);
-        const float sB = inv_mn / (1.f + a.aM[l] + aNy);
+        const float sA = inv_mn / (1.f + sM[l] + a0);
+        const float sB = inv_mn / (1.f + sM[l] + aNy);
         const float2 A = make_float2(0.5f * (Cl.x + Cm.x) * sA, 0.5f * (Cl.y - Cm.y) * sA);
         const float2 D = make_float2(0.5f * (Cl.x - Cm.x), 0.5f * (Cl.y + Cm.y));
         const float2 B = make_float2(D.y * sB, -D.x * sB);
@@ -334,11 +342,10 @@ __global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), col_min_blocks<
     __syncthreads();
   }
   if (k != 0) {
-    const float ak = a.aN[k];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-      const float s = inv_mn / (1.f + a.aM[u + (m << LOGTP)] + ak);
-      x[m] = make_float2(x[m].x * s, x[m].y * s);
+      const float sc = inv_mn / (1.f + sM[u + (m << LOGTP)] + ak);
+      x[m] = make_float2(x[m].x * sc, x[m].y * sc);
     }
   }
   stages<LOGM, LOGE, 0, true, CB>(x, base, u, stw);
@@ -512,7 +519,8 @@ static cudaError_t rowifft_go(const RowInvArgs& a, bool add, int nthreads, size_
 template <int LOGM, int CB, int LOGE>
 static cudaError_t col_go(const ColArgs& a, cudaStream_t s, bool set_attr) {
   constexpr int M = 1 << LOGM;
-  const size_t smem = ((size_t)CB * (M + M / 16) + TwPlan<LOGM, LOGE>::TOTAL) * sizeof(float2);
+  const size_t smem = ((size_t)CB * (M + M / 16) + TwPlan<LOGM, LOGE>::TOTAL) * sizeof(float2) +
+                      (size_t)M * sizeof(float);
   if (set_attr) return set_smem(k_colsolve2<LOGM, CB, LOGE>, smem);
   k_colsolve2<LOGM, CB, LOGE><<<a.geo.L / CB, CB * M / (1 << LOGE), smem, s>>>(a);
   return cudaGetLastError();
@@ -572,12 +580,14 @@ cudaError_t launch_rowifft2(const RowInvArgs& a, bool add, int logE, int nthread
   return cudaErrorInvalidValue;
 }
 
-// column schedules: 0 = (CB 4, E 16), 1 = (CB 2, E 8), 2 = (CB 4, E 8)
+// column schedules: 0 = (CB 4, E 16), 1 = (CB 2, E 8), 2 = (CB 4, E 8),
+// 4 = (CB 2, E 16)
 cudaError_t launch_colsolve2(const ColArgs& a, int sched, cudaStream_t s, bool set_attr) {
 #define SR_COL(lm)                                                   \
   case (1 << lm):                                                    \
     if (sched == 1) return col_go<lm, 2, 3>(a, s, set_attr);         \
     if (sched == 2) return col_go<lm, 4, 3>(a, s, set_attr);         \
+    if (sched == 4) return col_go<lm, 2, 4>(a, s, set_attr);         \
     return (lm == 12) ? col_go<lm, 2, 4>(a, s, set_attr) : col_go<lm, 4, 4>(a, s, set_attr);
   switch (a.geo.M) {
     SR_COL(4) SR_COL(5) SR_COL(6) SR_COL(7) SR_COL(8) SR_COL(9) SR_COL(10) SR_COL(11) SR_COL(12)
@@ -633,6 +643,7 @@ int colsolve2_threads(int M, int sched) {
   if (sched == 3) return colsolve_tma_cb(M) * M / 16;
   if (sched == 1) return 2 * M / 8;
   if (sched == 2) return 4 * M / 8;
+  if (sched == 4) return 2 * M / 16;
   return M == 4096 ? 2 * M / 16 : 4 * M / 16;
 }
 
