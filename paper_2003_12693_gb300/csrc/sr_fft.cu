@@ -196,11 +196,13 @@ __global__ void __launch_bounds__(512) k_rowfft(const RowFwdArgs a) {
   const bool live = i < a.geo.M;
   float2* base = smem2 + t * S;
   float2* stw = smem2 + a.T * S;
+  stage_table<TwPlan<LOGL, LOGE>::TOTAL>(stw, LOGE == 4 ? a.fft.tws16 : a.fft.tws8);
+  pdl_wait();
+  pdl_trigger();
   float2 x[E];
   const float2* row = reinterpret_cast<const float2*>(a.src + (size_t)(live ? i : 0) * a.geo.N);
 #pragma unroll
   for (int m = 0; m < E; ++m) x[m] = live ? __ldg(row + u + (m << LOGTP)) : make_float2(0.f, 0.f);
-  stage_table<TwPlan<LOGL, LOGE>::TOTAL>(stw, LOGE == 4 ? a.fft.tws16 : a.fft.tws8);
   stages<LOGL, LOGE, 0, false, 1>(x, base, u, stw);
   // even/odd split needs Z_{L-k}: exchange through shared memory
 #pragma unroll
@@ -241,6 +243,8 @@ __global__ void __launch_bounds__(512) k_rowifft(const RowInvArgs a) {
   float2* base = smem2 + t * S;
   float2* stw = smem2 + a.T * S;
   stage_table<TwPlan<LOGL, LOGE>::TOTAL>(stw, LOGE == 4 ? a.fft.tws16 : a.fft.tws8);
+  pdl_wait();
+  pdl_trigger();
   float2 p[E];
   if (ADD) {
     const float2* prow = reinterpret_cast<const float2*>(a.psi_in + (size_t)ii * a.geo.N);
@@ -306,15 +310,17 @@ __global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), col_min_blocks<
   float2* base = smem2 + c;
   float2* stw = smem2 + CB * (M + M / 16);
   float* sM = reinterpret_cast<float*>(stw + TwPlan<LOGM, LOGE>::TOTAL);
-  float2 x[E];
-#pragma unroll
-  for (int m = 0; m < E; ++m) x[m] = a.X[(size_t)(u + (m << LOGTP)) * L + k];
-  // the symbol's row part and this column's part are fetched with the data,
-  // so that the scaling between the two transforms waits on shared memory only
+  // the symbol (constant tables) is fetched before the data, so that the
+  // scaling between the two transforms waits on shared memory only
   const float ak = a.aN[k];
   const float a0 = a.aN[0], aNy = a.aN[L];
   for (int q = threadIdx.x; q < M; q += blockDim.x) sM[q] = __ldg(a.aM + q);
   stage_table<TwPlan<LOGM, LOGE>::TOTAL>(stw, LOGE == 4 ? a.fft.tws16 : a.fft.tws8);
+  pdl_wait();
+  pdl_trigger();
+  float2 x[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) x[m] = a.X[(size_t)(u + (m << LOGTP)) * L + k];
   if constexpr (TwPlan<LOGM, LOGE>::NST == 1) __syncthreads();  // no exchange barrier before use
   stages<LOGM, LOGE, 0, false, CB>(x, base, u, stw);
   const float inv_mn = 1.f / ((float)M * (float)a.geo.N);
@@ -376,6 +382,8 @@ __host__ __device__ constexpr size_t col_tma_smem() {
 template <int LOGM, int CB, int LOGE>
 __global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), 1)
     k_colsolve_tma(const ColArgs a, const __grid_constant__ CUtensorMap tmX) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int E = 1 << LOGE, M = 1 << LOGM, LOGTP = LOGM - LOGE;
   constexpr int BOXR = M < 256 ? M : 256;
   constexpr int NBOX = M / BOXR;
@@ -499,8 +507,7 @@ template <int LOGL, int LOGE>
 static cudaError_t rowfft_go(const RowFwdArgs& a, int nthreads, size_t smem, cudaStream_t s,
                              bool set_attr) {
   if (set_attr) return set_smem(k_rowfft<LOGL, LOGE>, smem);
-  k_rowfft<LOGL, LOGE><<<(a.geo.M + a.T - 1) / a.T, nthreads, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_k(k_rowfft<LOGL, LOGE>, dim3((a.geo.M + a.T - 1) / a.T), dim3(nthreads), smem, s, a);
 }
 
 template <int LOGL, int LOGE>
@@ -511,9 +518,8 @@ static cudaError_t rowifft_go(const RowInvArgs& a, bool add, int nthreads, size_
     return e != cudaSuccess ? e : set_smem(k_rowifft<LOGL, LOGE, false>, smem);
   }
   const int grid = (a.geo.M + a.T - 1) / a.T;
-  if (add) k_rowifft<LOGL, LOGE, true><<<grid, nthreads, smem, s>>>(a);
-  else k_rowifft<LOGL, LOGE, false><<<grid, nthreads, smem, s>>>(a);
-  return cudaGetLastError();
+  if (add) return launch_k(k_rowifft<LOGL, LOGE, true>, dim3(grid), dim3(nthreads), smem, s, a);
+  return launch_k(k_rowifft<LOGL, LOGE, false>, dim3(grid), dim3(nthreads), smem, s, a);
 }
 
 template <int LOGM, int CB, int LOGE>
@@ -522,8 +528,8 @@ static cudaError_t col_go(const ColArgs& a, cudaStream_t s, bool set_attr) {
   const size_t smem = ((size_t)CB * (M + M / 16) + TwPlan<LOGM, LOGE>::TOTAL) * sizeof(float2) +
                       (size_t)M * sizeof(float);
   if (set_attr) return set_smem(k_colsolve2<LOGM, CB, LOGE>, smem);
-  k_colsolve2<LOGM, CB, LOGE><<<a.geo.L / CB, CB * M / (1 << LOGE), smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_k(k_colsolve2<LOGM, CB, LOGE>, dim3(a.geo.L / CB), dim3(CB * M / (1 << LOGE)), smem,
+                  s, a);
 }
 
 bool fft2_supported(const Geo& geo) { return geo.L >= 16 && geo.L <= 2048 && geo.M >= 16 && geo.M <= 4096; }
@@ -601,8 +607,8 @@ static cudaError_t col_tma_go(const ColArgs& a, const CUtensorMap& tm, int grid,
                               bool set_attr) {
   const size_t smem = col_tma_smem<LOGM, CB>();
   if (set_attr) return set_smem(k_colsolve_tma<LOGM, CB, LOGE>, smem);
-  k_colsolve_tma<LOGM, CB, LOGE><<<grid, col_threads<LOGM, CB, LOGE>(), smem, s>>>(a, tm);
-  return cudaGetLastError();
+  return launch_k(k_colsolve_tma<LOGM, CB, LOGE>, dim3(grid), dim3(col_threads<LOGM, CB, LOGE>()),
+                  smem, s, a, tm);
 }
 
 // schedule 3: persistent TMA columns (4 columns x 16 values; 2 columns at H = 4096)

@@ -15,6 +15,36 @@ constexpr int kTileX = 32;      // 2-D tile of the window-sum kernels
 constexpr int kTileY = 8;
 constexpr int kMaxGauss = 32;   // taps of the edge-detector Gaussian
 
+// Programmatic dependent launch.  The kernels of the iteration are launched
+// with programmatic stream serialization, so a kernel's CTAs may be resident
+// while its predecessor on the stream is still finishing.  Every such kernel
+// executes pdl_wait() in every CTA before it reads anything a predecessor
+// wrote (and before it can exit), then pdl_trigger() to let its own successor
+// be scheduled.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// whether hot-path launches carry the attribute (SR_PDL=0 turns it off)
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t s, const Args&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Scalar model parameters in FP32 as the kernels use them.
 struct Model {
   float alpha, beta, gamma, mu, tau, eps, band_l;

@@ -22,6 +22,8 @@
 
 #include <algorithm>
 
+#include <cstdlib>
+
 #include "sr_internal.h"
 #include "sr_tma.cuh"
 
@@ -844,6 +846,8 @@ __device__ __forceinline__ int any_band4(float4 v, const Model& m) {
 template <int R>
 __global__ void __launch_bounds__(kTN, 4) k_prep(const PrepArgs a) {
   extern __shared__ __align__(16) float smem_f[];
+  pdl_wait();
+  pdl_trigger();
   const Model& m = a.mod;
   const int N = a.geo.N;
   const Quad q(a.geo);
@@ -910,6 +914,8 @@ __global__ void __launch_bounds__(kTN, 4) k_prep(const PrepArgs a) {
 template <int R>
 __global__ void __launch_bounds__(kTN, 4) k_wb_update(const WBArgs a) {
   extern __shared__ __align__(16) float smem_f[];
+  pdl_wait();
+  pdl_trigger();
   const Model& m = a.mod;
   const int N = a.geo.N;
   const Quad q(a.geo);
@@ -1054,6 +1060,8 @@ __global__ void __launch_bounds__(kTN, 3) k_prep_tma(const PrepArgs a, const __g
   using PB = PipeBand<R>;
   constexpr int NS = kPrepStages;
   extern __shared__ __align__(16) unsigned char smem_tt[];
+  pdl_wait();
+  pdl_trigger();
   float* sm = align128(smem_tt);
   float* bs = sm + NS * PP::STAGE;
   uint64_t* bar = reinterpret_cast<uint64_t*>(bs + PB::FLOATS);
@@ -1168,6 +1176,8 @@ __global__ void __launch_bounds__(kTN, 2) k_wb_tma(const WBArgs a, const __grid_
   using PB = PipeBand<R>;
   constexpr int NS = kWbStages;
   extern __shared__ __align__(16) unsigned char smem_tt[];
+  pdl_wait();
+  pdl_trigger();
   float* sm = align128(smem_tt);
   float* bs = sm + NS * PW::STAGE;
   uint64_t* bar = reinterpret_cast<uint64_t*>(bs + PB::FLOATS);
@@ -1346,6 +1356,8 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_energy(const EnergyArgs a) {
 // Sum the per-CTA partials in a fixed order (one CTA, deterministic).
 __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ partials, int nblocks,
                                                 int ncomp, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double red[4][256];
   for (int c = 0; c < ncomp; ++c) {
     double s = 0.0;
@@ -1472,6 +1484,14 @@ static cudaError_t allow_big_smem(K kernel) {
                               optin - (int)fa.sharedSizeBytes);
 }
 
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* env = std::getenv("SR_PDL");
+    return !(env && env[0] == '0');
+  }();
+  return on;
+}
+
 cudaError_t configure_kernels() {
   cudaError_t e;
   if ((e = allow_big_smem(k_rowfwd<kRowRHS>))) return e;
@@ -1525,7 +1545,7 @@ cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s) {
   const size_t sm = tile32_smem(a.mod.R);
   switch (a.mod.R) {
 #define SR_CASE(r) \
-  case r: k_wb_update<r><<<g, b, sm, s>>>(a); break;
+  case r: return launch_k(k_wb_update<r>, g, b, sm, s, a);
     SR_FOR_R(SR_CASE)
 #undef SR_CASE
     default: return cudaErrorInvalidValue;
@@ -1568,8 +1588,7 @@ cudaError_t launch_prep_tma(const PrepArgs& a, const PrepMaps& tm, cudaStream_t 
   switch (a.mod.R) {
 #define SR_CASE(r)                                                                 \
   case r:                                                                          \
-    k_prep_tma<r><<<tile_pipe_grid(k_prep_tma<r>, sm, nt), b, sm, s>>>(a, tm); \
-    break;
+    return launch_k(k_prep_tma<r>, dim3(tile_pipe_grid(k_prep_tma<r>, sm, nt)), b, sm, s, a, tm);
     SR_FOR_R(SR_CASE)
 #undef SR_CASE
     default: return cudaErrorInvalidValue;
@@ -1584,8 +1603,7 @@ cudaError_t launch_wb_tma(const WBArgs& a, const WBMaps& tm, cudaStream_t s) {
   switch (a.mod.R) {
 #define SR_CASE(r)                                                               \
   case r:                                                                        \
-    k_wb_tma<r><<<tile_pipe_grid(k_wb_tma<r>, sm, nt), b, sm, s>>>(a, tm); \
-    break;
+    return launch_k(k_wb_tma<r>, dim3(tile_pipe_grid(k_wb_tma<r>, sm, nt)), b, sm, s, a, tm);
     SR_FOR_R(SR_CASE)
 #undef SR_CASE
     default: return cudaErrorInvalidValue;
@@ -1598,7 +1616,7 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
   const size_t sm = tile32_smem(a.mod.R);
   switch (a.mod.R) {
 #define SR_CASE(r) \
-  case r: k_prep<r><<<g, b, sm, s>>>(a); break;
+  case r: return launch_k(k_prep<r>, g, b, sm, s, a);
     SR_FOR_R(SR_CASE)
 #undef SR_CASE
     default: return cudaErrorInvalidValue;
@@ -1618,8 +1636,7 @@ cudaError_t launch_energy(const EnergyArgs& a, cudaStream_t s) {
 
 cudaError_t launch_reduce(const double* partials, int nblocks, int ncomp, double* out,
                           cudaStream_t s) {
-  k_reduce<<<1, 256, 0, s>>>(partials, nblocks, ncomp, out);
-  return cudaGetLastError();
+  return launch_k(k_reduce, dim3(1), dim3(256), 0, s, partials, nblocks, ncomp, out);
 }
 
 static dim3 row_grid(const Geo& geo) { return dim3((geo.N + 127) / 128, geo.M); }
