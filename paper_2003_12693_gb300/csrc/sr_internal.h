@@ -53,6 +53,8 @@ struct Model {
   float inv_eps;    // 1 / eps
   float half_inv_eps;  // 1 / (2 eps), the scale of delta_eps (Eq. (6))
   float dp_scale;   // pi / (2 eps^2), the scale of delta'_eps (Eq. (29))
+  float l_eps;      // l / eps
+  float sin_l, cos_l;  // sin(pi l / eps), cos(pi l / eps)
   int R;            // window half width
   float kw[2 * kMaxR + 1];  // k(p) = exp(-p^2 / d^2), p = -R..R at index p + R
 };

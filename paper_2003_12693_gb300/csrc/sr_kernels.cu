@@ -220,19 +220,6 @@ __device__ __forceinline__ float deps(float x, const Model& m) {
   if (fabsf(y) > 1.f) return 0.f;
   return (1.f + cospif(y)) * m.half_inv_eps;
 }
-// H_eps and delta_eps of one argument from one sincospif
-__device__ __forceinline__ void hd_eps(float x, const Model& m, float& h, float& d) {
-  const float y = x * m.inv_eps;
-  if (fabsf(y) > 1.f) {
-    h = y > 0.f ? 1.f : 0.f;
-    d = 0.f;
-    return;
-  }
-  float sn, cs;
-  sincospif(y, &sn, &cs);
-  h = 0.5f * (1.f + y + sn * kInvPi);
-  d = (1.f + cs) * m.half_inv_eps;
-}
 // delta_eps and delta'_eps (Eq. (29)) of one argument
 __device__ __forceinline__ void dd_eps(float x, const Model& m, float& d, float& dp) {
   const float y = x * m.inv_eps;
@@ -245,16 +232,53 @@ __device__ __forceinline__ void dd_eps(float x, const Model& m, float& d, float&
   d = (1.f + cs) * m.half_inv_eps;
   dp = -m.dp_scale * sn;
 }
+// The band functions at x need H_eps and delta_eps at x + l and x - l, and
+// the rhs also delta_eps, delta'_eps at x.  All of them come from one
+// sincospif of y = x/eps: sin and cos at y +- l/eps follow by angle addition
+// with the host constants sin(pi l/eps), cos(pi l/eps) (absolute error a few
+// 1e-7, where the separate evaluations give about 1e-7).
+struct BandTrig {
+  float y, sn, cs;
+  __device__ __forceinline__ BandTrig(float x, const Model& m) {
+    y = x * m.inv_eps;
+    sincospif(y, &sn, &cs);
+  }
+  // H_eps and delta_eps at x + sign * l
+  __device__ __forceinline__ void at_shift(float sign, const Model& m, float& h, float& d) const {
+    const float Y = y + sign * m.l_eps;
+    const float sY = sn * m.cos_l + sign * cs * m.sin_l;
+    const float cY = cs * m.cos_l - sign * sn * m.sin_l;
+    const bool in = fabsf(Y) <= 1.f;
+    h = in ? 0.5f * (1.f + Y + sY * kInvPi) : (Y > 0.f ? 1.f : 0.f);
+    d = in ? (1.f + cY) * m.half_inv_eps : 0.f;
+  }
+  // delta_eps and delta'_eps at x
+  __device__ __forceinline__ void at_zero(const Model& m, float& d, float& dp) const {
+    const bool in = fabsf(y) <= 1.f;
+    d = in ? (1.f + cs) * m.half_inv_eps : 0.f;
+    dp = in ? -m.dp_scale * sn : 0.f;
+  }
+  // h(x) = H(x + l)(1 - H(x - l)) (Eq. (11)) and h'(x) (Eq. (28)), |x| < l + eps
+  __device__ __forceinline__ void band(const Model& m, float& h, float& hp) const {
+    float hA, dA, hB, dB;
+    at_shift(1.f, m, hA, dA);
+    at_shift(-1.f, m, hB, dB);
+    h = hA * (1.f - hB);
+    hp = dA * (1.f - hB) - hA * dB;
+  }
+};
+
 __device__ __forceinline__ float band_h(float x, const Model& m) {
   if (fabsf(x) >= m.band_l + m.eps) return 0.f;
-  return heps(x + m.band_l, m) * (1.f - heps(x - m.band_l, m));
+  float h, hp;
+  BandTrig(x, m).band(m, h, hp);
+  return h;
 }
 __device__ __forceinline__ float band_hp(float x, const Model& m) {
   if (fabsf(x) >= m.band_l + m.eps) return 0.f;
-  float hA, dA, hB, dB;
-  hd_eps(x + m.band_l, m, hA, dA);
-  hd_eps(x - m.band_l, m, hB, dB);
-  return dA * (1.f - hB) - hA * dB;
+  float h, hp;
+  BandTrig(x, m).band(m, h, hp);
+  return hp;
 }
 
 // ---------------------------------------------------------------------------
@@ -753,10 +777,11 @@ __device__ __forceinline__ float rhs_point(const Model& m, float x, float up, fl
   float force = m.mu * (dv + lap);
   if (BAND && in_band(x, m)) {
     const float wn = sqrtf(w1 * w1 + w2 * w2);
-    float dl, dpl;
-    dd_eps(x, m, dl, dpl);
-    force += -m.gamma * g * wn * dpl + m.alpha * g * dl +
-             2.f * m.beta * band_hp(x, m) * (w1 * v1 + w2 * v2);
+    const BandTrig bt(x, m);
+    float dl, dpl, hh, hp;
+    bt.at_zero(m, dl, dpl);
+    bt.band(m, hh, hp);
+    force += -m.gamma * g * wn * dpl + m.alpha * g * dl + 2.f * m.beta * hp * (w1 * v1 + w2 * v2);
   }
   return m.tau * force;
 }
@@ -772,10 +797,13 @@ __device__ __forceinline__ void wb_point(const Model& m, float x, float d1, floa
   float Bv2 = d2 + b2;
   float thr = 0.f;
   if (BAND && in_band(x, m)) {
-    const float h = band_h(x, m);
+    const BandTrig bt(x, m);
+    float h, hp, dl, dpl;
+    bt.band(m, h, hp);
+    bt.at_zero(m, dl, dpl);
     Bv1 = fmaf(m.beta2_mu * h, v1, Bv1);
     Bv2 = fmaf(m.beta2_mu * h, v2, Bv2);
-    thr = m.gamma_mu * g * deps(x, m);
+    thr = m.gamma_mu * g * dl;
   }
   // |B| and B/|B| from one reciprocal square root (a few ulp, against a
   // correctly rounded sqrt and two divisions)

@@ -149,6 +149,9 @@ extern "C" sr_status sr_phi_step_noalloc(int H, int W, const sr_params* p, const
   m.inv_eps = (float)(1.0 / (double)p->eps);
   m.half_inv_eps = (float)(0.5 / (double)p->eps);
   m.dp_scale = (float)(1.57079632679489661923 / ((double)p->eps * (double)p->eps));
+  m.l_eps = (float)((double)p->band_l / (double)p->eps);
+  m.sin_l = (float)std::sin(3.14159265358979323846 * (double)p->band_l / (double)p->eps);
+  m.cos_l = (float)std::cos(3.14159265358979323846 * (double)p->band_l / (double)p->eps);
   m.R = p->win_radius;
   for (int t = -m.R; t <= m.R; ++t)
     m.kw[t + m.R] = (float)std::exp(-(double)(t * t) / ((double)p->d * (double)p->d));
