@@ -204,7 +204,9 @@ sr_status sr_phi_step_noalloc(int H, int W, const sr_params* p, const float* g,
  *                 H = 4096); 1 = 2 columns, 8 values; 2 = 4 columns, 8 values;
  *                 3 = persistent CTAs fed by TMA (tensor-memory-accelerator
  *                 box loads/stores, double buffered), 4 columns, 16 values;
- *                 4 = 2 columns, 16 values
+ *                 4 = 2 columns, 16 values; 5 = 4 columns, 16 values with
+ *                 double-buffered exchanges; 6 = 4 columns, 16 values with
+ *                 registers capped for two CTAs per SM
  *   tuned_us: measured microseconds of one row pair plus one column pass
  *             when the autotuner chose the schedule, else 0.
  * Sizes below W = 32 use fixed kernels and report row_threads = 0.

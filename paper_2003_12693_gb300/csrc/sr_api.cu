@@ -271,7 +271,7 @@ int sched_rows(const sr_ctx* c, const sr_schedule& sc) {
 bool sched_valid(const sr_ctx* c, const sr_schedule& sc) {
   if (!c->fft2) return false;
   if (sc.row_values_per_thread != 8 && sc.row_values_per_thread != 16) return false;
-  if (sc.col_schedule < 0 || sc.col_schedule > 4) return false;
+  if (sc.col_schedule < 0 || sc.col_schedule > 6) return false;
   if (sc.col_schedule == 3 && !c->tm_X_ok) return false;
   if (srk::colsolve2_threads(c->H, sc.col_schedule) > 1024) return false;
   if (sc.row_threads < 1 || sc.row_threads > 512) return false;
@@ -475,7 +475,7 @@ sr_status autotune(sr_ctx* c) {
       }
     }
   float best_col = 1e30f;
-  for (int cs = 0; cs < 5 && err == cudaSuccess; ++cs) {
+  for (int cs = 0; cs < 7 && err == cudaSuccess; ++cs) {
     sr_schedule sc = best;
     sc.col_schedule = cs;
     if (!sched_valid(c, sc)) continue;

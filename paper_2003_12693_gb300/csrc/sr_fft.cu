@@ -132,9 +132,9 @@ __device__ __forceinline__ void stage_table(float2* dst, const float2* __restric
 // sequence offset).  The thread holds E = 2^LOGE values x[m] = seq[u + (L/E) m];
 // stages use radix E, the last one radix 2^(LOGL mod LOGE) if that is not 1.
 // stw is the stage-twiddle table in shared memory.
-template <int LOGL, int LOGE, int S, bool INV, int STRIDE>
+template <int LOGL, int LOGE, int S, bool INV, int STRIDE, bool DB = false>
 __device__ __forceinline__ void stages(float2 (&x)[1 << LOGE], float2* base, int u,
-                                       const float2* stw) {
+                                       const float2* stw, float2* base2 = nullptr) {
   using TP = TwPlan<LOGL, LOGE>;
   constexpr int E = 1 << LOGE;
   constexpr int NST = TP::NST;
@@ -164,19 +164,23 @@ __device__ __forceinline__ void stages(float2 (&x)[1 << LOGE], float2* base, int
       for (int t = 0; t < R; ++t) x[b + t * NB] = v[t];
     }
     if constexpr (S + 1 < NST) {
+      // with DB the exchanges alternate between two buffers: a buffer is
+      // written again only after the barrier of the exchange in between, so
+      // the barrier after the read-back is not needed
+      float2* buf = (DB && (S & 1)) ? base2 : base;
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         const int j = u + (b << LOGTP);
         const int k = j & ((1 << LOGNS) - 1);
         const int o = ((j >> LOGNS) << (LOGNS + LOGR)) + k;
 #pragma unroll
-        for (int t = 0; t < R; ++t) base[pad(o + (t << LOGNS)) * STRIDE] = x[b + t * NB];
+        for (int t = 0; t < R; ++t) buf[pad(o + (t << LOGNS)) * STRIDE] = x[b + t * NB];
       }
       __syncthreads();
 #pragma unroll
-      for (int m = 0; m < E; ++m) x[m] = base[pad(u + (m << LOGTP)) * STRIDE];
-      __syncthreads();
-      stages<LOGL, LOGE, S + 1, INV, STRIDE>(x, base, u, stw);
+      for (int m = 0; m < E; ++m) x[m] = buf[pad(u + (m << LOGTP)) * STRIDE];
+      if constexpr (!DB) __syncthreads();
+      stages<LOGL, LOGE, S + 1, INV, STRIDE, DB>(x, base, u, stw, base2);
     }
   }
 }
@@ -296,8 +300,8 @@ __host__ __device__ constexpr int col_min_blocks() {
                                                               : 1;
 }
 
-template <int LOGM, int CB, int LOGE>
-__global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), col_min_blocks<LOGM, CB, LOGE>())
+template <int LOGM, int CB, int LOGE, bool DB, int MINB>
+__global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), MINB)
     k_colsolve2(const ColArgs a) {
   constexpr int E = 1 << LOGE;
   constexpr int M = 1 << LOGM, LOGTP = LOGM - LOGE;
@@ -308,7 +312,8 @@ __global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), col_min_blocks<
   const int c0 = blockIdx.x * CB;
   const int k = c0 + c;
   float2* base = smem2 + c;
-  float2* stw = smem2 + CB * (M + M / 16);
+  float2* base2 = DB ? base + CB * (M + M / 16) : nullptr;
+  float2* stw = smem2 + (DB ? 2 : 1) * CB * (M + M / 16);
   float* sM = reinterpret_cast<float*>(stw + TwPlan<LOGM, LOGE>::TOTAL);
   // the symbol (constant tables) is fetched before the data, so that the
   // scaling between the two transforms waits on shared memory only
@@ -322,7 +327,7 @@ __global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), col_min_blocks<
 #pragma unroll
   for (int m = 0; m < E; ++m) x[m] = a.X[(size_t)(u + (m << LOGTP)) * L + k];
   if constexpr (TwPlan<LOGM, LOGE>::NST == 1) __syncthreads();  // no exchange barrier before use
-  stages<LOGM, LOGE, 0, false, CB>(x, base, u, stw);
+  stages<LOGM, LOGE, 0, false, CB, DB>(x, base, u, stw, base2);
   const float inv_mn = 1.f / ((float)M * (float)a.geo.N);
   if (c0 == 0) {
     // column 0 packs the DC and Nyquist columns of the row transforms: split
@@ -354,7 +359,7 @@ __global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), col_min_blocks<
       x[m] = make_float2(x[m].x * sc, x[m].y * sc);
     }
   }
-  stages<LOGM, LOGE, 0, true, CB>(x, base, u, stw);
+  stages<LOGM, LOGE, 0, true, CB, DB>(x, base, u, stw, base2);
 #pragma unroll
   for (int m = 0; m < E; ++m) a.X[(size_t)(u + (m << LOGTP)) * L + k] = x[m];
 }
@@ -522,14 +527,15 @@ static cudaError_t rowifft_go(const RowInvArgs& a, bool add, int nthreads, size_
   return launch_k(k_rowifft<LOGL, LOGE, false>, dim3(grid), dim3(nthreads), smem, s, a);
 }
 
-template <int LOGM, int CB, int LOGE>
+template <int LOGM, int CB, int LOGE, bool DB = false, int MINB = col_min_blocks<LOGM, CB, LOGE>()>
 static cudaError_t col_go(const ColArgs& a, cudaStream_t s, bool set_attr) {
   constexpr int M = 1 << LOGM;
-  const size_t smem = ((size_t)CB * (M + M / 16) + TwPlan<LOGM, LOGE>::TOTAL) * sizeof(float2) +
+  const size_t smem = ((size_t)(DB ? 2 : 1) * CB * (M + M / 16) + TwPlan<LOGM, LOGE>::TOTAL) *
+                          sizeof(float2) +
                       (size_t)M * sizeof(float);
-  if (set_attr) return set_smem(k_colsolve2<LOGM, CB, LOGE>, smem);
-  return launch_k(k_colsolve2<LOGM, CB, LOGE>, dim3(a.geo.L / CB), dim3(CB * M / (1 << LOGE)), smem,
-                  s, a);
+  if (set_attr) return set_smem(k_colsolve2<LOGM, CB, LOGE, DB, MINB>, smem);
+  return launch_k(k_colsolve2<LOGM, CB, LOGE, DB, MINB>, dim3(a.geo.L / CB),
+                  dim3(CB * M / (1 << LOGE)), smem, s, a);
 }
 
 bool fft2_supported(const Geo& geo) { return geo.L >= 16 && geo.L <= 2048 && geo.M >= 16 && geo.M <= 4096; }
@@ -587,13 +593,20 @@ cudaError_t launch_rowifft2(const RowInvArgs& a, bool add, int logE, int nthread
 }
 
 // column schedules: 0 = (CB 4, E 16), 1 = (CB 2, E 8), 2 = (CB 4, E 8),
-// 4 = (CB 2, E 16)
+// 4 = (CB 2, E 16), 5 = (CB 4, E 16) with double-buffered exchanges,
+// 6 = (CB 4, E 16) with registers capped for two CTAs per SM
 cudaError_t launch_colsolve2(const ColArgs& a, int sched, cudaStream_t s, bool set_attr) {
-#define SR_COL(lm)                                                   \
-  case (1 << lm):                                                    \
-    if (sched == 1) return col_go<lm, 2, 3>(a, s, set_attr);         \
-    if (sched == 2) return col_go<lm, 4, 3>(a, s, set_attr);         \
-    if (sched == 4) return col_go<lm, 2, 4>(a, s, set_attr);         \
+#define SR_COL(lm)                                                                  \
+  case (1 << lm):                                                                   \
+    if (sched == 1) return col_go<lm, 2, 3>(a, s, set_attr);                        \
+    if (sched == 2) return col_go<lm, 4, 3>(a, s, set_attr);                        \
+    if (sched == 4) return col_go<lm, 2, 4>(a, s, set_attr);                        \
+    if (sched == 5)                                                                 \
+      return (lm == 12) ? col_go<lm, 2, 4, true>(a, s, set_attr)                    \
+                        : col_go<lm, 4, 4, true>(a, s, set_attr);                   \
+    if (sched == 6)                                                                 \
+      return (lm == 12) ? col_go<lm, 2, 4, false, 2>(a, s, set_attr)                \
+                        : col_go<lm, 4, 4, false, 2>(a, s, set_attr);               \
     return (lm == 12) ? col_go<lm, 2, 4>(a, s, set_attr) : col_go<lm, 4, 4>(a, s, set_attr);
   switch (a.geo.M) {
     SR_COL(4) SR_COL(5) SR_COL(6) SR_COL(7) SR_COL(8) SR_COL(9) SR_COL(10) SR_COL(11) SR_COL(12)

@@ -68,7 +68,7 @@ def test_every_fft_schedule_matches_oracle(shape):
     tried = 0
     for vpt in (16, 8):
         for threads in (32, 64, 128, 256, 512):
-            for col in (0, 1, 2, 3, 4):
+            for col in range(7):
                 try:
                     ctx.set_schedule(vpt, threads, col)
                 except sr.SRError as e:
