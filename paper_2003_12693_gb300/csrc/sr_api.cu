@@ -41,17 +41,6 @@ struct sr_ctx {
   bool tm_X_ok = false;
   int col_tma_grid = 0;
   int* err_dev = nullptr;  // device error flag of the bounded waits
-  // tensor maps of the TMA tile kernels, keyed by buffer and box shape; the
-  // context's own buffers are encoded at creation, caller buffers on demand
-  struct MapEntry {
-    const void* p;
-    int kind;
-    CUtensorMap map;
-  };
-  std::vector<MapEntry> maps;
-  size_t own_maps = 0;
-  bool tile_tma = false;     // TMA tile kernels available for this size
-  bool tile_tma_on = false;  // chosen by the autotuner
   int n_tile = 0;    // CTAs of the 32 x 8 tile kernels (energy)
   int n_tile32 = 0;  // CTAs of the 32 x 32 tile kernels (w/b update)
 
@@ -342,32 +331,6 @@ bool make_tensor_map_2d(CUtensorMap* map, const void* base, int rows, int cols, 
 std::mutex g_tune_mutex;
 std::map<std::pair<int, int>, std::pair<int, sr_schedule>> g_tuned;  // (H, W) -> (device, schedule)
 
-// Box shapes of the TMA tile kernels.
-enum MapKind { MK_HALO = 0, MK_C32 = 1, MK_B1UP = 2, MK_B2LEFT = 3 };
-
-bool tile_map(sr_ctx* c, const float* p, int kind, CUtensorMap* out) {
-  for (const auto& e : c->maps)
-    if (e.p == p && e.kind == kind) {
-      *out = e.map;
-      return true;
-    }
-  int bw = 32, bh = 32;
-  if (kind == MK_HALO) {
-    bw = 32 + 2 * srk::tile_halo_x(c->prm.win_radius);
-    bh = 32 + 2 * srk::tile_halo_y(c->prm.win_radius);
-  } else if (kind == MK_B1UP) {
-    bh = 33;
-  } else if (kind == MK_B2LEFT) {
-    bw = 36;
-  }
-  sr_ctx::MapEntry e{p, kind, {}};
-  if (!make_tensor_map_2d(&e.map, p, c->H, c->W, c->W, bw, bh)) return false;
-  if (c->maps.size() >= 64) c->maps.resize(c->own_maps);  // forget caller buffers
-  c->maps.push_back(e);
-  *out = e.map;
-  return true;
-}
-
 // Time the candidate row and column schedules on the context's buffers and
 // keep the fastest (once per image size and device in the process).
 sr_status autotune(sr_ctx* c) {
@@ -527,16 +490,7 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
     pa.e1 = e1;
     pa.e2 = e2;
     pa.G = c->G;
-    pa.err = c->err_dev;
-    srk::PrepMaps pm{};
-    const bool use_tma = c->tile_tma && c->tile_tma_on &&
-                         tile_map(c, psi_in, MK_HALO, &pm.psi) &&
-                         tile_map(c, w1, MK_HALO, &pm.w1) && tile_map(c, w2, MK_HALO, &pm.w2) &&
-                         tile_map(c, e1, MK_B1UP, &pm.e1) && tile_map(c, e2, MK_B2LEFT, &pm.e2) &&
-                         tile_map(c, c->g, MK_C32, &pm.g);
-    st = run_kernel(c, SR_KCLASS_PREP, s, "k_prep", [&] {
-      return use_tma ? srk::launch_prep_tma(pa, pm, s) : srk::launch_prep(pa, s);
-    });
+    st = run_kernel(c, SR_KCLASS_PREP, s, "k_prep", [&] { return srk::launch_prep(pa, s); });
     if (st != SR_OK) return st;
     src = c->G;
   }
@@ -604,17 +558,8 @@ sr_status enqueue_wb(sr_ctx* c, cudaStream_t s, const float* phi1, const float* 
   a.e2o = e2o;
   a.phi_old = phi_old;
   a.partials = c->partials;
-  a.err = c->err_dev;
-  srk::WBMaps wm{};
-  const bool use_tma = c->tile_tma && c->tile_tma_on && tile_map(c, phi1, MK_HALO, &wm.psi) &&
-                       tile_map(c, w1i, MK_HALO, &wm.w1) && tile_map(c, w2i, MK_HALO, &wm.w2) &&
-                       tile_map(c, w1i, MK_C32, &wm.w1c) && tile_map(c, w2i, MK_C32, &wm.w2c) &&
-                       tile_map(c, e1i, MK_C32, &wm.e1) && tile_map(c, e2i, MK_C32, &wm.e2) &&
-                       tile_map(c, c->g, MK_C32, &wm.g) &&
-                       (!phi_old || tile_map(c, phi_old, MK_C32, &wm.phi_old));
-  sr_status st = run_kernel(c, SR_KCLASS_WB_UPDATE, s, "k_wb_update", [&] {
-    return use_tma ? srk::launch_wb_tma(a, wm, s) : srk::launch_wb_update(a, s);
-  });
+  sr_status st = run_kernel(c, SR_KCLASS_WB_UPDATE, s, "k_wb_update",
+                            [&] { return srk::launch_wb_update(a, s); });
   if (st != SR_OK || !phi_old) return st;
   return run_kernel(c, SR_KCLASS_REDUCE, s, "k_reduce", [&] {
     return srk::launch_reduce(c->partials, c->n_tile32, 2, c->red, s);
@@ -874,24 +819,6 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   }
   CREATE_CUDA(cudaMalloc((void**)&c->err_dev, sizeof(int)));
   CREATE_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
-  if (H >= 64 && W >= 64 && tensor_map_encoder()) {
-    CUtensorMap tmp;
-    bool ok = true;
-    for (int p = 0; p < 2; ++p) {
-      ok = ok && tile_map(c, c->phi[p], MK_HALO, &tmp) && tile_map(c, c->w1[p], MK_HALO, &tmp) &&
-           tile_map(c, c->w2[p], MK_HALO, &tmp) && tile_map(c, c->phi[p], MK_C32, &tmp) &&
-           tile_map(c, c->w1[p], MK_C32, &tmp) && tile_map(c, c->w2[p], MK_C32, &tmp);
-    }
-    ok = ok && tile_map(c, c->e1, MK_B1UP, &tmp) && tile_map(c, c->e2, MK_B2LEFT, &tmp) &&
-         tile_map(c, c->e1, MK_C32, &tmp) && tile_map(c, c->e2, MK_C32, &tmp) &&
-         tile_map(c, c->g, MK_C32, &tmp);
-    c->own_maps = c->maps.size();
-    c->tile_tma = ok;
-    // the plain-load tile kernels measured faster on GB300 (k_prep 31.5 us vs
-    // 37.4 us at 2048^2); SR_TILE_TMA=1 selects the TMA-fed ones
-    const char* env = std::getenv("SR_TILE_TMA");
-    c->tile_tma_on = ok && env && env[0] == '1';
-  }
   c->fft2 = srk::fft2_supported(c->geo);
   if (c->fft2) {
     const int cb = srk::colsolve_tma_cb(H);

@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(col_threads<LOGM, CB, LOGE>(), MINB)
   if (k != 0) {
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-      const float sc = inv_mn / (1.f + sM[u + (m << LOGTP)] + ak);
+      const float sc = __fdividef(inv_mn, 1.f + sM[u + (m << LOGTP)] + ak);  // lambda >= 1
       x[m] = make_float2(x[m].x * sc, x[m].y * sc);
     }
   }

@@ -129,7 +129,6 @@ struct PrepArgs {
   const float* e1;         // b1 - w1
   const float* e2;         // b2 - w2
   float* G;                // increment right-hand side, H x W
-  int* err;                // device error flag (bounded waits), may be null
 };
 
 // w and b update with the repulsion window sum fused in; b is carried as
@@ -149,18 +148,6 @@ struct WBArgs {
   float* e2o;
   const float* phi_old;    // phi^k for the stopping test, or nullptr
   double* partials;        // 2 doubles per 32 x 32 tile when phi_old != nullptr
-  int* err;                // device error flag (bounded waits), may be null
-};
-
-// 2-D float32 tensor maps (H x W planes) of the TMA tile kernels.  Boxes:
-// psi, w1, w2 (32 + 2 tile_halo_x(R)) x (32 + 2 tile_halo_y(R)) columns x
-// rows; prep: b1 32 x 33, b2 36 x 32, g 32 x 32; w/b update: b1, b2, g,
-// phi_old 32 x 32.
-struct PrepMaps {
-  CUtensorMap psi, w1, w2, e1, e2, g;   // e1: 32 x 33 (row above), e2: 36 x 32 (columns to the left)
-};
-struct WBMaps {
-  CUtensorMap psi, w1, w2, w1c, w2c, e1, e2, g, phi_old;  // w1, w2 halo; the rest 32 x 32
 };
 
 struct RepArgs {
@@ -204,11 +191,6 @@ cudaError_t launch_colsolve(const ColArgs& a, cudaStream_t s);
 cudaError_t launch_rowinv(const RowInvArgs& a, int mode, int nthreads, cudaStream_t s);
 cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s);
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
-cudaError_t launch_prep_tma(const PrepArgs& a, const PrepMaps& tm, cudaStream_t s);
-cudaError_t launch_wb_tma(const WBArgs& a, const WBMaps& tm, cudaStream_t s);
-size_t tile_tma_smem(int R, bool wb);
-int tile_halo_x(int R);
-int tile_halo_y(int R);
 int tile32_blocks(const Geo& geo);  // CTAs of the 32 x 32 tile kernels
 cudaError_t launch_repulsion(const RepArgs& a, cudaStream_t s);
 cudaError_t launch_energy(const EnergyArgs& a, cudaStream_t s);

@@ -25,7 +25,6 @@
 #include <cstdlib>
 
 #include "sr_internal.h"
-#include "sr_tma.cuh"
 
 // every supported repulsion window half width R
 #define SR_FOR_R(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
@@ -625,11 +624,11 @@ struct Tile {
   static constexpr int N4 = SH * SW4;      // staged float4 per plane
   static constexpr int IT = (N4 + kTN - 1) / kTN;
   static constexpr int NP = SH * SW;       // floats per staged plane
-  static constexpr int FLOATS = 5 * NP + 2 * kT * SW;
+  static constexpr int FLOATS = 2 * NP + 2 * kT * SW;
 };
 
 __host__ __device__ constexpr int tile32_floats(int R) {
-  return 5 * (kT + 2 * (R > 1 ? R : 1)) * (kT + 2 * (R > 4 ? 8 : 4)) +
+  return 2 * (kT + 2 * (R > 1 ? R : 1)) * (kT + 2 * (R > 4 ? 8 : 4)) +
          2 * kT * (kT + 2 * (R > 4 ? 8 : 4));
 }
 
@@ -637,59 +636,14 @@ __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ bool in_band(float x, const Model& m) { return fabsf(x) < m.band_l + m.eps; }
 
-// Stage one plane (zero outside the image); returns whether a staged value
-// lies in the narrow band when BAND is set.
-template <int R, bool BAND>
-__device__ __forceinline__ int stage4(float* dst, const float* __restrict__ src, const Geo& geo,
-                                      int i0, int j0, const Model& m) {
-  using TL = Tile<R>;
-  const int tid = threadIdx.y * kTBX + threadIdx.x;
-  float4 val[TL::IT];
-#pragma unroll
-  for (int k = 0; k < TL::IT; ++k) {
-    const int idx = tid + k * kTN;
-    const int r = idx / TL::SW4, c4 = idx - r * TL::SW4;
-    const int i = i0 - TL::HY + r, j = j0 - TL::HX + 4 * c4;
-    val[k] = (idx < TL::N4 && i >= 0 && i < geo.M && j >= 0 && j < geo.N)
-                 ? ld4(src + (size_t)i * geo.N + j)
-                 : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  int any = 0;
-#pragma unroll
-  for (int k = 0; k < TL::IT; ++k) {
-    const int idx = tid + k * kTN;
-    if (idx < TL::N4) {
-      st4(dst + 4 * idx, val[k]);
-      if (BAND)
-        any |= in_band(val[k].x, m) | in_band(val[k].y, m) | in_band(val[k].z, m) |
-               in_band(val[k].w, m);
-    }
-  }
-  return any;
-}
-
-// With psi and w in shared memory ([SH][SW] planes, zero outside the image):
-// form u = h(psi) w and return the window sums of the thread's four pixels.
+// With u1 = h(psi) w1, u2 = h(psi) w2 in shared memory ([SH][SW] planes,
+// zero outside the image): the window sums of the thread's four pixels.
 template <int R>
-__device__ __forceinline__ void window_sum(const float* t_psi, const float* t_w1,
-                                           const float* t_w2, float* t_u1, float* t_u2,
-                                           float* t_V1, float* t_V2, const Model& m,
-                                           float (&v1)[4], float (&v2)[4]) {
+__device__ __forceinline__ void window_vh(const float* t_u1, const float* t_u2, float* t_V1,
+                                          float* t_V2, const Model& m, float (&v1)[4],
+                                          float (&v2)[4]) {
   using TL = Tile<R>;
   const int tid = threadIdx.y * kTBX + threadIdx.x;
-  for (int idx = tid; idx < TL::NP / 4; idx += kTN) {
-    const float4 x = *reinterpret_cast<const float4*>(t_psi + 4 * idx);
-    const float4 a1 = *reinterpret_cast<const float4*>(t_w1 + 4 * idx);  // w = 0 outside the image
-    const float4 a2 = *reinterpret_cast<const float4*>(t_w2 + 4 * idx);
-    float4 h;
-    h.x = in_band(x.x, m) ? band_h(x.x, m) : 0.f;
-    h.y = in_band(x.y, m) ? band_h(x.y, m) : 0.f;
-    h.z = in_band(x.z, m) ? band_h(x.z, m) : 0.f;
-    h.w = in_band(x.w, m) ? band_h(x.w, m) : 0.f;
-    st4(t_u1 + 4 * idx, make_float4(h.x * a1.x, h.y * a1.y, h.z * a1.z, h.w * a1.w));
-    st4(t_u2 + 4 * idx, make_float4(h.x * a2.x, h.y * a2.y, h.z * a2.z, h.w * a2.w));
-  }
-  __syncthreads();
   // sum down the columns: a task is one plane, 4 rows x 4 columns, sliding
   // over 4 + 2R input rows
   constexpr int NTASK = 2 * (kT / 4) * TL::SW4;
@@ -740,25 +694,42 @@ __device__ __forceinline__ void window_sum(const float* t_psi, const float* t_w1
   }
 }
 
-// With psi staged: stage w, then the window sums of the thread's four pixels
-// (zero for tiles without band pixels).
+// Narrow-band tile: u1 = h(psi) w1 and u2 = h(psi) w2 are formed while the
+// halo is loaded (zero outside the image, where the window drops its terms)
+// and staged; then the separable window sums of the thread's four pixels.
+// Shared layout: u1, u2 ([SH][SW]), then V1, V2 ([32][SW]).
 template <int R>
-__device__ __forceinline__ void tile_window(float* sm, const Geo& geo, const Model& m,
+__device__ __forceinline__ void band_window(float* sm, const Geo& geo, const Model& m,
+                                            const float* __restrict__ psi,
                                             const float* __restrict__ w1,
                                             const float* __restrict__ w2, int i0, int j0,
-                                            bool band, float (&v1)[4], float (&v2)[4]) {
+                                            float (&v1)[4], float (&v2)[4]) {
   using TL = Tile<R>;
+  const int tid = threadIdx.y * kTBX + threadIdx.x;
+  float* t_u1 = sm;
+  float* t_u2 = sm + TL::NP;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) v1[q] = v2[q] = 0.f;
-  if (!band) return;  // uniform across the block
-  float* t_w1 = sm + 3 * TL::NP;
-  float* t_w2 = sm + 4 * TL::NP;
-  stage4<R, false>(t_w1, w1, geo, i0, j0, m);
-  stage4<R, false>(t_w2, w2, geo, i0, j0, m);
+  for (int k = 0; k < TL::IT; ++k) {
+    const int idx = tid + k * kTN;
+    const int r = idx / TL::SW4, c4 = idx - r * TL::SW4;
+    const int i = i0 - TL::HY + r, j = j0 - TL::HX + 4 * c4;
+    const bool ok = idx < TL::N4 && i >= 0 && i < geo.M && j >= 0 && j < geo.N;
+    const size_t o = ok ? (size_t)i * geo.N + j : 0;
+    const float4 x = ok ? ld4(psi + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 a1 = ok ? ld4(w1 + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 a2 = ok ? ld4(w2 + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 h;
+    h.x = in_band(x.x, m) ? band_h(x.x, m) : 0.f;
+    h.y = in_band(x.y, m) ? band_h(x.y, m) : 0.f;
+    h.z = in_band(x.z, m) ? band_h(x.z, m) : 0.f;
+    h.w = in_band(x.w, m) ? band_h(x.w, m) : 0.f;
+    if (idx < TL::N4) {
+      st4(t_u1 + 4 * idx, make_float4(h.x * a1.x, h.y * a1.y, h.z * a1.z, h.w * a1.w));
+      st4(t_u2 + 4 * idx, make_float4(h.x * a2.x, h.y * a2.y, h.z * a2.z, h.w * a2.w));
+    }
+  }
   __syncthreads();
-  float* t_V1 = sm + 5 * TL::NP;
-  window_sum<R>(sm, t_w1, t_w2, sm + TL::NP, sm + 2 * TL::NP, t_V1, t_V1 + kT * TL::SW, m, v1,
-                v2);
+  window_vh<R>(t_u1, t_u2, sm + 2 * TL::NP, sm + 2 * TL::NP + kT * TL::SW, m, v1, v2);
 }
 
 size_t tile32_smem(int R) { return (size_t)tile32_floats(R) * sizeof(float); }
@@ -768,22 +739,24 @@ size_t tile32_smem(int R) { return (size_t)tile32_floats(R) * sizeof(float); }
 // |psi| < l + eps; e = b - w, div the backward divergence).
 // BAND = false is the form for tiles without narrow-band pixels: the band
 // terms are not evaluated at all (rather than predicated off per pixel).
-template <bool BAND>
-__device__ __forceinline__ float rhs_point(const Model& m, float x, float up, float dn, float lf,
-                                           float rt, float e1, float e1u, float e2, float e2l,
-                                           float w1, float w2, float g, float v1, float v2) {
+__device__ __forceinline__ float rhs_bulk(const Model& m, float x, float up, float dn, float lf,
+                                          float rt, float e1, float e1u, float e2, float e2l) {
   const float lap = (up + dn) + (lf + rt) - 4.f * x;
   const float dv = (e1 - e1u) + (e2 - e2l);
-  float force = m.mu * (dv + lap);
-  if (BAND && in_band(x, m)) {
+  return m.mu * (dv + lap);
+}
+// the narrow-band terms added to the bulk force f at one pixel; G = tau f
+__device__ __forceinline__ float rhs_band(const Model& m, float f, float x, float w1, float w2,
+                                          float g, float v1, float v2) {
+  if (in_band(x, m)) {
     const float wn = sqrtf(w1 * w1 + w2 * w2);
     const BandTrig bt(x, m);
     float dl, dpl, hh, hp;
     bt.at_zero(m, dl, dpl);
     bt.band(m, hh, hp);
-    force += -m.gamma * g * wn * dpl + m.alpha * g * dl + 2.f * m.beta * hp * (w1 * v1 + w2 * v2);
+    f += -m.gamma * g * wn * dpl + m.alpha * g * dl + 2.f * m.beta * hp * (w1 * v1 + w2 * v2);
   }
-  return m.tau * force;
+  return m.tau * f;
 }
 
 // Eqs. (41), (42), (40), (23) at one pixel: B = grad phi + b + (2 beta/mu) h v,
@@ -899,39 +872,35 @@ __global__ void __launch_bounds__(kTN, 4) k_prep(const PrepArgs a) {
     if (!q.lf_g) LF = sl, e2l = sel;
     if (!q.rt_g) RT = sr;
   }
-  float v1[4], v2[4];
-  float4 W1 = make_float4(0.f, 0.f, 0.f, 0.f), W2 = W1, G4 = W1;
+  // the stencil part of the force first, so that only x and f stay live
+  // across the narrow-band work
+  float f[4];
+  {
+    const float x[4] = {X.x, X.y, X.z, X.w};
+    const float up[4] = {UP.x, UP.y, UP.z, UP.w}, dn[4] = {DN.x, DN.y, DN.z, DN.w};
+    const float lf[4] = {LF, X.x, X.y, X.z}, rt[4] = {X.y, X.z, X.w, RT};
+    const float e1[4] = {E1.x, E1.y, E1.z, E1.w}, e2[4] = {E2.x, E2.y, E2.z, E2.w};
+    const float e1u[4] = {E1u.x, E1u.y, E1u.z, E1u.w}, e2l4[4] = {e2l, E2.x, E2.y, E2.z};
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      f[t] = rhs_bulk(m, x[t], up[t], dn[t], lf[t], rt[t], e1[t], e1u[t], e2[t], e2l4[t]);
+  }
+  float out[4];
   if (band) {  // uniform across the block
-    const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
-    stage4<R, false>(smem_f, psi, a.geo, i0, j0, m);
-    tile_window<R>(smem_f, a.geo, m, a.w1, a.w2, i0, j0, true, v1, v2);
-    W1 = ld4_if(q.live, a.w1 + q.o);
-    W2 = ld4_if(q.live, a.w2 + q.o);
-    G4 = ld4_if(q.live, a.g + q.o);
+    const float4 W1 = ld4_if(q.live, a.w1 + q.o), W2 = ld4_if(q.live, a.w2 + q.o);
+    const float4 G4 = ld4_if(q.live, a.g + q.o);
+    float v1[4], v2[4];
+    band_window<R>(smem_f, a.geo, m, psi, a.w1, a.w2, blockIdx.y * kT, blockIdx.x * kT, v1, v2);
+    const float x[4] = {X.x, X.y, X.z, X.w};
+    const float w1[4] = {W1.x, W1.y, W1.z, W1.w}, w2[4] = {W2.x, W2.y, W2.z, W2.w};
+    const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) out[t] = rhs_band(m, f[t], x[t], w1[t], w2[t], gg[t], v1[t], v2[t]);
   } else {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) v1[t] = v2[t] = 0.f;
+    for (int t = 0; t < 4; ++t) out[t] = m.tau * f[t];
   }
   if (!q.live) return;
-  const float x[4] = {X.x, X.y, X.z, X.w};
-  const float up[4] = {UP.x, UP.y, UP.z, UP.w}, dn[4] = {DN.x, DN.y, DN.z, DN.w};
-  const float lf[4] = {LF, X.x, X.y, X.z}, rt[4] = {X.y, X.z, X.w, RT};
-  const float e1[4] = {E1.x, E1.y, E1.z, E1.w}, e2[4] = {E2.x, E2.y, E2.z, E2.w};
-  const float e1u[4] = {E1u.x, E1u.y, E1u.z, E1u.w}, e2l4[4] = {e2l, E2.x, E2.y, E2.z};
-  const float w1[4] = {W1.x, W1.y, W1.z, W1.w}, w2[4] = {W2.x, W2.y, W2.z, W2.w};
-  const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
-  float out[4];
-  if (band) {
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      out[t] = rhs_point<true>(m, x[t], up[t], dn[t], lf[t], rt[t], e1[t], e1u[t], e2[t], e2l4[t],
-                               w1[t], w2[t], gg[t], v1[t], v2[t]);
-  } else {
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      out[t] = rhs_point<false>(m, x[t], up[t], dn[t], lf[t], rt[t], e1[t], e1u[t], e2[t], e2l4[t],
-                                w1[t], w2[t], gg[t], v1[t], v2[t]);
-  }
   st4(a.G + q.o, make_float4(out[0], out[1], out[2], out[3]));
 }
 
@@ -964,10 +933,8 @@ __global__ void __launch_bounds__(kTN, 4) k_wb_update(const WBArgs a) {
   float v1[4], v2[4];
   float4 G4 = make_float4(0.f, 0.f, 0.f, 0.f);
   if (band) {  // uniform across the block
-    const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
-    stage4<R, false>(smem_f, phi, a.geo, i0, j0, m);
-    tile_window<R>(smem_f, a.geo, m, a.w1, a.w2, i0, j0, true, v1, v2);
     G4 = ld4_if(q.live, a.g + q.o);
+    band_window<R>(smem_f, a.geo, m, phi, a.w1, a.w2, blockIdx.y * kT, blockIdx.x * kT, v1, v2);
   } else {
 #pragma unroll
     for (int t = 0; t < 4; ++t) v1[t] = v2[t] = 0.f;
@@ -1006,319 +973,6 @@ __global__ void __launch_bounds__(kTN, 4) k_wb_update(const WBArgs a) {
     }
   }
   if (a.phi_old) block_sum_store<2>(part, a.partials + 2 * (blockIdx.y * gridDim.x + blockIdx.x));
-}
-
-// ---------------------------------------------------------------------------
-// Pipelined TMA versions of the two tile kernels.  A persistent CTA walks the
-// tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; thread 0 keeps the 2-D
-// box loads of the next NS tiles in flight (one mbarrier per stage), so HBM
-// sees a steady stream instead of one load burst per CTA lifetime.  Boxes
-// per stage: psi with the (HX, HY) halo (zero fill outside the image gives
-// the window sum's dropped terms), and for k_prep e1 with the row above
-// (32 x 33) and e2 with four columns to the left (36 x 32); for k_wb_update
-// e1, e2, w1, w2 and the old phi, 32 x 32.  Tiles with narrow-band pixels
-// load w1, w2 with the halo and g on a separate barrier.  Periodic
-// neighbours across the image edge come from global memory.  Every wait is
-// bounded; on a timeout the block records the error, drains its own loads
-// in flight (bounded again) and returns.
-// ---------------------------------------------------------------------------
-__host__ __device__ constexpr int a32(int n) { return (n + 31) / 32 * 32; }
-
-template <int R>
-struct PipeP {  // k_prep stage, floats; every box 128-B aligned
-  using TL = Tile<R>;
-  static constexpr int PSI = 0;
-  static constexpr int E1 = PSI + a32(TL::NP);   // 33 rows x 32
-  static constexpr int E2 = E1 + a32(33 * 32);   // 32 rows x 36
-  static constexpr int STAGE = E2 + a32(32 * 36);
-  static constexpr uint32_t BYTES = 4u * (TL::NP + 33 * 32 + 32 * 36);
-};
-
-template <int R>
-struct PipeW {  // k_wb_update stage
-  using TL = Tile<R>;
-  static constexpr int PSI = 0;
-  static constexpr int E1 = PSI + a32(TL::NP);
-  static constexpr int E2 = E1 + 1024;
-  static constexpr int W1 = E2 + 1024;
-  static constexpr int W2 = W1 + 1024;
-  static constexpr int PO = W2 + 1024;
-  static constexpr int STAGE = PO + 1024;
-  static constexpr uint32_t BYTES = 4u * (TL::NP + 4 * 1024);  // + 4096 with the old phi
-};
-
-template <int R>
-struct PipeBand {  // band-tile buffers; u = h(psi) w is formed in place of w
-  using TL = Tile<R>;
-  static constexpr int W1 = 0;
-  static constexpr int W2 = W1 + a32(TL::NP);
-  static constexpr int V1 = W2 + a32(TL::NP);
-  static constexpr int V2 = V1 + a32(kT * TL::SW);
-  static constexpr int GG = V2 + a32(kT * TL::SW);
-  static constexpr int FLOATS = GG + 1024;
-  static constexpr uint32_t BYTES = 4u * (2 * TL::NP + 1024);
-};
-
-constexpr int kPrepStages = 3, kWbStages = 3;
-
-template <class P, class B, int NS>
-__host__ __device__ constexpr int pipe_floats() {
-  return NS * P::STAGE + B::FLOATS + 2 * (NS + 1) + 2;  // + mbarriers and an error word
-}
-
-__device__ __forceinline__ float* align128(unsigned char* p) {
-  return reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(p) + 127) & ~static_cast<uintptr_t>(127));
-}
-
-// After a timeout: record it, then wait (bounded) for the loads this block
-// still has in flight so that none lands after the block has exited.
-__device__ __forceinline__ void pipe_drain(uint64_t* bar, int NS, int it, int tile, int stride,
-                                           int ntiles, bool band_pending, uint32_t band_par,
-                                           int* err) {
-  if (err) atomicCAS(err, 0, tma::kErrTimeout);
-  for (int k = 0; k < NS && tile + k * stride < ntiles; ++k)
-    tma::mbar_wait(&bar[(it + k) % NS], (uint32_t)((it + k) / NS) & 1u);
-  if (band_pending) tma::mbar_wait(&bar[NS], band_par);
-}
-
-template <int R>
-__global__ void __launch_bounds__(kTN, 3) k_prep_tma(const PrepArgs a, const __grid_constant__ PrepMaps tm) {
-  using TL = Tile<R>;
-  using PP = PipeP<R>;
-  using PB = PipeBand<R>;
-  constexpr int NS = kPrepStages;
-  extern __shared__ __align__(16) unsigned char smem_tt[];
-  pdl_wait();
-  pdl_trigger();
-  float* sm = align128(smem_tt);
-  float* bs = sm + NS * PP::STAGE;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(bs + PB::FLOATS);
-  volatile int* s_err = reinterpret_cast<volatile int*>(bar + NS + 1);
-  const int tid = threadIdx.y * kTBX + threadIdx.x;
-  const int M = a.geo.M, N = a.geo.N;
-  const int tiles_x = (N + kT - 1) / kT, ntiles = tiles_x * ((M + kT - 1) / kT);
-  const Model& m = a.mod;
-  auto issue = [&](int tile, int s) {
-    const int i0 = (tile / tiles_x) * kT, j0 = (tile % tiles_x) * kT;
-    float* st = sm + s * PP::STAGE;
-    tma::mbar_expect_tx(&bar[s], PP::BYTES);
-    tma::load_2d(st + PP::PSI, &tm.psi, j0 - TL::HX, i0 - TL::HY, &bar[s]);
-    tma::load_2d(st + PP::E1, &tm.e1, j0, i0 - 1, &bar[s]);
-    tma::load_2d(st + PP::E2, &tm.e2, j0 - 4, i0, &bar[s]);
-  };
-  if (tid == 0) {
-    for (int s = 0; s <= NS; ++s) tma::mbar_init(&bar[s], 1);
-    *s_err = 0;
-    tma::mbar_init_fence();
-    for (int s = 0; s < NS; ++s)
-      if (blockIdx.x + s * gridDim.x < ntiles) issue(blockIdx.x + s * gridDim.x, s);
-  }
-  __syncthreads();
-  const int ty = threadIdx.y, tx = threadIdx.x;
-  const int q = (ty + TL::HY) * TL::SW + 4 * tx + TL::HX;
-  auto f4 = [](const float* p) { return *reinterpret_cast<const float4*>(p); };
-  uint32_t band_par = 0;
-  int it = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-    const int s = it % NS;
-    const int i0 = (tile / tiles_x) * kT, j0 = (tile % tiles_x) * kT;
-    const int i = i0 + ty, j = j0 + 4 * tx;
-    const bool live = i < M && j < N;
-    const size_t o = (size_t)i * N + j;
-    if (!tma::mbar_wait(&bar[s], (uint32_t)(it / NS) & 1u)) *s_err = 1;
-    const float* st = sm + s * PP::STAGE;
-    const float4 X = f4(st + PP::PSI + q);
-    const bool band = __syncthreads_or(live && any_band4(X, m)) != 0;
-    if (*s_err) {
-      if (tid == 0) pipe_drain(bar, NS, it, tile, gridDim.x, ntiles, false, 0, a.err);
-      return;
-    }
-    float v1[4] = {0.f, 0.f, 0.f, 0.f}, v2[4] = {0.f, 0.f, 0.f, 0.f};
-    float4 W1 = make_float4(0.f, 0.f, 0.f, 0.f), W2 = W1, G4 = W1;
-    if (band) {  // uniform across the block
-      if (tid == 0) {
-        tma::fence_async_smem();
-        tma::mbar_expect_tx(&bar[NS], PB::BYTES);
-        tma::load_2d(bs + PB::W1, &tm.w1, j0 - TL::HX, i0 - TL::HY, &bar[NS]);
-        tma::load_2d(bs + PB::W2, &tm.w2, j0 - TL::HX, i0 - TL::HY, &bar[NS]);
-        tma::load_2d(bs + PB::GG, &tm.g, j0, i0, &bar[NS]);
-      }
-      if (live) {
-        W1 = ld4(a.w1 + o);
-        W2 = ld4(a.w2 + o);
-      }
-      const bool ok = tma::mbar_wait(&bar[NS], band_par);
-      if (!__syncthreads_and(ok)) {
-        if (tid == 0) pipe_drain(bar, NS, it, tile, gridDim.x, ntiles, true, band_par, a.err);
-        return;
-      }
-      band_par ^= 1u;
-      G4 = f4(bs + PB::GG + ty * 32 + 4 * tx);
-      window_sum<R>(st + PP::PSI, bs + PB::W1, bs + PB::W2, bs + PB::W1, bs + PB::W2,
-                    bs + PB::V1, bs + PB::V2, m, v1, v2);
-    }
-    if (live) {
-      const float4 UP = i > 0 ? f4(st + PP::PSI + q - TL::SW) : ld4(a.psi + (size_t)(M - 1) * N + j);
-      const float4 DN = i < M - 1 ? f4(st + PP::PSI + q + TL::SW) : ld4(a.psi + j);
-      const float LF = j > 0 ? st[PP::PSI + q - 1] : __ldg(a.psi + (size_t)i * N + N - 1);
-      const float RT = j + 4 < N ? st[PP::PSI + q + 4] : __ldg(a.psi + (size_t)i * N);
-      const float4 E1 = f4(st + PP::E1 + (ty + 1) * 32 + 4 * tx);
-      const float4 E1u =
-          i > 0 ? f4(st + PP::E1 + ty * 32 + 4 * tx) : ld4(a.e1 + (size_t)(M - 1) * N + j);
-      const float4 E2 = f4(st + PP::E2 + ty * 36 + 4 + 4 * tx);
-      const float e2l =
-          j > 0 ? st[PP::E2 + ty * 36 + 3 + 4 * tx] : __ldg(a.e2 + (size_t)i * N + N - 1);
-      const float x[4] = {X.x, X.y, X.z, X.w};
-      const float up[4] = {UP.x, UP.y, UP.z, UP.w}, dn[4] = {DN.x, DN.y, DN.z, DN.w};
-      const float lf[4] = {LF, X.x, X.y, X.z}, rt[4] = {X.y, X.z, X.w, RT};
-      const float e1[4] = {E1.x, E1.y, E1.z, E1.w}, e2[4] = {E2.x, E2.y, E2.z, E2.w};
-      const float e1u[4] = {E1u.x, E1u.y, E1u.z, E1u.w}, e2l4[4] = {e2l, E2.x, E2.y, E2.z};
-      const float w1[4] = {W1.x, W1.y, W1.z, W1.w}, w2[4] = {W2.x, W2.y, W2.z, W2.w};
-      const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
-      float out[4];
-      if (band) {
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          out[t] = rhs_point<true>(m, x[t], up[t], dn[t], lf[t], rt[t], e1[t], e1u[t], e2[t],
-                                   e2l4[t], w1[t], w2[t], gg[t], v1[t], v2[t]);
-      } else {
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          out[t] = rhs_point<false>(m, x[t], up[t], dn[t], lf[t], rt[t], e1[t], e1u[t], e2[t],
-                                    e2l4[t], w1[t], w2[t], gg[t], v1[t], v2[t]);
-      }
-      st4(a.G + o, make_float4(out[0], out[1], out[2], out[3]));
-    }
-    __syncthreads();  // stage s and the band buffers are free again
-    if (tid == 0 && tile + NS * (int)gridDim.x < ntiles) {
-      tma::fence_async_smem();
-      issue(tile + NS * gridDim.x, s);
-    }
-  }
-}
-
-template <int R>
-__global__ void __launch_bounds__(kTN, 2) k_wb_tma(const WBArgs a, const __grid_constant__ WBMaps tm) {
-  using TL = Tile<R>;
-  using PW = PipeW<R>;
-  using PB = PipeBand<R>;
-  constexpr int NS = kWbStages;
-  extern __shared__ __align__(16) unsigned char smem_tt[];
-  pdl_wait();
-  pdl_trigger();
-  float* sm = align128(smem_tt);
-  float* bs = sm + NS * PW::STAGE;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(bs + PB::FLOATS);
-  volatile int* s_err = reinterpret_cast<volatile int*>(bar + NS + 1);
-  const int tid = threadIdx.y * kTBX + threadIdx.x;
-  const int M = a.geo.M, N = a.geo.N;
-  const int tiles_x = (N + kT - 1) / kT, ntiles = tiles_x * ((M + kT - 1) / kT);
-  const Model& m = a.mod;
-  const bool chk = a.phi_old != nullptr;
-  auto issue = [&](int tile, int s) {
-    const int i0 = (tile / tiles_x) * kT, j0 = (tile % tiles_x) * kT;
-    float* st = sm + s * PW::STAGE;
-    tma::mbar_expect_tx(&bar[s], PW::BYTES + (chk ? 4096u : 0u));
-    tma::load_2d(st + PW::PSI, &tm.psi, j0 - TL::HX, i0 - TL::HY, &bar[s]);
-    tma::load_2d(st + PW::E1, &tm.e1, j0, i0, &bar[s]);
-    tma::load_2d(st + PW::E2, &tm.e2, j0, i0, &bar[s]);
-    tma::load_2d(st + PW::W1, &tm.w1c, j0, i0, &bar[s]);
-    tma::load_2d(st + PW::W2, &tm.w2c, j0, i0, &bar[s]);
-    if (chk) tma::load_2d(st + PW::PO, &tm.phi_old, j0, i0, &bar[s]);
-  };
-  if (tid == 0) {
-    for (int s = 0; s <= NS; ++s) tma::mbar_init(&bar[s], 1);
-    *s_err = 0;
-    tma::mbar_init_fence();
-    for (int s = 0; s < NS; ++s)
-      if (blockIdx.x + s * gridDim.x < ntiles) issue(blockIdx.x + s * gridDim.x, s);
-  }
-  __syncthreads();
-  const int ty = threadIdx.y, tx = threadIdx.x;
-  const int q = (ty + TL::HY) * TL::SW + 4 * tx + TL::HX;
-  const int c32 = ty * 32 + 4 * tx;
-  auto f4 = [](const float* p) { return *reinterpret_cast<const float4*>(p); };
-  uint32_t band_par = 0;
-  int it = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-    const int s = it % NS;
-    const int i0 = (tile / tiles_x) * kT, j0 = (tile % tiles_x) * kT;
-    const int i = i0 + ty, j = j0 + 4 * tx;
-    const bool live = i < M && j < N;
-    const size_t o = (size_t)i * N + j;
-    if (!tma::mbar_wait(&bar[s], (uint32_t)(it / NS) & 1u)) *s_err = 1;
-    const float* st = sm + s * PW::STAGE;
-    const float4 X = f4(st + PW::PSI + q);
-    const bool band = __syncthreads_or(live && any_band4(X, m)) != 0;
-    if (*s_err) {
-      if (tid == 0) pipe_drain(bar, NS, it, tile, gridDim.x, ntiles, false, 0, a.err);
-      return;
-    }
-    float v1[4] = {0.f, 0.f, 0.f, 0.f}, v2[4] = {0.f, 0.f, 0.f, 0.f};
-    float4 G4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (band) {  // uniform across the block
-      if (tid == 0) {
-        tma::fence_async_smem();
-        tma::mbar_expect_tx(&bar[NS], PB::BYTES);
-        tma::load_2d(bs + PB::W1, &tm.w1, j0 - TL::HX, i0 - TL::HY, &bar[NS]);
-        tma::load_2d(bs + PB::W2, &tm.w2, j0 - TL::HX, i0 - TL::HY, &bar[NS]);
-        tma::load_2d(bs + PB::GG, &tm.g, j0, i0, &bar[NS]);
-      }
-      const bool ok = tma::mbar_wait(&bar[NS], band_par);
-      if (!__syncthreads_and(ok)) {
-        if (tid == 0) pipe_drain(bar, NS, it, tile, gridDim.x, ntiles, true, band_par, a.err);
-        return;
-      }
-      band_par ^= 1u;
-      G4 = f4(bs + PB::GG + c32);
-      window_sum<R>(st + PW::PSI, bs + PB::W1, bs + PB::W2, bs + PB::W1, bs + PB::W2,
-                    bs + PB::V1, bs + PB::V2, m, v1, v2);
-    }
-    double part[2] = {0.0, 0.0};
-    if (live) {
-      const float4 DN = i < M - 1 ? f4(st + PW::PSI + q + TL::SW) : ld4(a.phi1 + j);
-      const float RT = j + 4 < N ? st[PW::PSI + q + 4] : __ldg(a.phi1 + (size_t)i * N);
-      const float4 E1 = f4(st + PW::E1 + c32), E2 = f4(st + PW::E2 + c32);
-      const float4 W1 = f4(st + PW::W1 + c32), W2 = f4(st + PW::W2 + c32);
-      const float x[4] = {X.x, X.y, X.z, X.w};
-      const float dn[4] = {DN.x, DN.y, DN.z, DN.w}, rt[4] = {X.y, X.z, X.w, RT};
-      const float b1[4] = {E1.x + W1.x, E1.y + W1.y, E1.z + W1.z, E1.w + W1.w};
-      const float b2[4] = {E2.x + W2.x, E2.y + W2.y, E2.z + W2.z, E2.w + W2.w};
-      const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
-      float wo1[4], wo2[4], eo1[4], eo2[4];
-      if (band) {
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          wb_point<true>(m, x[t], dn[t] - x[t], rt[t] - x[t], b1[t], b2[t], gg[t], v1[t], v2[t],
-                         wo1[t], wo2[t], eo1[t], eo2[t]);
-      } else {
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          wb_point<false>(m, x[t], dn[t] - x[t], rt[t] - x[t], b1[t], b2[t], gg[t], v1[t], v2[t],
-                          wo1[t], wo2[t], eo1[t], eo2[t]);
-      }
-      st4(a.w1o + o, make_float4(wo1[0], wo1[1], wo1[2], wo1[3]));
-      st4(a.w2o + o, make_float4(wo2[0], wo2[1], wo2[2], wo2[3]));
-      st4(a.e1o + o, make_float4(eo1[0], eo1[1], eo1[2], eo1[3]));
-      st4(a.e2o + o, make_float4(eo2[0], eo2[1], eo2[2], eo2[3]));
-      if (chk) {
-        const float4 P = f4(st + PW::PO + c32);
-        const float po[4] = {P.x, P.y, P.z, P.w};
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const double df = (double)x[t] - (double)po[t];
-          part[0] += df * df;
-          part[1] += (double)po[t] * (double)po[t];
-        }
-      }
-    }
-    if (chk) block_sum_store<2>(part, a.partials + 2 * tile);
-    __syncthreads();  // stage s and the band buffers are free again
-    if (tid == 0 && tile + NS * (int)gridDim.x < ntiles) {
-      tma::fence_async_smem();
-      issue(tile + NS * gridDim.x, s);
-    }
-  }
 }
 
 __global__ void __launch_bounds__(kTileX* kTileY) k_repulsion(const RepArgs a) {
@@ -1529,9 +1183,7 @@ cudaError_t configure_kernels() {
   if ((e = allow_big_smem(k_rowinv<kInvSTORE>))) return e;
 #define SR_CASE(r)                                                   \
   if ((e = allow_big_smem(k_prep<r>)) != cudaSuccess) return e;      \
-  if ((e = allow_big_smem(k_wb_update<r>)) != cudaSuccess) return e; \
-  if ((e = allow_big_smem(k_prep_tma<r>)) != cudaSuccess) return e;  \
-  if ((e = allow_big_smem(k_wb_tma<r>)) != cudaSuccess) return e;
+  if ((e = allow_big_smem(k_wb_update<r>)) != cudaSuccess) return e;
   SR_FOR_R(SR_CASE)
 #undef SR_CASE
   return cudaSuccess;
@@ -1574,64 +1226,6 @@ cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s) {
   switch (a.mod.R) {
 #define SR_CASE(r) \
   case r: return launch_k(k_wb_update<r>, g, b, sm, s, a);
-    SR_FOR_R(SR_CASE)
-#undef SR_CASE
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
-size_t tile_tma_smem(int R, bool wb) {
-  switch (R) {
-#define SR_CASE(r)                                                                            \
-  case r:                                                                                     \
-    return (size_t)(wb ? pipe_floats<PipeW<r>, PipeBand<r>, kWbStages>()                      \
-                       : pipe_floats<PipeP<r>, PipeBand<r>, kPrepStages>()) * sizeof(float) + \
-           128;
-    SR_FOR_R(SR_CASE)
-#undef SR_CASE
-  }
-  return 0;
-}
-
-// Persistent grid: SMs x resident CTAs, capped by the number of tiles.
-template <class K>
-static int tile_pipe_grid(K kernel, size_t smem, int ntiles) {
-  int dev = 0, nsm = 1, per = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kTN, smem) != cudaSuccess ||
-      per < 1)
-    per = 1;
-  return ntiles < nsm * per ? ntiles : nsm * per;
-}
-
-int tile_halo_x(int R) { return R > 4 ? 8 : 4; }
-int tile_halo_y(int R) { return R > 1 ? R : 1; }
-
-cudaError_t launch_prep_tma(const PrepArgs& a, const PrepMaps& tm, cudaStream_t s) {
-  const dim3 b(kTBX, kTBY);
-  const size_t sm = tile_tma_smem(a.mod.R, false);
-  const int nt = tile32_blocks(a.geo);
-  switch (a.mod.R) {
-#define SR_CASE(r)                                                                 \
-  case r:                                                                          \
-    return launch_k(k_prep_tma<r>, dim3(tile_pipe_grid(k_prep_tma<r>, sm, nt)), b, sm, s, a, tm);
-    SR_FOR_R(SR_CASE)
-#undef SR_CASE
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_wb_tma(const WBArgs& a, const WBMaps& tm, cudaStream_t s) {
-  const dim3 b(kTBX, kTBY);
-  const size_t sm = tile_tma_smem(a.mod.R, true);
-  const int nt = tile32_blocks(a.geo);
-  switch (a.mod.R) {
-#define SR_CASE(r)                                                               \
-  case r:                                                                        \
-    return launch_k(k_wb_tma<r>, dim3(tile_pipe_grid(k_wb_tma<r>, sm, nt)), b, sm, s, a, tm);
     SR_FOR_R(SR_CASE)
 #undef SR_CASE
     default: return cudaErrorInvalidValue;
