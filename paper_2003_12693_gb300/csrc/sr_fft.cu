@@ -131,8 +131,10 @@ __device__ __forceinline__ void stage_table(float2* dst, const float2* __restric
 // 1 for rows, CB for interleaved columns; `base` already includes the
 // sequence offset).  The thread holds E = 2^LOGE values x[m] = seq[u + (L/E) m];
 // stages use radix E, the last one radix 2^(LOGL mod LOGE) if that is not 1.
-// stw is the stage-twiddle table in shared memory.
-template <int LOGL, int LOGE, int S, bool INV, int STRIDE, bool DB = false>
+// stw is the stage-twiddle table: in shared memory, or with TWG in global
+// memory read through the read-only cache (the row passes: every CTA reads
+// the same table, so it stays in L1 and no per-CTA copy is needed).
+template <int LOGL, int LOGE, int S, bool INV, int STRIDE, bool DB = false, bool TWG = false>
 __device__ __forceinline__ void stages(float2 (&x)[1 << LOGE], float2* base, int u,
                                        const float2* stw, float2* base2 = nullptr) {
   using TP = TwPlan<LOGL, LOGE>;
@@ -154,7 +156,8 @@ __device__ __forceinline__ void stages(float2 (&x)[1 << LOGE], float2* base, int
         constexpr int OFF = TP::offset(S);
 #pragma unroll
         for (int t = 1; t < R; ++t) {
-          float2 w = stw[OFF + ((t - 1) << LOGNS) + k];
+          const int ti = OFF + ((t - 1) << LOGNS) + k;
+          float2 w = TWG ? __ldg(stw + ti) : stw[ti];
           if (INV) w.y = -w.y;
           v[t] = cmul(v[t], w);
         }
@@ -180,7 +183,7 @@ __device__ __forceinline__ void stages(float2 (&x)[1 << LOGE], float2* base, int
 #pragma unroll
       for (int m = 0; m < E; ++m) x[m] = buf[pad(u + (m << LOGTP)) * STRIDE];
       if constexpr (!DB) __syncthreads();
-      stages<LOGL, LOGE, S + 1, INV, STRIDE, DB>(x, base, u, stw, base2);
+      stages<LOGL, LOGE, S + 1, INV, STRIDE, DB, TWG>(x, base, u, stw, base2);
     }
   }
 }
@@ -199,15 +202,14 @@ __global__ void __launch_bounds__(512) k_rowfft(const RowFwdArgs a) {
   const int i = blockIdx.x * a.T + t;
   const bool live = i < a.geo.M;
   float2* base = smem2 + t * S;
-  float2* stw = smem2 + a.T * S;
-  stage_table<TwPlan<LOGL, LOGE>::TOTAL>(stw, LOGE == 4 ? a.fft.tws16 : a.fft.tws8);
+  const float2* stw = LOGE == 4 ? a.fft.tws16 : a.fft.tws8;
   pdl_wait();
   pdl_trigger();
   float2 x[E];
   const float2* row = reinterpret_cast<const float2*>(a.src + (size_t)(live ? i : 0) * a.geo.N);
 #pragma unroll
   for (int m = 0; m < E; ++m) x[m] = live ? __ldg(row + u + (m << LOGTP)) : make_float2(0.f, 0.f);
-  stages<LOGL, LOGE, 0, false, 1>(x, base, u, stw);
+  stages<LOGL, LOGE, 0, false, 1, false, true>(x, base, u, stw);
   // even/odd split needs Z_{L-k}: exchange through shared memory
 #pragma unroll
   for (int m = 0; m < E; ++m) base[pad(u + (m << LOGTP))] = x[m];
@@ -245,8 +247,7 @@ __global__ void __launch_bounds__(512) k_rowifft(const RowInvArgs a) {
   const bool live = i < a.geo.M;
   const int ii = live ? i : 0;
   float2* base = smem2 + t * S;
-  float2* stw = smem2 + a.T * S;
-  stage_table<TwPlan<LOGL, LOGE>::TOTAL>(stw, LOGE == 4 ? a.fft.tws16 : a.fft.tws8);
+  const float2* stw = LOGE == 4 ? a.fft.tws16 : a.fft.tws8;
   pdl_wait();
   pdl_trigger();
   float2 p[E];
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(512) k_rowifft(const RowInvArgs a) {
     const float2 Xo = cmul(D, cconj(__ldg(&a.twN[k])));
     x[m] = make_float2(Xe.x - Xo.y, Xe.y + Xo.x);
   }
-  stages<LOGL, LOGE, 0, true, 1>(x, base, u, stw);
+  stages<LOGL, LOGE, 0, true, 1, false, true>(x, base, u, stw);
   if (!live) return;
   float2* orow = reinterpret_cast<float2*>(a.out + (size_t)i * a.geo.N);
 #pragma unroll
@@ -558,9 +559,7 @@ int stage_twiddles(int L, int logE) {
   return 0;
 }
 
-size_t rowfft2_smem(int T, int L, int logE) {
-  return ((size_t)T * (L + L / 16) + stage_twiddles(L, logE)) * sizeof(float2);
-}
+size_t rowfft2_smem(int T, int L, int) { return (size_t)T * (L + L / 16) * sizeof(float2); }
 
 #define SR_ROW_SWITCH(CALL)                         \
   switch (a.geo.L) {                                \
