@@ -55,6 +55,7 @@ struct sr_ctx {
   float* tmp2 = nullptr;
   float* stage = nullptr;
   float* G = nullptr;         // increment right-hand side of the current inner step
+  float* divE = nullptr;      // div e of the current outer iteration (fixed over the inner loop)
   unsigned char* mask_dev = nullptr;
   float2* X = nullptr;
   float2* tw_row = nullptr;
@@ -474,9 +475,11 @@ sr_status autotune(sr_ctx* c) {
 // ---- one inner step: psi_out = psi_in + L^{-1} G ---------------------------
 // With load_src set, the step solves L out = load_src instead (Eqs. (31)-(33)
 // alone).
+// div_mode: 0 forms div e in the step, 1 also stores it in divE (first inner
+// step of an outer iteration), 2 reads it from divE (later inner steps).
 sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const float* w1,
                            const float* w2, const float* e1, const float* e2, float* psi_out,
-                           const float* load_src) {
+                           const float* load_src, int div_mode = 0) {
   sr_status st;
   const float* src = load_src;
   if (!load_src) {
@@ -490,6 +493,8 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
     pa.e1 = e1;
     pa.e2 = e2;
     pa.G = c->G;
+    pa.D = div_mode ? c->divE : nullptr;
+    pa.D_load = div_mode == 2;
     st = run_kernel(c, SR_KCLASS_PREP, s, "k_prep", [&] { return srk::launch_prep(pa, s); });
     if (st != SR_OK) return st;
     src = c->G;
@@ -571,7 +576,8 @@ sr_status enqueue_iteration(sr_ctx* c, cudaStream_t s, int p, bool check) {
   const int q = 1 - p;
   for (int it = 0; it < c->prm.inner_S; ++it) {
     const float* in = it == 0 ? c->phi[p] : c->phi[q];
-    sr_status st = enqueue_phi_step(c, s, in, c->w1[p], c->w2[p], c->e1, c->e2, c->phi[q], nullptr);
+    sr_status st = enqueue_phi_step(c, s, in, c->w1[p], c->w2[p], c->e1, c->e2, c->phi[q], nullptr,
+                                    it == 0 ? 1 : 2);
     if (st != SR_OK) return st;
   }
   return enqueue_wb(c, s, c->phi[q], c->w1[p], c->w2[p], c->e1, c->e2, c->w1[q], c->w2[q], c->e1,
@@ -683,7 +689,7 @@ void sr_destroy(sr_ctx* c) {
   drop_graphs(c);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   void* bufs[] = {c->phi[0], c->phi[1], c->w1[0], c->w1[1], c->w2[0], c->w2[1], c->e1, c->e2,
-                  c->g, c->tmp1, c->tmp2, c->stage, c->G, c->mask_dev, c->X, c->tw_row, c->tw_col,
+                  c->g, c->tmp1, c->tmp2, c->stage, c->G, c->divE, c->mask_dev, c->X, c->tw_row, c->tw_col,
                   c->tw_n, c->aM, c->aN, c->partials, c->red, c->err_dev,
                   c->tws[0], c->tws[1], c->tws[2], c->tws[3]};
   for (void* b : bufs)
@@ -776,7 +782,7 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   const size_t P = (size_t)H * W;
   float** planes[] = {&c->phi[0], &c->phi[1], &c->w1[0], &c->w1[1], &c->w2[0], &c->w2[1],
                       &c->e1,     &c->e2,     &c->g,     &c->tmp1,  &c->tmp2,  &c->stage,
-                      &c->G};
+                      &c->G,      &c->divE};
   for (float** pl : planes) CREATE_CUDA(cudaMalloc((void**)pl, P * sizeof(float)));
   CREATE_CUDA(cudaMalloc((void**)&c->mask_dev, P));
   CREATE_CUDA(cudaMalloc((void**)&c->X, (size_t)H * L * sizeof(float2)));

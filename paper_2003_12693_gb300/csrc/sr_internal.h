@@ -129,6 +129,10 @@ struct PrepArgs {
   const float* e1;         // b1 - w1
   const float* e2;         // b2 - w2
   float* G;                // increment right-hand side, H x W
+  // div e is fixed over the inner loop: with D set, the first inner step
+  // stores it there (D_load false) and the later ones read it (D_load true)
+  float* D;
+  bool D_load;
 };
 
 // w and b update with the repulsion window sum fused in; b is carried as
@@ -177,6 +181,7 @@ struct EdgeArgs {
 };
 
 enum { kRowRHS = 0, kRowLOAD = 1 };
+enum { kDivCompute = 0, kDivStore = 1, kDivLoad = 2 };
 enum { kInvADD = 0, kInvSTORE = 1 };
 
 // Shared-memory bytes of each kernel for the given configuration.

@@ -739,10 +739,13 @@ size_t tile32_smem(int R) { return (size_t)tile32_floats(R) * sizeof(float); }
 // |psi| < l + eps; e = b - w, div the backward divergence).
 // BAND = false is the form for tiles without narrow-band pixels: the band
 // terms are not evaluated at all (rather than predicated off per pixel).
+// div(b - w) = div e, backward differences (Eq. (36))
+__device__ __forceinline__ float div_e(float e1, float e1u, float e2, float e2l) {
+  return (e1 - e1u) + (e2 - e2l);
+}
 __device__ __forceinline__ float rhs_bulk(const Model& m, float x, float up, float dn, float lf,
-                                          float rt, float e1, float e1u, float e2, float e2l) {
+                                          float rt, float dv) {
   const float lap = (up + dn) + (lf + rt) - 4.f * x;
-  const float dv = (e1 - e1u) + (e2 - e2l);
   return m.mu * (dv + lap);
 }
 // the narrow-band terms added to the bulk force f at one pixel; G = tau f
@@ -844,7 +847,10 @@ __device__ __forceinline__ int any_band4(float4 v, const Model& m) {
 // its tile holds narrow-band pixels; only such tiles stage psi and w with a
 // halo for the window sum v (which enters only at band pixels, so the test
 // over the tile's own pixels is exact).
-template <int R>
+// DIV selects where div e comes from: kDivCompute forms it from e1, e2;
+// kDivStore also writes it to D (the first inner step of an outer
+// iteration: e is fixed for the whole inner loop); kDivLoad reads D.
+template <int R, int DIV>
 __global__ void __launch_bounds__(kTN, 4) k_prep(const PrepArgs a) {
   extern __shared__ __align__(16) float smem_f[];
   pdl_wait();
@@ -854,36 +860,49 @@ __global__ void __launch_bounds__(kTN, 4) k_prep(const PrepArgs a) {
   const Quad q(a.geo);
   const float* psi = a.psi;
   const float4 X = ld4_if(q.live, psi + q.o);
-  const float4 E1 = ld4_if(q.live, a.e1 + q.o), E2 = ld4_if(q.live, a.e2 + q.o);
+  float4 E1 = make_float4(0.f, 0.f, 0.f, 0.f), E2 = E1, E1u = E1, Dv = E1;
+  float e2l = 0.f;
+  if (DIV == kDivLoad) {
+    Dv = ld4_if(q.live, a.D + q.o);
+  } else {
+    E1 = ld4_if(q.live, a.e1 + q.o);
+    E2 = ld4_if(q.live, a.e2 + q.o);
+    E1u = ld4_if(q.live && q.up_g, a.e1 + (size_t)q.iu * N + q.j);
+    e2l = ld_if(q.live && q.lf_g, a.e2 + (size_t)q.i * N + q.jl);
+  }
   float4 UP = ld4_if(q.live && q.up_g, psi + (size_t)q.iu * N + q.j);
   float4 DN = ld4_if(q.live && q.dn_g, psi + (size_t)q.id * N + q.j);
-  float4 E1u = ld4_if(q.live && q.up_g, a.e1 + (size_t)q.iu * N + q.j);
   float LF = ld_if(q.live && q.lf_g, psi + (size_t)q.i * N + q.jl);
   float RT = ld_if(q.live && q.rt_g, psi + (size_t)q.i * N + q.jr);
-  float e2l = ld_if(q.live && q.lf_g, a.e2 + (size_t)q.i * N + q.jl);
   const bool band = __syncthreads_or(q.live && any_band4(X, m)) != 0;
   {
-    const float4 su = shfl_up4(X, kTBX), sd = shfl_down4(X, kTBX), se = shfl_up4(E1, kTBX);
+    const float4 su = shfl_up4(X, kTBX), sd = shfl_down4(X, kTBX);
     const float sl = __shfl_up_sync(0xffffffffu, X.w, 1);
     const float sr = __shfl_down_sync(0xffffffffu, X.x, 1);
-    const float sel = __shfl_up_sync(0xffffffffu, E2.w, 1);
-    if (!q.up_g) UP = su, E1u = se;
+    if (!q.up_g) UP = su;
     if (!q.dn_g) DN = sd;
-    if (!q.lf_g) LF = sl, e2l = sel;
+    if (!q.lf_g) LF = sl;
     if (!q.rt_g) RT = sr;
+    if (DIV != kDivLoad) {
+      const float4 se = shfl_up4(E1, kTBX);
+      const float sel = __shfl_up_sync(0xffffffffu, E2.w, 1);
+      if (!q.up_g) E1u = se;
+      if (!q.lf_g) e2l = sel;
+      Dv = make_float4(div_e(E1.x, E1u.x, E2.x, e2l), div_e(E1.y, E1u.y, E2.y, E2.x),
+                       div_e(E1.z, E1u.z, E2.z, E2.y), div_e(E1.w, E1u.w, E2.w, E2.z));
+      if (DIV == kDivStore && q.live) st4(a.D + q.o, Dv);
+    }
   }
-  // the stencil part of the force first, so that only x and f stay live
-  // across the narrow-band work
+  // the stencil part of the force first, so that only psi and the force stay
+  // live across the narrow-band work
   float f[4];
   {
     const float x[4] = {X.x, X.y, X.z, X.w};
     const float up[4] = {UP.x, UP.y, UP.z, UP.w}, dn[4] = {DN.x, DN.y, DN.z, DN.w};
     const float lf[4] = {LF, X.x, X.y, X.z}, rt[4] = {X.y, X.z, X.w, RT};
-    const float e1[4] = {E1.x, E1.y, E1.z, E1.w}, e2[4] = {E2.x, E2.y, E2.z, E2.w};
-    const float e1u[4] = {E1u.x, E1u.y, E1u.z, E1u.w}, e2l4[4] = {e2l, E2.x, E2.y, E2.z};
+    const float dv[4] = {Dv.x, Dv.y, Dv.z, Dv.w};
 #pragma unroll
-    for (int t = 0; t < 4; ++t)
-      f[t] = rhs_bulk(m, x[t], up[t], dn[t], lf[t], rt[t], e1[t], e1u[t], e2[t], e2l4[t]);
+    for (int t = 0; t < 4; ++t) f[t] = rhs_bulk(m, x[t], up[t], dn[t], lf[t], rt[t], dv[t]);
   }
   float out[4];
   if (band) {  // uniform across the block
@@ -1182,7 +1201,9 @@ cudaError_t configure_kernels() {
   if ((e = allow_big_smem(k_rowinv<kInvADD>))) return e;
   if ((e = allow_big_smem(k_rowinv<kInvSTORE>))) return e;
 #define SR_CASE(r)                                                   \
-  if ((e = allow_big_smem(k_prep<r>)) != cudaSuccess) return e;      \
+  if ((e = allow_big_smem(k_prep<r, kDivCompute>)) != cudaSuccess) return e; \
+  if ((e = allow_big_smem(k_prep<r, kDivStore>)) != cudaSuccess) return e;   \
+  if ((e = allow_big_smem(k_prep<r, kDivLoad>)) != cudaSuccess) return e;    \
   if ((e = allow_big_smem(k_wb_update<r>)) != cudaSuccess) return e;
   SR_FOR_R(SR_CASE)
 #undef SR_CASE
@@ -1238,7 +1259,10 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
   const size_t sm = tile32_smem(a.mod.R);
   switch (a.mod.R) {
 #define SR_CASE(r) \
-  case r: return launch_k(k_prep<r>, g, b, sm, s, a);
+  case r:                                                                    \
+    return a.D == nullptr ? launch_k(k_prep<r, kDivCompute>, g, b, sm, s, a)  \
+           : a.D_load     ? launch_k(k_prep<r, kDivLoad>, g, b, sm, s, a)     \
+                          : launch_k(k_prep<r, kDivStore>, g, b, sm, s, a);
     SR_FOR_R(SR_CASE)
 #undef SR_CASE
     default: return cudaErrorInvalidValue;
