@@ -243,6 +243,26 @@ long long sr_kernel_launches(const sr_ctx* ctx, int reset);
 sr_status sr_profile_enable(sr_ctx* ctx, int enable);
 sr_status sr_kernel_times(sr_ctx* ctx, int kclass, double* total_ms, long long* launches);
 
+/* Batched iteration (many images, uneven sizes).  A group holds n contexts
+ * created on the same device with the same stream (sizes may differ; every
+ * size sr_create accepts).  sr_group_iterate runs max_outer outer iterations
+ * of Alg. 1 on every member: one CUDA graph per parity holds the members'
+ * iterations as concurrent branches (each a chain of its own kernels), so
+ * small images share the GPU instead of running one after another.  Each
+ * member's results are bit-identical to sr_iterate(member, max_outer, 0, ...)
+ * on that member alone.  There is no stopping test inside the group call
+ * (tol = 0 semantics); sr_iterate on a member afterwards gives its relative
+ * change.  The members must be at the same parity: created or reset with
+ * sr_set_phi / sr_set_state together and iterated only through the group, or
+ * by the same counts.
+ *   Errors: SR_EINVAL for n < 1, a NULL member, members on different streams
+ *   or devices, or members at different parities; SR_ECUDA as usual.  The
+ *   group does not own the contexts: destroy the group first. */
+typedef struct sr_group sr_group;
+sr_status sr_group_create(sr_ctx* const* members, int n, sr_group** out);
+sr_status sr_group_iterate(sr_group* group, int max_outer);
+void sr_group_destroy(sr_group* group);
+
 /* Convenience for callers with host buffers: copy the image and phi0 from
  * host memory (pinned memory gives asynchronous copies), compute g, set
  * phi0, run max_outer iterations (tol as in sr_iterate), and copy the mask

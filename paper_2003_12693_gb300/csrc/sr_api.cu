@@ -1121,6 +1121,127 @@ sr_status sr_kernel_times(sr_ctx* c, int kclass, double* total_ms, long long* la
   return SR_OK;
 }
 
+// ---- groups: many contexts iterated by one graph with concurrent branches ----
+}  // extern "C"
+
+struct sr_group {
+  std::vector<sr_ctx*> m;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // per parity
+  int device = 0;
+};
+
+namespace {
+
+void group_release(sr_group* g) {
+  for (int p = 0; p < 2; ++p)
+    if (g->graph[p]) cudaGraphExecDestroy(g->graph[p]);
+  delete g;
+}
+
+// One outer iteration of every member (parity p), each captured on its own
+// stream exactly as sr_iterate captures it and placed as a child graph of one
+// parent graph.  The members are spread over a bounded number of lanes
+// (longest-processing-time first, by pixel count); members of one lane run
+// one after another, the lanes run concurrently.  On failure, why holds the
+// member's message.
+cudaError_t group_build(sr_group* g, int p, std::string& why) {
+  const int n = (int)g->m.size();
+  int lanes = 32;  // measured best of 8, 16, 32 on 64-256 images of 64..1024 px sides
+  if (const char* env = std::getenv("SR_GROUP_LANES")) lanes = std::max(1, std::atoi(env));
+  lanes = std::min(lanes, n);
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (long long)g->m[a]->H * g->m[a]->W > (long long)g->m[b]->H * g->m[b]->W;
+  });
+  std::vector<long long> load(lanes, 0);
+  std::vector<cudaGraphNode_t> last(lanes, nullptr);
+  cudaGraph_t parent = nullptr;
+  cudaError_t e = cudaGraphCreate(&parent, 0);
+  for (int idx = 0; idx < n && e == cudaSuccess; ++idx) {
+    sr_ctx* c = g->m[order[idx]];
+    const int lane = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[lane] += (long long)c->H * c->W;
+    cudaGraph_t child = nullptr;
+    e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    const long long before = c->launches;
+    const sr_status st = enqueue_iteration(c, c->cap_stream, p, false);
+    c->graph_kernels = (int)(c->launches - before);
+    c->launches = before;  // capture enqueues nothing
+    e = cudaStreamEndCapture(c->cap_stream, &child);
+    if (st != SR_OK) {
+      why = c->err;
+      if (e == cudaSuccess) e = cudaErrorUnknown;
+    }
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess)
+      e = cudaGraphAddChildGraphNode(&node, parent, last[lane] ? &last[lane] : nullptr,
+                                     last[lane] ? 1 : 0, child);
+    if (e == cudaSuccess) last[lane] = node;
+    if (child) cudaGraphDestroy(child);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g->graph[p], parent, 0);
+  if (parent) cudaGraphDestroy(parent);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+sr_status sr_group_create(sr_ctx* const* members, int n, sr_group** out) {
+  if (!out) return SR_EINVAL;
+  *out = nullptr;
+  if (!members || n < 1) return SR_EINVAL;
+  for (int k = 0; k < n; ++k)
+    if (!members[k]) return SR_EINVAL;
+  sr_ctx* c0 = members[0];
+  for (int k = 0; k < n; ++k)
+    if (members[k]->profile) return fail(c0, SR_EINVAL, "group members must not be profiling");
+  for (int k = 1; k < n; ++k) {
+    if (members[k]->stream != c0->stream || members[k]->device != c0->device)
+      return fail(c0, SR_EINVAL, "group members must share the device and the stream");
+  }
+  sr_group* g = new sr_group;
+  g->m.assign(members, members + n);
+  g->device = c0->device;
+  cudaError_t e = cudaSuccess;
+  std::string why;
+  for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = group_build(g, p, why);
+  if (e != cudaSuccess) {
+    group_release(g);
+    if (!why.empty()) return fail(c0, SR_ECUDA, "sr_group_create: " + why);
+    return cuda_fail(c0, e, "sr_group_create");
+  }
+  *out = g;
+  return SR_OK;
+}
+
+sr_status sr_group_iterate(sr_group* g, int max_outer) {
+  if (!g) return SR_EINVAL;
+  sr_ctx* c0 = g->m[0];
+  if (max_outer < 0) return fail(c0, SR_EINVAL, "max_outer must be >= 0");
+  for (sr_ctx* c : g->m) {
+    if (c->cur != c0->cur) return fail(c0, SR_EINVAL, "group members are at different parities");
+    if (c->profile) return fail(c0, SR_EINVAL, "group members must not be profiling");
+  }
+  for (int k = 0; k < max_outer; ++k) {
+    cudaError_t e = cudaGraphLaunch(g->graph[c0->cur], c0->stream);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "cudaGraphLaunch (group)");
+    for (sr_ctx* c : g->m) {
+      c->launches += c->graph_kernels;
+      c->cur ^= 1;
+      c->iters += 1;
+    }
+  }
+  return SR_OK;
+}
+
+void sr_group_destroy(sr_group* g) {
+  if (g) group_release(g);
+}
+
 sr_status sr_segment_host(sr_ctx* c, const float* image_host, const float* phi0_host,
                           int max_outer, double tol, unsigned char* mask_host, float* phi_host,
                           int* outer_done, double* rel_change) {

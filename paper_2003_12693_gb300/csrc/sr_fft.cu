@@ -506,7 +506,19 @@ using namespace fft2;
 
 template <class K>
 static cudaError_t set_smem(K kernel, size_t smem) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // The attribute belongs to the kernel, not to a context: contexts of other
+  // sizes launch the same instantiation with other shared-memory sizes, so
+  // raise it to the device maximum once instead of to this context's size.
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  const int limit = optin - (int)fa.sharedSizeBytes;
+  if ((int)smem > limit) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
 }
 
 template <int LOGL, int LOGE>

@@ -112,6 +112,12 @@ def lib() -> C.CDLL:
     L.sr_segment_host.restype = st
     L.sr_segment_host.argtypes = [_P, _P, _P, C.c_int, C.c_double, _P, _P,
                                   C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.sr_group_create.restype = st
+    L.sr_group_create.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(_P)]
+    L.sr_group_iterate.restype = st
+    L.sr_group_iterate.argtypes = [_P, C.c_int]
+    L.sr_group_destroy.restype = None
+    L.sr_group_destroy.argtypes = [_P]
     _lib = L
     return L
 
@@ -300,6 +306,34 @@ class Context:
                                    C.byref(done), C.byref(rel))
         _check(st, self)
         return done.value, rel.value
+
+
+class Group:
+    """Many contexts (sizes may differ) iterated by one CUDA graph whose
+    branches run concurrently (sr_group_create / sr_group_iterate).  The group
+    does not own the contexts; close it before them."""
+
+    def __init__(self, members: list["Context"]):
+        self.members = list(members)
+        arr = (_P * len(members))(*[m.handle for m in members])
+        h = _P()
+        st = lib().sr_group_create(arr, len(members), C.byref(h))
+        _check(st, members[0] if members else None)
+        self.handle = h
+
+    def iterate(self, max_outer: int):
+        _check(lib().sr_group_iterate(self.handle, int(max_outer)), self.members[0])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sr_group_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def phi_step_noalloc(params: sr_params, g: torch.Tensor, psi: torch.Tensor, w1: torch.Tensor,
