@@ -247,17 +247,17 @@ def _time_crop(f, phi0, p, c):
 # ----------------------------------------------------------------------------
 def batched_sample(stream, n_images: int = 256, iters: int = 100) -> dict:
     """Many small images in one graph (sr_group_*) against the same images one
-    after another.  Sides drawn (seed 3) from the powers of two 64..1024: a
-    stand-in for a mix of sides 64, 96, ..., 1024 (the mixed-radix transforms
-    such sides need are not built).  Each image is the six-ellipse scene of its
-    size (one scene per size pair), inset-rectangle start, R = d = 4."""
+    after another.  Height and width drawn independently (seed 3) from the
+    31 sides 64, 96, ..., 1024; sides that are not powers of two run the
+    mixed-radix FFT passes.  Each image is the six-ellipse scene of its size
+    (one scene per size pair), inset-rectangle start, R = d = 4."""
     import numpy as np
     import torch
 
     from paper_2003_12693_gb300 import sr, synth
 
     rng = np.random.default_rng(3)
-    sides = [64, 128, 256, 512, 1024]
+    sides = list(range(64, 1025, 32))
     scenes, ctxs, P = {}, [], 0
     for k in range(n_images):
         H, W = int(rng.choice(sides)), int(rng.choice(sides))
@@ -292,7 +292,7 @@ def batched_sample(stream, n_images: int = 256, iters: int = 100) -> dict:
     grp.close()
     for c in ctxs:
         c.close()
-    return {"images": n_images, "pixels": P, "sides": sides, "iterations": iters,
+    return {"images": n_images, "pixels": P, "sides": "64, 96, ..., 1024", "iterations": iters,
             "value": P * iters / t_group / 1e6, "unit": UNIT,
             "one_by_one": P * iters / t_seq / 1e6, "speedup": t_seq / t_group,
             "how": "sr_group_iterate: one CUDA graph per parity, members' iterations as "

@@ -73,8 +73,12 @@ sr_status sr_params_default(sr_params* p);
 /* Create a solver for H x W images.  Validates the parameters (finite, mu,
  * tau, eps > 0, 0 <= R <= 8, S >= 1, s in {1, 2}), allocates the device state
  * and FFT workspace and builds the twiddle and symbol tables of Eq. (32).
- * Supported sizes in this build: H and W powers of two in [16, 4096]
- * (SR_EUNSUPPORTED otherwise).  cuda_stream is a cudaStream_t (may be 0). */
+ * Supported sizes: H and W multiples of 16 in [16, 4096] such that H and
+ * W/2 have no prime factor above 31 (SR_EUNSUPPORTED otherwise).  Powers of
+ * two use register-resident FFT passes with an autotuned schedule, other
+ * sides (e.g. 96, 160, 224) mixed-radix shared-memory passes with radices 16,
+ * 8, 4, 2, 3, 5 and direct DFTs of the other primes.  cuda_stream is a
+ * cudaStream_t (may be 0). */
 sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx** out);
 
 /* Release everything the context owns.  NULL is ignored. */

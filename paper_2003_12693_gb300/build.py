@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsr.so")
-SOURCES = ["sr_kernels.cu", "sr_fft.cu", "sr_api.cu", "sr_noalloc.cu"]
+SOURCES = ["sr_kernels.cu", "sr_fft.cu", "sr_fftgen.cu", "sr_api.cu", "sr_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

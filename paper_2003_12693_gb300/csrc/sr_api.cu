@@ -36,6 +36,9 @@ struct sr_ctx {
   Fft fft_row{}, fft_col{};
   int row_T = 0, row_NT = 0, row_CW = 0;
   bool fft2 = false;  // register-resident FFT passes (sr_fft.cu) for this size
+  bool fftgen = false;  // mixed-radix passes (sr_fftgen.cu): a side is not a power of two
+  srk::GenPlan plan_row{}, plan_col{};
+  float2* gen_tab = nullptr;  // stage twiddles and roots of both plans
   sr_schedule sched{};  // schedule of the fft2 passes
   CUtensorMap tm_X{};   // X as a float32 matrix, boxes for the TMA column pass
   bool tm_X_ok = false;
@@ -156,6 +159,50 @@ sr_status check_params(const sr_params* p, std::string& why) {
     return SR_EUNSUPPORTED;
   }
   return SR_OK;
+}
+
+// Mixed-radix plan of length n: radix-16 stages, one radix 8, 4 or 2 for the
+// rest of the power of two, then the odd primes (each at most 31).  Appends
+// the stage twiddles exp(-2 pi i t k / (Ns R)) and, for primes without a
+// dedicated butterfly, the roots exp(-2 pi i e / R) to tab (FP64, rounded).
+bool gen_plan(int n, srk::GenPlan& P, std::vector<float2>& tab, std::vector<int>& root_at) {
+  std::vector<int> rad;
+  int m = n;
+  while (m % 16 == 0) rad.push_back(16), m /= 16;
+  if (m % 8 == 0) rad.push_back(8), m /= 8;
+  else if (m % 4 == 0) rad.push_back(4), m /= 4;
+  else if (m % 2 == 0) rad.push_back(2), m /= 2;
+  for (int p = 3; p < srk::kGenMaxRadix && m > 1; p += 2)
+    while (m % p == 0) rad.push_back(p), m /= p;
+  if (m != 1 || (int)rad.size() > srk::kGenMaxStages) return false;
+  P = srk::GenPlan{};
+  P.n = n;
+  P.nst = (int)rad.size();
+  int Ns = 1;
+  for (int s = 0; s < P.nst; ++s) {
+    const int R = rad[s];
+    P.radix[s] = R;
+    P.ns[s] = Ns;
+    P.twoff[s] = (int)tab.size();
+    for (int t = 1; t < R; ++t)
+      for (int k = 0; k < Ns; ++k) {
+        const double a = -2.0 * M_PI * (double)t * (double)k / ((double)Ns * R);
+        tab.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+      }
+    const bool dedicated = R == 2 || R == 3 || R == 4 || R == 5 || R == 8 || R == 16;
+    if (!dedicated) {
+      if (root_at[R] < 0) {
+        root_at[R] = (int)tab.size();
+        for (int e = 0; e < R; ++e) {
+          const double a = -2.0 * M_PI * (double)e / (double)R;
+          tab.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+        }
+      }
+      P.rootoff[s] = root_at[R];
+    }
+    Ns *= R;
+  }
+  return true;
 }
 
 void make_fft(Fft& f, int L, const float2* tw) {
@@ -506,9 +553,10 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
   fa.twN = c->tw_n;
   fa.src = src;
   fa.X = c->X;
-  fa.T = c->fft2 ? sched_rows(c, c->sched) : c->row_T;
+  fa.T = c->fft2 ? sched_rows(c, c->sched) : c->fftgen ? srk::gen_rows_per_cta(c->L) : c->row_T;
   fa.CW = c->row_CW;
   st = run_kernel(c, SR_KCLASS_ROWFFT, s, "k_rowfwd", [&] {
+    if (c->fftgen) return srk::launch_rowfft_gen(fa, c->plan_row, s);
     return c->fft2 ? srk::launch_rowfft2(fa, c->sched.row_values_per_thread == 8 ? 3 : 4,
                                          c->sched.row_threads, s, false)
                    : srk::launch_rowfwd(fa, srk::kRowLOAD, c->row_NT, s);
@@ -522,6 +570,7 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
   ca.X = c->X;
   ca.err = c->err_dev;
   st = run_kernel(c, SR_KCLASS_COLSOLVE, s, "k_colsolve", [&] {
+    if (c->fftgen) return srk::launch_colsolve_gen(ca, c->plan_col, s);
     if (!c->fft2) return srk::launch_colsolve(ca, s);
     if (c->sched.col_schedule == 3)
       return srk::launch_colsolve_tma(ca, c->tm_X, c->col_tma_grid, s, false);
@@ -535,9 +584,10 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
   ia.X = c->X;
   ia.psi_in = psi_in;
   ia.out = psi_out;
-  ia.T = c->fft2 ? sched_rows(c, c->sched) : c->row_T;
+  ia.T = c->fft2 ? sched_rows(c, c->sched) : c->fftgen ? srk::gen_rows_per_cta(c->L) : c->row_T;
   const int imode = load_src ? srk::kInvSTORE : srk::kInvADD;
   return run_kernel(c, SR_KCLASS_ROWIFFT, s, "k_rowinv", [&] {
+    if (c->fftgen) return srk::launch_rowifft_gen(ia, c->plan_row, imode == srk::kInvADD, s);
     return c->fft2 ? srk::launch_rowifft2(ia, imode == srk::kInvADD,
                                           c->sched.row_values_per_thread == 8 ? 3 : 4,
                                           c->sched.row_threads, s, false)
@@ -690,7 +740,7 @@ void sr_destroy(sr_ctx* c) {
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   void* bufs[] = {c->phi[0], c->phi[1], c->w1[0], c->w1[1], c->w2[0], c->w2[1], c->e1, c->e2,
                   c->g, c->tmp1, c->tmp2, c->stage, c->G, c->divE, c->mask_dev, c->X, c->tw_row, c->tw_col,
-                  c->tw_n, c->aM, c->aN, c->partials, c->red, c->err_dev,
+                  c->tw_n, c->aM, c->aN, c->partials, c->red, c->err_dev, c->gen_tab,
                   c->tws[0], c->tws[1], c->tws[2], c->tws[3]};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -706,8 +756,17 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   std::string why;
   sr_status st = check_params(p, why);
   if (st != SR_OK) return st;
-  if (!is_pow2(H) || !is_pow2(W) || H < 16 || W < 16 || H > 4096 || W > 4096)
-    return SR_EUNSUPPORTED;
+  // powers of two use the register-resident passes; other sides (multiples of
+  // 16 whose prime factors are at most 31) the mixed-radix passes
+  if (H < 16 || W < 16 || H > 4096 || W > 4096 || H % 16 || W % 16) return SR_EUNSUPPORTED;
+  const bool pow2 = is_pow2(H) && is_pow2(W);
+  {
+    srk::GenPlan tmp;
+    std::vector<float2> tab;
+    std::vector<int> at(srk::kGenMaxRadix, -1);
+    if (!pow2 && (!gen_plan(H, tmp, tab, at) || !gen_plan(W / 2, tmp, tab, at)))
+      return SR_EUNSUPPORTED;
+  }
 
   sr_ctx* c = new (std::nothrow) sr_ctx();
   if (!c) return SR_ENOMEM;
@@ -719,7 +778,7 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   c->geo.M = H;
   c->geo.N = W;
   c->geo.L = W / 2;
-  c->geo.logN = ilog2(W);
+  c->geo.logN = ilog2(W);  // used by the power-of-two paths only
 
   auto bail = [&](sr_status s) {
     sr_destroy(c);
@@ -760,21 +819,24 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   for (int t = -m.R; t <= m.R; ++t)
     m.kw[t + m.R] = (float)std::exp(-(double)(t * t) / ((double)p->d * (double)p->d));
 
-  // row-pass shape: T rows per CTA with T * (W/2) = 16 * threads
+  // row-pass shape of the fixed small-size passes (powers of two): T rows per
+  // CTA with T * (W/2) = 16 * threads
   const int L = c->L;
-  int NT = L >= 2048 ? 512 : 256;
-  int T = 16 * NT / L;
-  while (NT > 64 && T > 1 && (H + T - 1) / T < 2 * c->nsm) {
-    NT /= 2;
-    T = 16 * NT / L;
+  if (pow2) {
+    int NT = L >= 2048 ? 512 : 256;
+    int T = 16 * NT / L;
+    while (NT > 64 && T > 1 && (H + T - 1) / T < 2 * c->nsm) {
+      NT /= 2;
+      T = 16 * NT / L;
+    }
+    if (T > H) {
+      T = H;
+      NT = T * L / 16;
+    }
+    if (T < 1 || NT < 1 || NT * 16 != T * L) return bail(SR_EUNSUPPORTED);
+    c->row_T = T;
+    c->row_NT = NT;
   }
-  if (T > H) {
-    T = H;
-    NT = T * L / 16;
-  }
-  if (T < 1 || NT < 1 || NT * 16 != T * L) return bail(SR_EUNSUPPORTED);
-  c->row_T = T;
-  c->row_NT = NT;
   c->row_CW = W < 128 ? W : 128;
   c->n_tile = srk::tile_blocks(c->geo);
   c->n_tile32 = srk::tile32_blocks(c->geo);
@@ -810,7 +872,7 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   if (upload(c, &c->aN, aN) != SR_OK) return bail(SR_ECUDA);
   make_fft(c->fft_row, L, c->tw_row);
   make_fft(c->fft_col, H, c->tw_col);
-  {
+  if (pow2) {
     const int lens[4] = {L, L, H, H}, loges[4] = {4, 3, 4, 3};
     for (int q = 0; q < 4; ++q) {
       std::vector<float2> tb = stage_twiddle_table(lens[q], loges[q]);
@@ -825,7 +887,18 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   }
   CREATE_CUDA(cudaMalloc((void**)&c->err_dev, sizeof(int)));
   CREATE_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
-  c->fft2 = srk::fft2_supported(c->geo);
+  c->fft2 = pow2 && srk::fft2_supported(c->geo);
+  if (!pow2) {
+    std::vector<float2> tab;
+    std::vector<int> at(srk::kGenMaxRadix, -1);
+    gen_plan(W / 2, c->plan_row, tab, at);
+    gen_plan(H, c->plan_col, tab, at);
+    if (upload(c, &c->gen_tab, tab) != SR_OK) return bail(SR_ECUDA);
+    c->plan_row.tw = c->plan_row.roots = c->gen_tab;
+    c->plan_col.tw = c->plan_col.roots = c->gen_tab;
+    CREATE_CUDA(srk::configure_fftgen());
+    c->fftgen = true;
+  }
   if (c->fft2) {
     const int cb = srk::colsolve_tma_cb(H);
     c->tm_X_ok = make_tensor_map_2d(&c->tm_X, c->X, H, W, W, 2 * cb, H < 256 ? H : 256);

@@ -96,6 +96,21 @@ struct RowFwdArgs {
   int CW;                  // column chunk of the window sum
 };
 
+// Mixed-radix Stockham plan of one length (sides that are not powers of two).
+constexpr int kGenMaxRadix = 32;      // largest radix (primes up to 31)
+constexpr int kGenMaxStages = 16;
+constexpr int kGenSmemFloat2 = 12288; // shared-memory budget per CTA: 96 KB
+struct GenPlan {
+  int n;
+  int nst;
+  int radix[kGenMaxStages];
+  int ns[kGenMaxStages];      // product of the earlier radices
+  int twoff[kGenMaxStages];   // stage twiddles at tw + twoff[s] + (t-1) ns[s] + k
+  int rootoff[kGenMaxStages]; // roots exp(-2 pi i e / R) at roots + rootoff[s] + e
+  const float2* tw;
+  const float2* roots;
+};
+
 // Column pass: forward column FFT, divide by the symbol of Eq. (32), inverse.
 struct ColArgs {
   Geo geo;
@@ -218,6 +233,13 @@ cudaError_t configure_kernels();   // raise dynamic shared-memory limits once
 // values per thread; 2 columns at H = 4096), 1 (2 columns, 8 values),
 // 2 (4 columns, 8 values).
 bool fft2_supported(const Geo& geo);
+
+// Mixed-radix passes (sr_fftgen.cu) for sides that are not powers of two.
+int gen_rows_per_cta(int n);
+cudaError_t configure_fftgen();
+cudaError_t launch_rowfft_gen(const RowFwdArgs& a, const GenPlan& P, cudaStream_t s);
+cudaError_t launch_colsolve_gen(const ColArgs& a, const GenPlan& P, cudaStream_t s);
+cudaError_t launch_rowifft_gen(const RowInvArgs& a, const GenPlan& P, bool add, cudaStream_t s);
 size_t rowfft2_smem(int T, int L, int logE);
 int stage_twiddles(int L, int logE);  // entries of the stage-twiddle table
 cudaError_t launch_rowfft2(const RowFwdArgs& a, int logE, int nthreads, cudaStream_t s,

@@ -48,7 +48,8 @@ def test_create_rejects_bad_parameters_before_touching_cuda(srmod, kw, status):
     assert st == status and not h.value
 
 
-@pytest.mark.parametrize("H,W", [(0, 64), (64, -1), (48, 64), (64, 100), (8, 64), (8192, 64)])
+@pytest.mark.parametrize("H,W", [(0, 64), (64, -1), (40, 64), (64, 100), (8, 64), (8192, 64),
+                                 (592, 64), (64, 1184)])
 def test_create_rejects_unsupported_sizes(srmod, H, W):
     st, h = _create(srmod, H, W)
     assert st in (1, 7) and not h.value

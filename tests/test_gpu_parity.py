@@ -199,6 +199,20 @@ def test_one_outer_iteration_full_size_2048():
     ctx.close()
 
 
+def test_one_outer_iteration_full_size_4096():
+    """The largest single image (4096^2 blob pairs 1-3 px apart, R = d = 8, the
+    17 x 17 window): one outer iteration from phi0, every pixel compared."""
+    wl = synth.WORKLOADS["blobs_4096"]
+    p = oracle.Params.from_dict(wl.params())
+    g64 = f32(oracle.edge(wl.image()))
+    st = oracle_state_after(wl.phi0(), g64, 0, p)
+    state = rounded_state(st)
+    ctx = context(wl.H, wl.W, R=wl.R, d=wl.d)
+    gpu, ref = one_iteration_both(ctx, state, g64, p)
+    check_one_iteration(gpu, ref, state, g64, p)
+    ctx.close()
+
+
 # ---------------------------------------------------------------- whole run
 @pytest.fixture(scope="module")
 def two_disks_full():
