@@ -111,35 +111,67 @@ __device__ __forceinline__ void dft5(float2* x, bool inv) {
   x[3] = csub(r2, i2);
 }
 
-// Length-R DFT of x (R a prime without a dedicated butterfly): y_q =
-// sum_t x_t root[(t q) mod R], root[e] = exp(-2 pi i e / R) (conjugated when
-// inv).
-__device__ __forceinline__ void dft_direct(float2* x, int R, bool inv, const float2* root) {
-  float2 y[kGenMaxRadix];
-  for (int q = 0; q < R; ++q) {
-    float2 acc = make_float2(0.f, 0.f);
-    int e = 0;
-    for (int t = 0; t < R; ++t) {
-      float2 w = __ldg(root + e);
-      if (inv) w.y = -w.y;
-      acc = make_float2(acc.x + x[t].x * w.x - x[t].y * w.y, acc.y + x[t].x * w.y + x[t].y * w.x);
-      e += q;
-      if (e >= R) e -= R;
-    }
-    y[q] = acc;
-  }
-  for (int q = 0; q < R; ++q) x[q] = y[q];
+template <int R>
+__host__ __device__ constexpr bool dedicated() {
+  return R == 2 || R == 3 || R == 4 || R == 5 || R == 8 || R == 16;
 }
 
-__device__ __forceinline__ void dft_any(float2* x, int R, bool inv, const float2* root) {
-  switch (R) {
-    case 2: dft2(x); break;
-    case 3: dft3(x, inv); break;
-    case 4: dft4(x, inv); break;
-    case 5: dft5(x, inv); break;
-    case 8: dft8(x, inv); break;
-    case 16: dft16(x, inv); break;
-    default: dft_direct(x, R, inv, root); break;
+template <int R>
+__device__ __forceinline__ void dft_fixed(float2 (&x)[R], bool inv) {
+  if constexpr (R == 2) dft2(x);
+  else if constexpr (R == 3) dft3(x, inv);
+  else if constexpr (R == 4) dft4(x, inv);
+  else if constexpr (R == 5) dft5(x, inv);
+  else if constexpr (R == 8) dft8(x, inv);
+  else if constexpr (R == 16) dft16(x, inv);
+}
+
+// One Stockham stage of radix R over nseq sequences of length n (a -> b).
+// Primes without a dedicated butterfly take the direct DFT y_q = sum_t x_t
+// root[(t q) mod R], root[e] = exp(-2 pi i e / R) (conjugated when inv),
+// each y_q written as soon as it is summed.
+template <int R>
+__device__ __forceinline__ void stage_r(const float2* a, float2* b, int nseq, int n, int Ns,
+                                        const float2* tw, const float2* root, bool inv) {
+  const int m = n / R;
+  for (int idx = threadIdx.x; idx < nseq * m; idx += blockDim.x) {
+    const int q = idx / m, j = idx - q * m;
+    const int k = j % Ns;
+    const float2* in = a + (size_t)q * n;
+    float2* out = b + (size_t)q * n;
+    float2 v[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) v[t] = in[j + t * m];
+    if (Ns > 1) {
+#pragma unroll
+      for (int t = 1; t < R; ++t) {
+        float2 w = __ldg(tw + (t - 1) * Ns + k);
+        if (inv) w.y = -w.y;
+        v[t] = cmul(v[t], w);
+      }
+    }
+    const int o = (j / Ns) * Ns * R + k;
+    if constexpr (dedicated<R>()) {
+      dft_fixed<R>(v, inv);
+#pragma unroll
+      for (int t = 0; t < R; ++t) out[o + t * Ns] = v[t];
+    } else {
+#pragma unroll 1
+      for (int y = 0; y < R; ++y) {
+        float2 acc = v[0];
+        int e = 0;  // (t y) mod R
+#pragma unroll
+        for (int t = 1; t < R; ++t) {
+          e += y;
+          if (e >= R) e -= R;
+          float2 w = __ldg(root + e);
+          if (inv) w.y = -w.y;
+          acc.x += v[t].x * w.x - v[t].y * w.y;
+          acc.y += v[t].x * w.y + v[t].y * w.x;
+        }
+        out[o + y * Ns] = acc;
+      }
+    }
   }
 }
 
@@ -149,26 +181,16 @@ __device__ __forceinline__ void dft_any(float2* x, int R, bool inv, const float2
 __device__ float2* stockham(float2* a, float2* b, int nseq, const GenPlan& P, bool inv) {
   const int n = P.n;
   for (int s = 0; s < P.nst; ++s) {
-    const int R = P.radix[s], Ns = P.ns[s], m = n / R;
+    const int Ns = P.ns[s];
     const float2* tw = P.tw + P.twoff[s];
     const float2* root = P.roots + P.rootoff[s];
-    for (int idx = threadIdx.x; idx < nseq * m; idx += blockDim.x) {
-      const int q = idx / m, j = idx - q * m;
-      const int k = j % Ns;
-      const float2* in = a + (size_t)q * n;
-      float2* out = b + (size_t)q * n;
-      float2 v[kGenMaxRadix];
-      for (int t = 0; t < R; ++t) {
-        v[t] = in[j + t * m];
-        if (t > 0 && Ns > 1) {
-          float2 w = __ldg(tw + (t - 1) * Ns + k);
-          if (inv) w.y = -w.y;
-          v[t] = cmul(v[t], w);
-        }
-      }
-      dft_any(v, R, inv, root);
-      const int o = (j / Ns) * Ns * R + k;
-      for (int t = 0; t < R; ++t) out[o + t * Ns] = v[t];
+    switch (P.radix[s]) {
+#define SR_RADIX(r) \
+  case r: stage_r<r>(a, b, nseq, n, Ns, tw, root, inv); break;
+      SR_RADIX(2) SR_RADIX(3) SR_RADIX(4) SR_RADIX(5) SR_RADIX(7) SR_RADIX(8) SR_RADIX(11)
+      SR_RADIX(13) SR_RADIX(16) SR_RADIX(17) SR_RADIX(19) SR_RADIX(23) SR_RADIX(29) SR_RADIX(31)
+#undef SR_RADIX
+      default: break;  // the host builds plans from these radices only
     }
     __syncthreads();
     float2* tmp = a;
@@ -181,7 +203,7 @@ __device__ float2* stockham(float2* a, float2* b, int nseq, const GenPlan& P, bo
 // ---------------------------------------------------------------------------
 // rows, forward: z[n] = G[2n] + i G[2n+1], FFT_L, even/odd split -> X
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_rowfft_gen(const RowFwdArgs a, const GenPlan P) {
+__global__ void __launch_bounds__(256, 2) k_rowfft_gen(const RowFwdArgs a, const GenPlan P) {
   extern __shared__ __align__(16) float2 gsm[];
   pdl_wait();
   pdl_trigger();
@@ -215,7 +237,7 @@ __global__ void __launch_bounds__(256) k_rowfft_gen(const RowFwdArgs a, const Ge
 // ---------------------------------------------------------------------------
 // columns: CB columns of X per CTA, forward FFT_M, / (M N lambda), inverse
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_colsolve_gen(const ColArgs a, const GenPlan P, int CB) {
+__global__ void __launch_bounds__(256, 2) k_colsolve_gen(const ColArgs a, const GenPlan P, int CB) {
   extern __shared__ __align__(16) float2 gsm[];
   pdl_wait();
   pdl_trigger();
@@ -265,7 +287,7 @@ __global__ void __launch_bounds__(256) k_colsolve_gen(const ColArgs a, const Gen
 // rows, inverse: rebuild the length-L sequence, inverse FFT_L, interleave,
 // add psi (ADD) or store
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_rowifft_gen(const RowInvArgs a, const GenPlan P, int add) {
+__global__ void __launch_bounds__(256, 2) k_rowifft_gen(const RowInvArgs a, const GenPlan P, int add) {
   extern __shared__ __align__(16) float2 gsm[];
   pdl_wait();
   pdl_trigger();
