@@ -38,6 +38,7 @@ struct sr_ctx {
   bool fft2 = false;  // register-resident FFT passes (sr_fft.cu) for this size
   bool fftgen = false;  // mixed-radix passes (sr_fftgen.cu): a side is not a power of two
   srk::GenPlan plan_row{}, plan_col{};
+  bool gen_batched = false;  // member of a group: launch shapes for many images at once
   float2* gen_tab = nullptr;  // stage twiddles and roots of both plans
   sr_schedule sched{};  // schedule of the fft2 passes
   CUtensorMap tm_X{};   // X as a float32 matrix, boxes for the TMA column pass
@@ -183,6 +184,12 @@ bool gen_plan(int n, srk::GenPlan& P, std::vector<float2>& tab, std::vector<int>
     const int R = rad[s];
     P.radix[s] = R;
     P.ns[s] = Ns;
+    // ceil(2^32 / d) for the device's multiply-high division; 0 stands for d = 1
+    auto magic = [](int d) {
+      return d == 1 ? 0u : (unsigned)(((1ull << 32) + (unsigned)d - 1) / (unsigned)d);
+    };
+    P.mag_m[s] = magic(n / R);
+    P.mag_ns[s] = magic(Ns);
     P.twoff[s] = (int)tab.size();
     for (int t = 1; t < R; ++t)
       for (int k = 0; k < Ns; ++k) {
@@ -553,10 +560,10 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
   fa.twN = c->tw_n;
   fa.src = src;
   fa.X = c->X;
-  fa.T = c->fft2 ? sched_rows(c, c->sched) : c->fftgen ? srk::gen_rows_per_cta(c->L) : c->row_T;
+  fa.T = c->fft2 ? sched_rows(c, c->sched) : c->fftgen ? srk::gen_rows_per_cta(c->L, c->H, c->gen_batched) : c->row_T;
   fa.CW = c->row_CW;
   st = run_kernel(c, SR_KCLASS_ROWFFT, s, "k_rowfwd", [&] {
-    if (c->fftgen) return srk::launch_rowfft_gen(fa, c->plan_row, s);
+    if (c->fftgen) return srk::launch_rowfft_gen(fa, c->plan_row, c->gen_batched, s);
     return c->fft2 ? srk::launch_rowfft2(fa, c->sched.row_values_per_thread == 8 ? 3 : 4,
                                          c->sched.row_threads, s, false)
                    : srk::launch_rowfwd(fa, srk::kRowLOAD, c->row_NT, s);
@@ -570,7 +577,7 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
   ca.X = c->X;
   ca.err = c->err_dev;
   st = run_kernel(c, SR_KCLASS_COLSOLVE, s, "k_colsolve", [&] {
-    if (c->fftgen) return srk::launch_colsolve_gen(ca, c->plan_col, s);
+    if (c->fftgen) return srk::launch_colsolve_gen(ca, c->plan_col, c->gen_batched, s);
     if (!c->fft2) return srk::launch_colsolve(ca, s);
     if (c->sched.col_schedule == 3)
       return srk::launch_colsolve_tma(ca, c->tm_X, c->col_tma_grid, s, false);
@@ -584,10 +591,11 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
   ia.X = c->X;
   ia.psi_in = psi_in;
   ia.out = psi_out;
-  ia.T = c->fft2 ? sched_rows(c, c->sched) : c->fftgen ? srk::gen_rows_per_cta(c->L) : c->row_T;
+  ia.T = c->fft2 ? sched_rows(c, c->sched) : c->fftgen ? srk::gen_rows_per_cta(c->L, c->H, c->gen_batched) : c->row_T;
   const int imode = load_src ? srk::kInvSTORE : srk::kInvADD;
   return run_kernel(c, SR_KCLASS_ROWIFFT, s, "k_rowinv", [&] {
-    if (c->fftgen) return srk::launch_rowifft_gen(ia, c->plan_row, imode == srk::kInvADD, s);
+    if (c->fftgen)
+      return srk::launch_rowifft_gen(ia, c->plan_row, imode == srk::kInvADD, c->gen_batched, s);
     return c->fft2 ? srk::launch_rowifft2(ia, imode == srk::kInvADD,
                                           c->sched.row_values_per_thread == 8 ? 3 : 4,
                                           c->sched.row_threads, s, false)
@@ -1239,7 +1247,9 @@ cudaError_t group_build(sr_group* g, int p, std::string& why) {
     e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) break;
     const long long before = c->launches;
+    c->gen_batched = true;  // same arithmetic, launch shapes for many images at once
     const sr_status st = enqueue_iteration(c, c->cap_stream, p, false);
+    c->gen_batched = false;
     c->graph_kernels = (int)(c->launches - before);
     c->launches = before;  // capture enqueues nothing
     e = cudaStreamEndCapture(c->cap_stream, &child);

@@ -17,6 +17,8 @@
 namespace srk {
 namespace fftgen {
 
+constexpr int kGenThreads = 128;
+
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -130,13 +132,20 @@ __device__ __forceinline__ void dft_fixed(float2 (&x)[R], bool inv) {
 // Primes without a dedicated butterfly take the direct DFT y_q = sum_t x_t
 // root[(t q) mod R], root[e] = exp(-2 pi i e / R) (conjugated when inv),
 // each y_q written as soon as it is summed.
+// x / d for x < 2^20 from magic = ceil(2^32 / d) (host-computed): exact, since
+// x (magic d - 2^32) < 2^32 there.  d = 1 is passed as magic 0.
+__device__ __forceinline__ int divm(int x, unsigned magic) {
+  return magic ? (int)__umulhi((unsigned)x, magic) : x;
+}
+
 template <int R>
 __device__ __forceinline__ void stage_r(const float2* a, float2* b, int nseq, int n, int Ns,
-                                        const float2* tw, const float2* root, bool inv) {
+                                        unsigned mag_m, unsigned mag_ns, const float2* tw,
+                                        const float2* root, bool inv) {
   const int m = n / R;
   for (int idx = threadIdx.x; idx < nseq * m; idx += blockDim.x) {
-    const int q = idx / m, j = idx - q * m;
-    const int k = j % Ns;
+    const int q = divm(idx, mag_m), j = idx - q * m;
+    const int jn = divm(j, mag_ns), k = j - jn * Ns;
     const float2* in = a + (size_t)q * n;
     float2* out = b + (size_t)q * n;
     float2 v[R];
@@ -150,7 +159,7 @@ __device__ __forceinline__ void stage_r(const float2* a, float2* b, int nseq, in
         v[t] = cmul(v[t], w);
       }
     }
-    const int o = (j / Ns) * Ns * R + k;
+    const int o = jn * Ns * R + k;
     if constexpr (dedicated<R>()) {
       dft_fixed<R>(v, inv);
 #pragma unroll
@@ -186,7 +195,7 @@ __device__ float2* stockham(float2* a, float2* b, int nseq, const GenPlan& P, bo
     const float2* root = P.roots + P.rootoff[s];
     switch (P.radix[s]) {
 #define SR_RADIX(r) \
-  case r: stage_r<r>(a, b, nseq, n, Ns, tw, root, inv); break;
+  case r: stage_r<r>(a, b, nseq, n, Ns, P.mag_m[s], P.mag_ns[s], tw, root, inv); break;
       SR_RADIX(2) SR_RADIX(3) SR_RADIX(4) SR_RADIX(5) SR_RADIX(7) SR_RADIX(8) SR_RADIX(11)
       SR_RADIX(13) SR_RADIX(16) SR_RADIX(17) SR_RADIX(19) SR_RADIX(23) SR_RADIX(29) SR_RADIX(31)
 #undef SR_RADIX
@@ -327,12 +336,22 @@ __global__ void __launch_bounds__(256, 2) k_rowifft_gen(const RowInvArgs a, cons
 
 }  // namespace fftgen
 
-// sequences per CTA: the two buffers stay within kGenSmemFloat2 values, at
-// most 16 sequences so that small images still spread over many CTAs
-int gen_rows_per_cta(int n) {
+using fftgen::kGenThreads;
+
+// sequences per CTA for `count` sequences of length n: the two buffers stay
+// within kGenSmemFloat2 values and hold at most 16 sequences.  Alone, an image
+// spreads over a few hundred CTAs (about count / 256 sequences each); in a
+// batched group the other images fill the GPU, so the CTAs are filled up.
+int gen_rows_per_cta(int n, int count, bool batched) {
   const int fit = n >= kGenSmemFloat2 / 2 ? 1 : kGenSmemFloat2 / 2 / n;
-  return fit < 16 ? fit : 16;
+  int t = batched ? 16 : count / 256;
+  if (t < 1) t = 1;
+  if (t > 16) t = 16;
+  return t < fit ? t : fit;
 }
+
+// threads per CTA: 256 for the filled CTAs of a group, 128 alone
+static int gen_threads(bool batched) { return batched ? 256 : kGenThreads; }
 
 size_t gen_smem(int nseq, int n) { return 2 * (size_t)nseq * n * sizeof(float2); }
 
@@ -347,22 +366,26 @@ cudaError_t configure_fftgen() {
   return e;
 }
 
-cudaError_t launch_rowfft_gen(const RowFwdArgs& a, const GenPlan& P, cudaStream_t s) {
+cudaError_t launch_rowfft_gen(const RowFwdArgs& a, const GenPlan& P, bool batched,
+                              cudaStream_t s) {
   const int grid = (a.geo.M + a.T - 1) / a.T;
-  return launch_k(fftgen::k_rowfft_gen, dim3(grid), dim3(256), gen_smem(a.T, a.geo.L), s, a, P);
+  return launch_k(fftgen::k_rowfft_gen, dim3(grid), dim3(gen_threads(batched)),
+                  gen_smem(a.T, a.geo.L), s, a, P);
 }
 
-cudaError_t launch_colsolve_gen(const ColArgs& a, const GenPlan& P, cudaStream_t s) {
-  const int CB = gen_rows_per_cta(a.geo.M);
+cudaError_t launch_colsolve_gen(const ColArgs& a, const GenPlan& P, bool batched,
+                                cudaStream_t s) {
+  const int CB = gen_rows_per_cta(a.geo.M, a.geo.L, batched);
   const int grid = (a.geo.L + CB - 1) / CB;
-  return launch_k(fftgen::k_colsolve_gen, dim3(grid), dim3(256), gen_smem(CB, a.geo.M), s, a, P,
-                  CB);
+  return launch_k(fftgen::k_colsolve_gen, dim3(grid), dim3(gen_threads(batched)),
+                  gen_smem(CB, a.geo.M), s, a, P, CB);
 }
 
-cudaError_t launch_rowifft_gen(const RowInvArgs& a, const GenPlan& P, bool add, cudaStream_t s) {
+cudaError_t launch_rowifft_gen(const RowInvArgs& a, const GenPlan& P, bool add, bool batched,
+                               cudaStream_t s) {
   const int grid = (a.geo.M + a.T - 1) / a.T;
-  return launch_k(fftgen::k_rowifft_gen, dim3(grid), dim3(256), gen_smem(a.T, a.geo.L), s, a, P,
-                  add ? 1 : 0);
+  return launch_k(fftgen::k_rowifft_gen, dim3(grid), dim3(gen_threads(batched)),
+                  gen_smem(a.T, a.geo.L), s, a, P, add ? 1 : 0);
 }
 
 }  // namespace srk

@@ -107,6 +107,8 @@ struct GenPlan {
   int ns[kGenMaxStages];      // product of the earlier radices
   int twoff[kGenMaxStages];   // stage twiddles at tw + twoff[s] + (t-1) ns[s] + k
   int rootoff[kGenMaxStages]; // roots exp(-2 pi i e / R) at roots + rootoff[s] + e
+  unsigned mag_m[kGenMaxStages];   // ceil(2^32 / (n / radix)): division by magic multiply
+  unsigned mag_ns[kGenMaxStages];  // ceil(2^32 / ns)
   const float2* tw;
   const float2* roots;
 };
@@ -235,11 +237,13 @@ cudaError_t configure_kernels();   // raise dynamic shared-memory limits once
 bool fft2_supported(const Geo& geo);
 
 // Mixed-radix passes (sr_fftgen.cu) for sides that are not powers of two.
-int gen_rows_per_cta(int n);
+// batched: the launch shapes for a member of a group (fuller CTAs)
+int gen_rows_per_cta(int n, int count, bool batched);
 cudaError_t configure_fftgen();
-cudaError_t launch_rowfft_gen(const RowFwdArgs& a, const GenPlan& P, cudaStream_t s);
-cudaError_t launch_colsolve_gen(const ColArgs& a, const GenPlan& P, cudaStream_t s);
-cudaError_t launch_rowifft_gen(const RowInvArgs& a, const GenPlan& P, bool add, cudaStream_t s);
+cudaError_t launch_rowfft_gen(const RowFwdArgs& a, const GenPlan& P, bool batched, cudaStream_t s);
+cudaError_t launch_colsolve_gen(const ColArgs& a, const GenPlan& P, bool batched, cudaStream_t s);
+cudaError_t launch_rowifft_gen(const RowInvArgs& a, const GenPlan& P, bool add, bool batched,
+                               cudaStream_t s);
 size_t rowfft2_smem(int T, int L, int logE);
 int stage_twiddles(int L, int logE);  // entries of the stage-twiddle table
 cudaError_t launch_rowfft2(const RowFwdArgs& a, int logE, int nthreads, cudaStream_t s,
