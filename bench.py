@@ -249,8 +249,8 @@ def batched_sample(stream, n_images: int = 256, iters: int = 100) -> dict:
     """Many small images in one graph (sr_group_*) against the same images one
     after another.  Height and width drawn independently (seed 3) from the
     31 sides 64, 96, ..., 1024; sides that are not powers of two run the
-    mixed-radix FFT passes.  Each image is the six-ellipse scene of its size
-    (one scene per size pair), inset-rectangle start, R = d = 4."""
+    mixed-radix FFT passes.  Each image is a crop of one 1024^2 six-ellipse
+    scene, inset-rectangle start, R = d = 4."""
     import numpy as np
     import torch
 
@@ -258,15 +258,13 @@ def batched_sample(stream, n_images: int = 256, iters: int = 100) -> dict:
 
     rng = np.random.default_rng(3)
     sides = list(range(64, 1025, 32))
-    scenes, ctxs, P = {}, [], 0
+    # one 1024^2 six-ellipse scene, each image its top-left H x W crop
+    scene = synth.ellipse_scene(1000, H=1024, W=1024, scale=2.0).astype(np.float32)
+    ctxs, P = [], 0
     for k in range(n_images):
         H, W = int(rng.choice(sides)), int(rng.choice(sides))
-        if (H, W) not in scenes:
-            img = synth.ellipse_scene(1000 + len(scenes), H=H, W=W,
-                                      scale=max(min(H, W) / 512.0, 0.125))
-            scenes[(H, W)] = (torch.from_numpy(img.astype(np.float32)).cuda(),
-                              torch.from_numpy(synth.inset_rect_sdf(H, W).astype(np.float32)).cuda())
-        img_d, phi_d = scenes[(H, W)]
+        img_d = torch.from_numpy(np.ascontiguousarray(scene[:H, :W])).cuda()
+        phi_d = torch.from_numpy(synth.inset_rect_sdf(H, W).astype(np.float32)).cuda()
         c = sr.Context(H, W, sr.make_params(win_radius=4, d=4.0), stream)
         c.edge_function(img_d)
         c.set_phi(phi_d)
