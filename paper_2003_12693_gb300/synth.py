@@ -335,3 +335,33 @@ def random_state(H: int, W: int, seed: int, phi_scale: float = 3.0):
     b2 = 0.5 * rng.normal(size=(H, W))
     g = 1.0 / (1.0 + 4.0 * rng.uniform(0, 1, (H, W)) ** 2)
     return phi, w1, w2, b1, b2, g
+
+
+# ----------------------------------------------------------------------------
+# Warm-start network: seeded parameters and bf16-representable test values
+# ----------------------------------------------------------------------------
+def net_init(seed: int, layers) -> np.ndarray:
+    """Flat He-normal parameters of a stack of 3x3 convolutions.
+
+    ``layers`` lists (Cin, Cout); per layer the flat vector holds W in
+    (Cout, 3, 3, Cin) order, W ~ N(0, 2 / (9 Cin)), then Cout zero biases.
+    The last layer's weights are scaled by 0.1 so that the initial output is
+    small.
+    """
+    rng = np.random.default_rng(seed)
+    parts = []
+    for k, (ci, co) in enumerate(layers):
+        w = rng.normal(0.0, math.sqrt(2.0 / (9 * ci)), co * 9 * ci)
+        if k == len(layers) - 1:
+            w *= 0.1
+        parts += [w, np.zeros(co)]
+    return np.concatenate(parts)
+
+
+def bf16_exact(a) -> np.ndarray:
+    """Round to the nearest bfloat16 value (ties to even), returned as float64,
+    so that a test can hand both sides values that bf16 holds exactly."""
+    x = np.ascontiguousarray(a, dtype=np.float32)
+    u = x.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
+    return (u.astype(np.uint32)).view(np.float32).astype(np.float64)
