@@ -150,23 +150,25 @@ def loss(y, t):
     return 0.5 * np.mean((y - t) ** 2)
 
 
-def backward(params, cache, y, t):
-    """Gradients of loss(y, t) with respect to every (W, b), by the adjoints."""
-    (W1, _), (W2, _), (W3, _), (W4, _), (W5, _), (W6, _) = params
+def deltas(params, cache, y, t):
+    """Per layer, the pair (layer input, loss gradient at the layer's
+    pre-activation output) that its weight gradient contracts, by the
+    adjoints of the forward pass in reverse order."""
+    (_, _), (W2, _), (W3, _), (W4, _), (W5, _), (W6, _) = params
     c = cache
-    dy = ((y - t) / y.size)[..., None]
-    g6 = conv3x3_wgrad(c["u5"], dy)
-    da5 = up2_adjoint(conv3x3_adjoint(dy, W6, c["u5"].shape)) * (c["a5"] > 0)
-    g5 = conv3x3_wgrad(c["u4"], da5)
-    da4 = up2_adjoint(conv3x3_adjoint(da5, W5, c["u4"].shape)) * (c["a4"] > 0)
-    g4 = conv3x3_wgrad(c["a3"], da4)
-    da3 = conv3x3_adjoint(da4, W4, c["a3"].shape) * (c["a3"] > 0)
-    g3 = conv3x3_wgrad(c["p2"], da3)
-    da2 = avgpool2_adjoint(conv3x3_adjoint(da3, W3, c["p2"].shape)) * (c["a2"] > 0)
-    g2 = conv3x3_wgrad(c["p1"], da2)
-    da1 = avgpool2_adjoint(conv3x3_adjoint(da2, W2, c["p1"].shape)) * (c["a1"] > 0)
-    g1 = conv3x3_wgrad(c["x"], da1)
-    return [g1, g2, g3, g4, g5, g6]
+    d6 = ((y - t) / y.size)[..., None]
+    d5 = up2_adjoint(conv3x3_adjoint(d6, W6, c["u5"].shape)) * (c["a5"] > 0)
+    d4 = up2_adjoint(conv3x3_adjoint(d5, W5, c["u4"].shape)) * (c["a4"] > 0)
+    d3 = conv3x3_adjoint(d4, W4, c["a3"].shape) * (c["a3"] > 0)
+    d2 = avgpool2_adjoint(conv3x3_adjoint(d3, W3, c["p2"].shape)) * (c["a2"] > 0)
+    d1 = avgpool2_adjoint(conv3x3_adjoint(d2, W2, c["p1"].shape)) * (c["a1"] > 0)
+    return [(c["x"], d1), (c["p1"], d2), (c["p2"], d3), (c["a3"], d4), (c["u4"], d5),
+            (c["u5"], d6)]
+
+
+def backward(params, cache, y, t):
+    """Gradients [(dW, db)] of loss(y, t) with respect to every (W, b)."""
+    return [conv3x3_wgrad(x, d) for x, d in deltas(params, cache, y, t)]
 
 
 def loss_and_grad(theta, f, phi_star, clip, layers=LAYERS):

@@ -1,6 +1,6 @@
 """Build libsr.so (the sm_103a kernels and the C-ABI of include/sr.h) in-tree.
 
-Both translation units are compiled in parallel with nvcc for sm_103a only,
+The translation units are compiled in parallel with nvcc for sm_103a only,
 then linked into paper_2003_12693_gb300/libsr.so.  No PyTorch headers are
 involved: the library exposes plain C entry points.
 """
@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsr.so")
-SOURCES = ["sr_kernels.cu", "sr_fft.cu", "sr_fftgen.cu", "sr_api.cu", "sr_noalloc.cu"]
+SOURCES = ["sr_kernels.cu", "sr_fft.cu", "sr_fftgen.cu", "sr_api.cu", "sr_noalloc.cu", "sr_net.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 
@@ -29,7 +29,8 @@ def _nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "sr_internal.h"), os.path.join(INCLUDE, "sr.h")]
+    files += [os.path.join(CSRC, "sr_internal.h"), os.path.join(INCLUDE, "sr.h"),
+              os.path.join(INCLUDE, "sr_net.h")]
     return files
 
 

@@ -46,11 +46,17 @@ _lib = None
 _P = C.c_void_p
 
 
+HEADERS = [HEADER, os.path.join(os.path.dirname(_HERE), "include", "sr_net.h")]
+
+
 def declared_functions() -> list[str]:
-    """Names of the functions include/sr.h declares."""
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(sr_[a-z_0-9]+)\s*\(", text)))
+    """Names of the functions include/sr.h and include/sr_net.h declare."""
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        text = re.sub(r"#define[^\n]*", "", text)
+        names |= set(re.findall(r"\b(sr_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 def lib() -> C.CDLL:
