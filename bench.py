@@ -299,6 +299,67 @@ def batched_sample(stream, n_images: int = 256, iters: int = 100) -> dict:
                    f"about {P * 14 * 4 / 1e9:.1f} GB)"}
 
 
+def warm_start_net_sample(stream, H: int = 256, W: int = 256, B: int = 32,
+                          steps: int = 20) -> dict:
+    """The warm-start network (include/sr_net.h) at its configured size: one
+    training step (forward, loss, backward, Adam) and one forward pass on a
+    batch of B images, CUDA events on the stream.  Algorithmic work: the six
+    3x3 convolutions' 2 * pixels * Cout * 9 * Cin multiply-adds forward, twice
+    that backward (input and weight gradients), with the real channel counts
+    (the padded first and last layers' extra products are not counted)."""
+    import numpy as np
+    import torch
+
+    from paper_2003_12693_gb300 import sr_net, synth
+
+    net = sr_net.Net(H, W, max_batch=B, phi_clip=4.0, stream=stream)
+    layers = sr_net.layers()
+    net.set_params(torch.from_numpy(synth.net_init(1, layers).astype(np.float32)).cuda())
+    rng = np.random.default_rng(0)
+    f = torch.from_numpy(rng.uniform(0, 1, (B, H, W)).astype(np.float32)).cuda()
+    phi = torch.from_numpy(rng.normal(0, 3, (B, H, W)).astype(np.float32)).cuda()
+    div = [1, 2, 4, 4, 2, 1]    # resolution divisor of each layer's output
+    fwd = sum(2.0 * B * (H // d) * (W // d) * ci * co * 9 for (ci, co), d in zip(layers, div))
+    # the first layer needs no input gradient
+    bwd = 2 * fwd - 2.0 * B * H * W * layers[0][0] * layers[0][1] * 9
+    for _ in range(3):
+        net.train_step(f, phi, 1e-4)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    net.kernel_launches(reset=True)
+    e0.record(stream)
+    for _ in range(steps):
+        net.train_step(f, phi, 1e-4)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_train = e0.elapsed_time(e1) / steps / 1e3
+    launches = net.kernel_launches() / steps
+    e0.record(stream)
+    for _ in range(steps):
+        net.forward(f)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_fwd = e0.elapsed_time(e1) / steps / 1e3
+    net.close()
+    peak = None
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            peak = float(json.load(fh)["bf16_tflops"])
+    tr_tf = (fwd + bwd) / t_train / 1e12
+    fw_tf = fwd / t_fwd / 1e12
+    return {"images": B, "H": H, "W": W, "layers": layers, "dtype": "bf16 operands, fp32 accumulate",
+            "train_step_ms": t_train * 1e3, "forward_ms": t_fwd * 1e3,
+            "train_images_per_s": B / t_train, "forward_images_per_s": B / t_fwd,
+            "train_tflops": tr_tf, "forward_tflops": fw_tf,
+            "peak_bf16_tflops": peak,
+            "frac_train": None if peak is None else tr_tf / peak,
+            "frac_forward": None if peak is None else fw_tf / peak,
+            "kernel_launches_per_train_step": launches,
+            "how": "mma.sync m16n8k16 implicit-GEMM convolutions (cp.async, ldmatrix); "
+                   "peak = measured cuBLAS bf16 (burst)"}
+
+
 def run_gpu(args, wl, rank: int, world: int, local_rank: int):
     import numpy as np
     import torch
@@ -433,6 +494,7 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
     if rank != 0:
         return
     batched = None if args.no_batched else batched_sample(stream)
+    wsnet = None if args.no_net else warm_start_net_sample(stream)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         rate, iters, el = _oracle_rate(f.astype(np.float64), phi0.astype(np.float64),
@@ -455,6 +517,7 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched": batched,
+        "warm_start_net": wsnet,
         "gpu_launches": launches,
         "prewarm": {"seconds": args.prewarm_s, "steps": prewarm_steps},
         "clocks": clk.summary(),
@@ -474,6 +537,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the many-small-images sample (sr_group_*)")
+    ap.add_argument("--no-net", action="store_true",
+                    help="skip the warm-start network timing sample (sr_net_*)")
+    ap.add_argument("--net-only", action="store_true",
+                    help="print only the warm-start network sample (profiling runs)")
+    ap.add_argument("--net-steps", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--prewarm-s", type=float, default=1.0,
                     help="untimed back-to-back steps before the warm-up steps (clock ramp)")
@@ -488,6 +556,15 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, wl, rank, world)
+        return
+    if args.net_only:
+        import torch
+
+        from paper_2003_12693_gb300 import build
+        torch.cuda.set_device(local_rank)
+        build.build()
+        print(json.dumps(warm_start_net_sample(torch.cuda.current_stream(),
+                                               steps=args.net_steps)), flush=True)
         return
     if world > 1:
         import torch

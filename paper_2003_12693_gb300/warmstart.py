@@ -165,3 +165,95 @@ def train(net: "sr_net.Net", images: torch.Tensor, phi_star: torch.Tensor, steps
         a = 0.5 * (1.0 + np.cos(np.pi * s / max(1, steps - 1)))
         net.train_step(fb, pb, lr_final + (lr - lr_final) * a, loss[s:s + 1])
     return loss.cpu().tolist()
+
+
+# ----------------------------------------------------------------------------
+# Experiment: what the trained network gains over the rectangle start
+# ----------------------------------------------------------------------------
+def _scene(args):
+    from . import synth
+    seed, n, noise = args
+    return synth.ellipse_scene(seed, n, n, scale=n / 512.0, noise=noise).astype(np.float32)
+
+
+def experiment(n: int = 128, n_train: int = 2048, n_eval: int = 32, t_ref: int = 3000,
+               steps: int = 4000, batch: int = 32, lr: float = 2e-3, rho: float = 1e4,
+               sigma: float = 3.0, check: int = 100, procs: int = 16) -> dict:
+    """Generate n_train (image, phi after t_ref iterations) pairs of n x n
+    ellipse scenes with the plain solver from the inset rectangle, train the
+    network on them, then run n_eval held-out images (a) plain, one image per
+    context, from the rectangle and (b) batched in one group from the
+    network's phi0, each until its mask settles (at most 0.2 % of the pixels
+    change over ``check`` iterations; at most 3 t_ref iterations)."""
+    import multiprocessing as mp
+
+    from scipy import ndimage
+
+    from . import synth
+    with mp.get_context("spawn").Pool(procs) as pool:
+        tr = np.stack(pool.map(_scene, [(20000 + k, n, 0.1) for k in range(n_train)], 16))
+        ev = np.stack(pool.map(_scene, [(90000 + k, n, 0.1) for k in range(n_eval)], 2))
+    torch.cuda.set_device(torch.cuda.current_device())
+    prm = dict(synth.WORKLOADS["ellipses_512"].params())
+    prm.update(rho=rho, sigma=sigma)
+    p = sr.make_params(**prm)
+    rect = torch.from_numpy(synth.inset_rect_sdf(n, n).astype(np.float32)).cuda()
+    trd, evd = torch.from_numpy(tr).cuda(), torch.from_numpy(ev).cuda()
+    t0 = time.perf_counter()
+    phis = generate_pairs(trd, rect, p, t_ref)
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    net = sr_net.Net(n, n, max_batch=max(batch, n_eval), phi_clip=4.0)
+    layers = sr_net.layers()
+    net.set_params(torch.from_numpy(synth.net_init(7, layers).astype(np.float32)).cuda())
+    t0 = time.perf_counter()
+    hist = train(net, trd, phis, steps, batch, lr)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    ref_phi = generate_pairs(evd, rect, p, t_ref)
+    lossd = torch.zeros(1, dtype=torch.float64, device="cuda")
+    net.gradients(evd, ref_phi, lossd)
+    tgt = torch.clamp(ref_phi, -4.0, 4.0) / 4.0
+    rect_loss = 0.5 * torch.mean((torch.clamp(rect, -4.0, 4.0) / 4.0 - tgt) ** 2).item()
+    thr = int(0.002 * n * n)
+    mx = 3 * t_ref
+    plain = solve_plain(evd, rect, p, check=check, thr=thr, max_iters=mx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    phi0 = net.forward(evd)
+    lb = solve_batched(evd, phi0, p, check=check, thr=thr, max_iters=mx)
+    torch.cuda.synchronize()
+    t_lb = time.perf_counter() - t0
+    rb = solve_batched(evd, rect, p, check=check, thr=thr, max_iters=mx)
+    ref_m = [(ref_phi[k] < 0).to(torch.uint8) for k in range(n_eval)]
+    rect_m = (rect < 0).to(torch.uint8)
+    comps = lambda m: ndimage.label(m.cpu().numpy() > 0)[1]  # noqa: E731
+    return dict(
+        size=n, train_pairs=n_train, t_ref=t_ref, train_steps=steps, batch=batch,
+        pairs_s=t_pairs, train_s=t_train, loss_first=hist[0], loss_last=float(np.mean(hist[-50:])),
+        heldout_loss=lossd.item(), rect_loss=rect_loss,
+        start_iou_net=float(np.mean([_iou((phi0[k] < 0).to(torch.uint8), ref_m[k])
+                                     for k in range(n_eval)])),
+        start_iou_rect=float(np.mean([_iou(rect_m, ref_m[k]) for k in range(n_eval)])),
+        settle_thr_px=thr, check=check, max_iters=mx,
+        plain_iters=float(np.mean(plain.iters)), plain_settled=int(sum(plain.settled)),
+        plain_s_per_image=plain.seconds / n_eval,
+        learned_batched_iters=float(np.mean(lb.iters)), learned_batched_settled=int(sum(lb.settled)),
+        learned_batched_s_per_image=t_lb / n_eval,
+        rect_batched_iters=float(np.mean(rb.iters)), rect_batched_settled=int(sum(rb.settled)),
+        rect_batched_s_per_image=rb.seconds / n_eval,
+        final_iou_learned_vs_plain=float(np.mean([_iou(a, b) for a, b in
+                                                  zip(plain.masks, lb.masks)])),
+        topology_agree=int(sum(comps(a) == comps(b) for a, b in zip(plain.masks, lb.masks))))
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="learned warm start versus the rectangle start")
+    ap.add_argument("--size", type=int, default=128)
+    ap.add_argument("--train", type=int, default=2048)
+    ap.add_argument("--t-ref", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=4000)
+    a = ap.parse_args()
+    print(json.dumps(experiment(n=a.size, n_train=a.train, t_ref=a.t_ref, steps=a.steps)))
