@@ -94,6 +94,7 @@ struct ConvArgs {
   int B, H, W, Cin, Cout;
   int mode;
   float out_scale;
+  int taps;           // 9: 3x3 window; 1: a 1x1 product (the input holds the taps)
 };
 
 constexpr int kConvBM = 128;   // pixels per CTA
@@ -140,12 +141,12 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a) {
   }
   const int av = tid % VPR;
   const int cchunks = a.Cin / KC;
-  const int NK = 9 * cchunks;
+  const int NK = a.taps * cchunks;
 
   auto load = [&](int kc, int st) {
     const int tap = kc / cchunks;
     const int c0 = (kc - tap * cchunks) * KC;
-    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const int dy = a.taps == 9 ? tap / 3 - 1 : 0, dx = a.taps == 9 ? tap % 3 - 1 : 0;
 #pragma unroll
     for (int i = 0; i < AV; ++i) {
       const int r = tid / VPR + i * RSTEP;
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a) {
 #pragma unroll
     for (int idx = tid; idx < BVEC; idx += NT) {
       const int n = idx / VPR, v = idx % VPR;
-      const bf16* src = a.w + ((long long)(n0 + n) * 9 + tap) * a.Cin + c0 + v * 8;
+      const bf16* src = a.w + ((long long)(n0 + n) * a.taps + tap) * a.Cin + c0 + v * 8;
       cp_async16(&Bs[st][n * LDS + v * 8], src, 16);
     }
   };
@@ -244,6 +245,7 @@ struct WgradArgs {
   float* dw;       // [cout_real, 9, cin_real], accumulated
   int B, H, W, Cin, Cout, cin_real, cout_real;
   long long pix_per_cta;  // multiple of kWgKP
+  int taps;               // 9, or 1 for a 1x1 product
 };
 
 constexpr int kWgKP = 64;        // pixels per pipeline stage
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad(WgradArgs a) {
   const int cib = by % nci;
   const int tap = by / nci;
   const int co0 = cob * BCO, ci0 = cib * BCI;
-  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+  const int dy = a.taps == 9 ? tap / 3 - 1 : 0, dx = a.taps == 9 ? tap % 3 - 1 : 0;
   const long long HW = (long long)a.H * a.W;
   const long long Mtot = HW * a.B;
   const long long pb = (long long)blockIdx.x * a.pix_per_cta;
@@ -401,25 +403,41 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad(WgradArgs a) {
         const int co = co0 + wm * TMo + i * 16 + (lane >> 2) + (e >> 1) * 8;
         const int ci = ci0 + wn * TNi + j * 8 + (lane & 3) * 2 + (e & 1);
         if (co < a.cout_real && ci < a.cin_real)
-          atomicAdd(a.dw + ((long long)co * 9 + tap) * a.cin_real + ci, acc[i][j][e]);
+          atomicAdd(a.dw + ((long long)co * a.taps + tap) * a.cin_real + ci, acc[i][j][e]);
       }
 }
 
-// db[c] += sum_p dy[p, c] for c < c_real (C divides 256)
+// db[c] += sum_p dy[p, c] for c < c_real; 8 channels (16 bytes) per thread,
+// C / 8 threads per pixel row (C a multiple of 8 dividing 256 * 8)
 __global__ void __launch_bounds__(256) k_bias_grad(const bf16* __restrict__ dy, long long Mtot,
                                                    int C, int c_real, long long pix_per_cta,
                                                    float* __restrict__ db) {
-  __shared__ float red[256];
-  const int c = threadIdx.x % C, row = threadIdx.x / C, rows = 256 / C;
+  __shared__ float red[256][9];
+  const int CV = C / 8;
+  const int v = threadIdx.x % CV, row = threadIdx.x / CV, rows = 256 / CV;
   const long long pb = (long long)blockIdx.x * pix_per_cta;
   const long long pe = min(Mtot, pb + pix_per_cta);
-  float s = 0.f;
-  for (long long p = pb + row; p < pe; p += rows) s += __bfloat162float(dy[p * C + c]);
-  red[threadIdx.x] = s;
+  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (row < rows) {
+    for (long long p = pb + row; p < pe; p += rows) {
+      const uint4 u = *reinterpret_cast<const uint4*>(dy + p * C + v * 8);
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 f = __bfloat1622float2(h[k]);
+        s[2 * k] += f.x;
+        s[2 * k + 1] += f.y;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) red[threadIdx.x][k] = s[k];
   __syncthreads();
-  if (row == 0) {
-    for (int k = 1; k < rows; ++k) s += red[k * C + c];
-    if (c < c_real) atomicAdd(db + c, s);
+  if (threadIdx.x < C) {
+    const int c = threadIdx.x, cv = c / 8, ck = c % 8;
+    float t = 0.f;
+    for (int r = 0; r < rows; ++r) t += red[r * CV + cv][ck];
+    if (c < c_real) atomicAdd(db + c, t);
   }
 }
 
@@ -537,47 +555,196 @@ __global__ void k_up2_adj_mask(const bf16* __restrict__ du, const bf16* __restri
   }
 }
 
-// x0 [P, 16] bf16: channel 0 = f, channels 1..15 = 0
-__global__ void k_pack_input(const float* __restrict__ f, bf16* __restrict__ x0, long long P) {
+// The first layer has one input channel, so its 3x3 window is packed into
+// the channels instead: x0[p, t] = f[p + s(t)] for the nine taps t (zero
+// outside the image), channels 9..15 zero, and the layer becomes a 1x1
+// product with K = 16 instead of a 3x3 one with K = 9 x 16.
+__global__ void k_pack_input(const float* __restrict__ f, bf16* __restrict__ x0, int B, int H,
+                             int W) {
+  const long long P = (long long)B * H * W;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
        p += (long long)gridDim.x * blockDim.x) {
-    uint4 u0 = make_uint4(0, 0, 0, 0);
-    const bf16 v = __float2bfloat16_rn(f[p]);
-    u0.x = (unsigned)*reinterpret_cast<const unsigned short*>(&v);
+    const long long HW = (long long)H * W;
+    const int rem = (int)(p % HW);
+    const int y = rem / W, x = rem % W;
+    uint4 u[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+    unsigned short* h = reinterpret_cast<unsigned short*>(u);
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int ys = y + t / 3 - 1, xs = x + t % 3 - 1;
+      const float v = (ys >= 0 && ys < H && xs >= 0 && xs < W) ? f[p + (ys - y) * W + (xs - x)] : 0.f;
+      const bf16 b = __float2bfloat16_rn(v);
+      h[t] = *reinterpret_cast<const unsigned short*>(&b);
+    }
     uint4* d = reinterpret_cast<uint4*>(x0 + p * 16);
-    d[0] = u0;
-    d[1] = make_uint4(0, 0, 0, 0);
+    d[0] = u[0];
+    d[1] = u[1];
   }
 }
 
-// t = clip(phi*, -c, c) / c, r = y - t; dout[p, 0] = r / n (channels 1..15 = 0);
-// loss += sum r^2 / (2 n) in fp64
+// t = clip(phi*, -c, c) / c, r = y - t; dout[p] = r / n (fp32);
+// loss += sum r^2 / (2 n) in fp64; db_last += sum r / n (the last layer's bias)
 __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ y,
                                               const float* __restrict__ phi, long long n,
-                                              float clip, bf16* __restrict__ dout,
-                                              double* __restrict__ loss) {
-  __shared__ double red[256];
-  double s = 0.0;
+                                              float clip, float* __restrict__ dout,
+                                              double* __restrict__ loss,
+                                              float* __restrict__ db_last) {
+  __shared__ double red[2][256];
+  double s2 = 0.0, s1 = 0.0;
   const float inv_n = (float)(1.0 / (double)n);
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
     const float t = fminf(fmaxf(phi[p], -clip), clip) / clip;
     const float r = y[p] - t;
-    s += (double)r * (double)r;
-    uint4 u0 = make_uint4(0, 0, 0, 0);
-    const bf16 v = __float2bfloat16_rn(r * inv_n);
-    u0.x = (unsigned)*reinterpret_cast<const unsigned short*>(&v);
-    uint4* d = reinterpret_cast<uint4*>(dout + p * 16);
-    d[0] = u0;
-    d[1] = make_uint4(0, 0, 0, 0);
+    s2 += (double)r * (double)r;
+    const float d = r * inv_n;
+    s1 += (double)d;
+    dout[p] = d;
   }
-  red[threadIdx.x] = s;
+  red[0][threadIdx.x] = s2;
+  red[1][threadIdx.x] = s1;
   __syncthreads();
   for (int k = 128; k > 0; k >>= 1) {
-    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    if (threadIdx.x < k) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + k];
+      red[1][threadIdx.x] += red[1][threadIdx.x + k];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0 && loss != nullptr) atomicAdd(loss, 0.5 * red[0] / (double)n);
+  if (threadIdx.x == 0) {
+    if (loss != nullptr) atomicAdd(loss, 0.5 * red[0][0] / (double)n);
+    atomicAdd(db_last, (float)red[1][0]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The last layer (32 -> 1 channel, on the 2x upsampled a5) by direct kernels:
+// a single output channel leaves nothing for a tensor-core tile to share, and
+// the upsampling is folded into the indexing (u5[y, x] = a5[y / 2, x / 2]).
+// w6 is the layer's float weights [9][32] (tap-major), read from the
+// parameter vector.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load32(const bf16* p, float* v) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const V8 r = load8(p + q * 8);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[q * 8 + k] = r.v[k];
+  }
+}
+
+// y[p] = scale * (b6 + sum_{tap, c} u5[p + s(tap), c] w6[tap, c])
+__global__ void __launch_bounds__(256) k_out_fwd(const bf16* __restrict__ a5,
+                                                 const float* __restrict__ w6,
+                                                 const float* __restrict__ b6,
+                                                 float* __restrict__ y, int B, int H, int W,
+                                                 float scale) {
+  __shared__ float ws[288];
+  for (int i = threadIdx.x; i < 288; i += blockDim.x) ws[i] = w6[i];
+  __syncthreads();
+  const int h = H / 2, w = W / 2;
+  const long long P = (long long)B * H * W;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
+       p += (long long)gridDim.x * blockDim.x) {
+    const long long HW = (long long)H * W;
+    const long long b = p / HW;
+    const int rem = (int)(p - b * HW);
+    const int yy = rem / W, xx = rem % W;
+    float acc = 0.f;
+    for (int t = 0; t < 9; ++t) {
+      const int ys = yy + t / 3 - 1, xs = xx + t % 3 - 1;
+      if (ys < 0 || ys >= H || xs < 0 || xs >= W) continue;
+      float v[32];
+      load32(a5 + ((b * h + ys / 2) * w + xs / 2) * 32, v);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) acc = fmaf(v[c], ws[t * 32 + c], acc);
+    }
+    y[p] = scale * (acc + b6[0]);
+  }
+}
+
+// dz5[q, c] = (a5[q, c] > 0) * sum over the four copies p of q in u5 of
+// sum_tap dout[p - s(tap)] w6[tap, c]: the last layer's input gradient, the
+// upsampling's adjoint and a5's ReLU mask in one pass over half-resolution q
+__global__ void __launch_bounds__(256) k_out_dgrad(const float* __restrict__ dout,
+                                                   const float* __restrict__ w6,
+                                                   const bf16* __restrict__ a5,
+                                                   bf16* __restrict__ dz5, int B, int H, int W) {
+  __shared__ float ws[288];
+  for (int i = threadIdx.x; i < 288; i += blockDim.x) ws[i] = w6[i];
+  __syncthreads();
+  const int h = H / 2, w = W / 2;
+  const long long Q = (long long)B * h * w;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Q;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long hw = (long long)h * w;
+    const long long b = q / hw;
+    const int rem = (int)(q - b * hw);
+    const int qy = rem / w, qx = rem % w;
+    // the 4 x 4 block of dout around the four copies, rows 2qy-1 .. 2qy+2
+    float D[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int yy = 2 * qy - 1 + r, xx = 2 * qx - 1 + c;
+        D[r][c] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? dout[(b * H + yy) * W + xx] : 0.f;
+      }
+    // E[tap] = sum over the copies (i, j) of dout[(2qy + i, 2qx + j) - s(tap)]
+    float E[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int dy = t / 3 - 1, dx = t % 3 - 1;
+      E[t] = (D[1 - dy][1 - dx] + D[1 - dy][2 - dx]) + (D[2 - dy][1 - dx] + D[2 - dy][2 - dx]);
+    }
+    float m[32];
+    load32(a5 + q * 32, m);
+    V8 out[4];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      float acc = 0.f;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) acc = fmaf(E[t], ws[t * 32 + c], acc);
+      out[c / 8].v[c % 8] = m[c] > 0.f ? acc : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) store8(dz5 + q * 32 + k * 8, out[k]);
+  }
+}
+
+// dw6[tap, c] += sum_p dout[p] u5[p + s(tap), c]; one warp per tap, a slab of
+// pixels per CTA, lane l takes pixels l, l + 32, ...
+__global__ void __launch_bounds__(288) k_out_wgrad(const float* __restrict__ dout,
+                                                   const bf16* __restrict__ a5,
+                                                   float* __restrict__ dw6, int B, int H, int W,
+                                                   long long pix_per_cta) {
+  __shared__ float red[9][32][33];
+  const int t = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int dy = t / 3 - 1, dx = t % 3 - 1;
+  const int h = H / 2, w = W / 2;
+  const long long HW = (long long)H * W, P = HW * B;
+  const long long pb = (long long)blockIdx.x * pix_per_cta;
+  const long long pe = min(P, pb + pix_per_cta);
+  float acc[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+  for (long long p = pb + lane; p < pe; p += 32) {
+    const long long b = p / HW;
+    const int rem = (int)(p - b * HW);
+    const int ys = rem / W + dy, xs = rem % W + dx;
+    if (ys < 0 || ys >= H || xs < 0 || xs >= W) continue;
+    const float d = dout[p];
+    float v[32];
+    load32(a5 + ((b * h + ys / 2) * w + xs / 2) * 32, v);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = fmaf(d, v[c], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c) red[t][lane][c] = acc[c];
+  __syncthreads();
+  float s = 0.f;
+  for (int l = 0; l < 32; ++l) s += red[t][l][lane];
+  atomicAdd(dw6 + t * 32 + lane, s);
 }
 
 // Per-layer weight repacking: forward [CoutP, 9, CinP] and flipped
@@ -586,7 +753,8 @@ struct PackLayer {
   int cin, cout, cinp, coutp;
   long long off;     // offset of W in the flat parameter vector
   bf16* wf;
-  bf16* wb;
+  bf16* wb;          // null: no input-gradient copy
+  int taps_packed;   // 1: one input channel, wf [coutp][1][cinp] holds the 9 taps
 };
 struct PackArgs {
   PackLayer l[SR_NET_LAYERS];
@@ -595,6 +763,16 @@ struct PackArgs {
 
 __global__ void k_pack_weights(PackArgs a) {
   const PackLayer L = a.l[blockIdx.y];
+  if (L.wf == nullptr) return;
+  if (L.taps_packed) {
+    const int n = L.coutp * L.cinp;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+      const int t = idx % L.cinp, o = idx / L.cinp;
+      const float v = (o < L.cout && t < 9) ? a.theta[L.off + (long long)o * 9 + t] : 0.f;
+      L.wf[idx] = __float2bfloat16_rn(v);
+    }
+    return;
+  }
   const int n = L.coutp * 9 * L.cinp;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     const int c = idx % L.cinp;
@@ -604,7 +782,7 @@ __global__ void k_pack_weights(PackArgs a) {
         (o < L.cout && c < L.cin) ? a.theta[L.off + ((long long)o * 9 + tap) * L.cin + c] : 0.f;
     const bf16 b = __float2bfloat16_rn(v);
     L.wf[idx] = b;
-    L.wb[((long long)c * 9 + (8 - tap)) * L.coutp + o] = b;
+    if (L.wb) L.wb[((long long)c * 9 + (8 - tap)) * L.coutp + o] = b;
   }
 }
 
@@ -691,7 +869,7 @@ cudaError_t wgrad_go(const WgradArgs& a0, cudaStream_t s) {
     attr = true;
   }
   const long long M = (long long)a.B * a.H * a.W;
-  const int tiles = 9 * (a.Cout / BCO) * (a.Cin / BCI);
+  const int tiles = a.taps * (a.Cout / BCO) * (a.Cin / BCI);
   // about two CTAs per SM in total, slabs a multiple of the stage size
   long long slabs = std::max(1LL, (long long)(2 * num_sms() + tiles - 1) / tiles);
   long long per = (M + slabs - 1) / slabs;
@@ -749,13 +927,16 @@ struct sr_net {
   float *theta, *grad, *m, *v;
   long long woff[SR_NET_LAYERS], boff[SR_NET_LAYERS];
   int cinp[SR_NET_LAYERS], coutp[SR_NET_LAYERS];
+  // bf16 weights of the tensor-core layers: wf forward [coutp][taps][cinp],
+  // wb input gradient [cinp][9][coutp]; layer 1 has no wb (no input gradient
+  // is needed) and a tap-packed wf; layer 6 runs on the float weights
   bf16 *wf[SR_NET_LAYERS], *wb[SR_NET_LAYERS];
   bool packed;
   long long step;
   // activations (NHWC bf16) and gradients
-  bf16 *x0, *a1, *p1, *a2, *p2, *a3, *a4, *u4, *a5, *u5;
-  bf16 *dout, *du5, *dz5, *du4, *dz4, *dz3, *dp2, *dz2, *dp1, *dz1;
-  float* y;
+  bf16 *x0, *a1, *p1, *a2, *p2, *a3, *a4, *u4, *a5;
+  bf16 *dz5, *du4, *dz4, *dz3, *dp2, *dz2, *dp1, *dz1;
+  float *y, *dout;
   long long launches;
   std::string err;
   std::vector<void*> allocs;
@@ -774,6 +955,12 @@ static sr_status net_fail(sr_net* n, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return net_fail(n, e_, what); \
   } while (0)
 
+#define NET_TRY(x)                 \
+  do {                             \
+    sr_status s_ = (x);            \
+    if (s_ != SR_OK) return s_;    \
+  } while (0)
+
 static sr_status net_alloc(sr_net* n, void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
@@ -787,16 +974,18 @@ static sr_status net_alloc(sr_net* n, void** p, size_t bytes) {
 
 static sr_status net_conv(sr_net* n, const bf16* x, int B, int H, int W, int cin, const bf16* w,
                           const float* bias, int cout, int mode, const bf16* ref, void* y,
-                          float out_scale) {
-  ConvArgs a{x, w, bias, ref, y, B, H, W, cin, cout, mode, out_scale};
+                          int taps = 9) {
+  ConvArgs a{x, w, bias, ref, y, B, H, W, cin, cout, mode, 1.f, taps};
   NET_CK(n, launch_conv(a, n->stream), "conv3x3");
   ++n->launches;
   return SR_OK;
 }
 
+// weight and bias gradients of tensor-core layer k (0-based)
 static sr_status net_wgrad(sr_net* n, int k, const bf16* dy, const bf16* x, int B, int H, int W) {
-  WgradArgs a{dy, x, n->grad + n->woff[k], B, H, W, n->cinp[k], n->coutp[k], kLayerCin[k],
-              kLayerCout[k], 0};
+  const bool packed = k == 0;   // tap-packed first layer: a 1x1 product over 9 "channels"
+  WgradArgs a{dy, x, n->grad + n->woff[k], B, H, W, n->cinp[k], n->coutp[k],
+              packed ? 9 : kLayerCin[k], kLayerCout[k], 0, packed ? 1 : 9};
   NET_CK(n, launch_wgrad(a, n->stream), "conv3x3 weight gradient");
   NET_CK(n, launch_bias_grad(dy, (long long)B * H * W, n->coutp[k], kLayerCout[k],
                              n->grad + n->boff[k], n->stream),
@@ -811,7 +1000,7 @@ static sr_status net_pack(sr_net* n) {
   int maxn = 0;
   for (int k = 0; k < SR_NET_LAYERS; ++k) {
     a.l[k] = PackLayer{kLayerCin[k], kLayerCout[k], n->cinp[k], n->coutp[k], n->woff[k],
-                       n->wf[k], n->wb[k]};
+                       n->wf[k], n->wb[k], k == 0 ? 1 : 0};
     maxn = std::max(maxn, n->coutp[k] * 9 * n->cinp[k]);
   }
   a.theta = n->theta;
@@ -822,38 +1011,31 @@ static sr_status net_pack(sr_net* n) {
   return SR_OK;
 }
 
-#define NET_TRY(x)                 \
-  do {                             \
-    sr_status s_ = (x);            \
-    if (s_ != SR_OK) return s_;    \
-  } while (0)
-
 static sr_status net_forward(sr_net* n, const float* f, int B, float out_scale, float* yout) {
   const int H = n->H, W = n->W, H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
   cudaStream_t s = n->stream;
   NET_TRY(net_pack(n));
   const long long P0 = (long long)B * H * W;
-  k_pack_input<<<ew_grid(P0), 256, 0, s>>>(f, n->x0, P0);
+  k_pack_input<<<ew_grid(P0), 256, 0, s>>>(f, n->x0, B, H, W);
   NET_CK(n, cudaGetLastError(), "pack input");
   ++n->launches;
   const float* th = n->theta;
   NET_TRY(net_conv(n, n->x0, B, H, W, 16, n->wf[0], th + n->boff[0], 32, SR_CONV_RELU, nullptr,
-                   n->a1, 1.f));
+                   n->a1, 1));
   k_pool2<<<ew_grid((long long)B * H2 * W2 * 4), 256, 0, s>>>(n->a1, n->p1, B, H, W, 32);
   NET_TRY(net_conv(n, n->p1, B, H2, W2, 32, n->wf[1], th + n->boff[1], 64, SR_CONV_RELU, nullptr,
-                   n->a2, 1.f));
+                   n->a2));
   k_pool2<<<ew_grid((long long)B * H4 * W4 * 8), 256, 0, s>>>(n->a2, n->p2, B, H2, W2, 64);
   NET_TRY(net_conv(n, n->p2, B, H4, W4, 64, n->wf[2], th + n->boff[2], 128, SR_CONV_RELU,
-                   nullptr, n->a3, 1.f));
+                   nullptr, n->a3));
   NET_TRY(net_conv(n, n->a3, B, H4, W4, 128, n->wf[3], th + n->boff[3], 64, SR_CONV_RELU,
-                   nullptr, n->a4, 1.f));
+                   nullptr, n->a4));
   k_up2<<<ew_grid((long long)B * H2 * W2 * 8), 256, 0, s>>>(n->a4, n->u4, B, H4, W4, 64);
   NET_TRY(net_conv(n, n->u4, B, H2, W2, 64, n->wf[4], th + n->boff[4], 32, SR_CONV_RELU, nullptr,
-                   n->a5, 1.f));
-  k_up2<<<ew_grid((long long)B * H * W * 4), 256, 0, s>>>(n->a5, n->u5, B, H2, W2, 32);
-  NET_TRY(net_conv(n, n->u5, B, H, W, 32, n->wf[5], th + n->boff[5], 16, SR_CONV_OUT1, nullptr,
-                   yout, out_scale));
-  NET_CK(n, cudaGetLastError(), "pool / upsample");
+                   n->a5));
+  k_out_fwd<<<ew_grid(P0), 256, 0, s>>>(n->a5, th + n->woff[5], th + n->boff[5], yout, B, H, W,
+                                         out_scale);
+  NET_CK(n, cudaGetLastError(), "pool / upsample / output layer");
   n->launches += 4;
   return SR_OK;
 }
@@ -864,41 +1046,48 @@ static sr_status net_backward(sr_net* n, const float* phi_star, int B, double* l
   const long long P0 = (long long)B * H * W;
   NET_CK(n, cudaMemsetAsync(n->grad, 0, sizeof(float) * n->P, s), "zero gradient");
   if (loss) NET_CK(n, cudaMemsetAsync(loss, 0, sizeof(double), s), "zero loss");
-  k_loss<<<ew_grid(P0), 256, 0, s>>>(n->y, phi_star, P0, n->clip, n->dout, loss);
+  k_loss<<<ew_grid(P0), 256, 0, s>>>(n->y, phi_star, P0, n->clip, n->dout, loss,
+                                     n->grad + n->boff[5]);
   NET_CK(n, cudaGetLastError(), "loss");
-  ++n->launches;
-  // layer 6: y = conv(u5)
-  NET_TRY(net_wgrad(n, 5, n->dout, n->u5, B, H, W));
-  NET_TRY(net_conv(n, n->dout, B, H, W, 16, n->wb[5], nullptr, 32, SR_CONV_PLAIN, nullptr,
-                   n->du5, 1.f));
-  k_up2_adj_mask<<<ew_grid((long long)B * H2 * W2 * 4), 256, 0, s>>>(n->du5, n->a5, n->dz5, B,
-                                                                     H2, W2, 32);
+  // layer 6: y = conv(up2(a5)); weight gradient, then input gradient through
+  // the upsampling and a5's ReLU
+  {
+    const long long blocks = std::min<long long>(2 * num_sms(), std::max(1LL, P0 / 1024));
+    const long long per = (P0 + blocks - 1) / blocks;
+    k_out_wgrad<<<(unsigned)((P0 + per - 1) / per), 288, 0, s>>>(n->dout, n->a5,
+                                                                 n->grad + n->woff[5], B, H, W,
+                                                                 per);
+  }
+  k_out_dgrad<<<ew_grid((long long)B * H2 * W2), 256, 0, s>>>(n->dout, n->theta + n->woff[5],
+                                                              n->a5, n->dz5, B, H, W);
+  NET_CK(n, cudaGetLastError(), "output layer gradients");
+  n->launches += 3;
   // layer 5: a5 = relu(conv(u4))
   NET_TRY(net_wgrad(n, 4, n->dz5, n->u4, B, H2, W2));
   NET_TRY(net_conv(n, n->dz5, B, H2, W2, 32, n->wb[4], nullptr, 64, SR_CONV_PLAIN, nullptr,
-                   n->du4, 1.f));
+                   n->du4));
   k_up2_adj_mask<<<ew_grid((long long)B * H4 * W4 * 8), 256, 0, s>>>(n->du4, n->a4, n->dz4, B,
                                                                      H4, W4, 64);
   // layer 4: a4 = relu(conv(a3)); its input gradient carries a3's ReLU mask
   NET_TRY(net_wgrad(n, 3, n->dz4, n->a3, B, H4, W4));
-  NET_TRY(net_conv(n, n->dz4, B, H4, W4, 64, n->wb[3], nullptr, 128, SR_CONV_MASK, n->a3, n->dz3,
-                   1.f));
+  NET_TRY(net_conv(n, n->dz4, B, H4, W4, 64, n->wb[3], nullptr, 128, SR_CONV_MASK, n->a3,
+                   n->dz3));
   // layer 3: a3 = relu(conv(p2))
   NET_TRY(net_wgrad(n, 2, n->dz3, n->p2, B, H4, W4));
   NET_TRY(net_conv(n, n->dz3, B, H4, W4, 128, n->wb[2], nullptr, 64, SR_CONV_PLAIN, nullptr,
-                   n->dp2, 1.f));
+                   n->dp2));
   k_pool2_adj_mask<<<ew_grid((long long)B * H2 * W2 * 8), 256, 0, s>>>(n->dp2, n->a2, n->dz2, B,
                                                                        H2, W2, 64);
   // layer 2: a2 = relu(conv(p1))
   NET_TRY(net_wgrad(n, 1, n->dz2, n->p1, B, H2, W2));
   NET_TRY(net_conv(n, n->dz2, B, H2, W2, 64, n->wb[1], nullptr, 32, SR_CONV_PLAIN, nullptr,
-                   n->dp1, 1.f));
+                   n->dp1));
   k_pool2_adj_mask<<<ew_grid((long long)B * H * W * 4), 256, 0, s>>>(n->dp1, n->a1, n->dz1, B, H,
                                                                      W, 32);
-  // layer 1: a1 = relu(conv(x0))
+  // layer 1: a1 = relu(x0 . w1), tap-packed
   NET_TRY(net_wgrad(n, 0, n->dz1, n->x0, B, H, W));
   NET_CK(n, cudaGetLastError(), "adjoint kernels");
-  n->launches += 4;
+  n->launches += 3;
   return SR_OK;
 }
 
@@ -961,10 +1150,10 @@ sr_status sr_net_create(int H, int W, int max_batch, float phi_clip, void* cuda_
   A((void**)&n->grad, sizeof(float) * n->P);
   A((void**)&n->m, sizeof(float) * n->P);
   A((void**)&n->v, sizeof(float) * n->P);
-  for (int k = 0; k < SR_NET_LAYERS; ++k) {
+  for (int k = 0; k < SR_NET_LAYERS - 1; ++k) {
     const size_t nw = (size_t)n->coutp[k] * 9 * n->cinp[k];
     A((void**)&n->wf[k], sizeof(bf16) * nw);
-    A((void**)&n->wb[k], sizeof(bf16) * nw);
+    if (k > 0) A((void**)&n->wb[k], sizeof(bf16) * nw);
   }
   const size_t P0 = (size_t)max_batch * H * W, P1 = P0 / 4, P2 = P0 / 16;
   const size_t b = sizeof(bf16);
@@ -977,9 +1166,7 @@ sr_status sr_net_create(int H, int W, int max_batch, float phi_clip, void* cuda_
   A((void**)&n->a4, b * P2 * 64);
   A((void**)&n->u4, b * P1 * 64);
   A((void**)&n->a5, b * P1 * 32);
-  A((void**)&n->u5, b * P0 * 32);
-  A((void**)&n->dout, b * P0 * 16);
-  A((void**)&n->du5, b * P0 * 32);
+  A((void**)&n->dout, sizeof(float) * P0);
   A((void**)&n->dz5, b * P1 * 32);
   A((void**)&n->du4, b * P1 * 64);
   A((void**)&n->dz4, b * P2 * 64);
@@ -1081,7 +1268,7 @@ sr_status sr_conv3x3(const uint16_t* x, int B, int H, int W, int cin, const uint
     return SR_EINVAL;
   }
   ConvArgs a{reinterpret_cast<const bf16*>(x), reinterpret_cast<const bf16*>(w), bias,
-             reinterpret_cast<const bf16*>(ref), y, B, H, W, cin, cout, mode, out_scale};
+             reinterpret_cast<const bf16*>(ref), y, B, H, W, cin, cout, mode, out_scale, 9};
   if (mode == SR_CONV_MASK) a.bias = nullptr;
   cudaError_t e = launch_conv(a, static_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) return net_fail(nullptr, e, "sr_conv3x3");
@@ -1106,7 +1293,7 @@ sr_status sr_conv3x3_dgrad(const uint16_t* dy, int B, int H, int W, int cout, co
   e = cudaGetLastError();
   if (e == cudaSuccess) {
     ConvArgs a{reinterpret_cast<const bf16*>(dy), wt, nullptr, reinterpret_cast<const bf16*>(ref),
-               dx, B, H, W, cout, cin, mode, 1.f};
+               dx, B, H, W, cout, cin, mode, 1.f, 9};
     e = launch_conv(a, s);
   }
   cudaError_t e2 = cudaFreeAsync(wt, s);
@@ -1125,7 +1312,7 @@ sr_status sr_conv3x3_wgrad(const uint16_t* dy, const uint16_t* x, int B, int H, 
   }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   WgradArgs a{reinterpret_cast<const bf16*>(dy), reinterpret_cast<const bf16*>(x), dw, B, H, W,
-              cin, cout, cin_real, cout_real, 0};
+              cin, cout, cin_real, cout_real, 0, 9};
   cudaError_t e = launch_wgrad(a, s);
   if (e == cudaSuccess && db)
     e = launch_bias_grad(a.dy, (long long)B * H * W, cout, cout_real, db, s);
