@@ -104,7 +104,7 @@ constexpr int kConvStages = 3;
 // BN output channels per CTA, KC input channels per pipeline stage, warps
 // arranged WM (pixels) x WN (channels).
 template <int BN, int KC, int WM, int WN>
-__global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a) {
+__global__ void __launch_bounds__(kConvThreads, 4) k_conv3x3(ConvArgs a) {
   constexpr int BM = kConvBM, NT = kConvThreads, ST = kConvStages;
   constexpr int LDS = KC + 8;       // shared row stride: conflict-free ldmatrix
   constexpr int VPR = KC / 8;       // 16-byte vectors per row
@@ -870,8 +870,9 @@ cudaError_t wgrad_go(const WgradArgs& a0, cudaStream_t s) {
   }
   const long long M = (long long)a.B * a.H * a.W;
   const int tiles = a.taps * (a.Cout / BCO) * (a.Cin / BCI);
-  // about two CTAs per SM in total, slabs a multiple of the stage size
-  long long slabs = std::max(1LL, (long long)(2 * num_sms() + tiles - 1) / tiles);
+  // about six CTAs per SM in total (the partial tiles meet in fp32 atomics),
+  // slabs a multiple of the stage size
+  long long slabs = std::max(1LL, (long long)(6 * num_sms() + tiles - 1) / tiles);
   long long per = (M + slabs - 1) / slabs;
   per = std::max((long long)kWgKP, (per + kWgKP - 1) / kWgKP * kWgKP);
   slabs = (M + per - 1) / per;

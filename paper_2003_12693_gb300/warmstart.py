@@ -171,7 +171,7 @@ def train(net: "sr_net.Net", images: torch.Tensor, phi_star: torch.Tensor, steps
 # Experiment: what the trained network gains over the rectangle start
 # ----------------------------------------------------------------------------
 def _scene(args):
-    from . import synth
+    from paper_2003_12693_gb300 import synth
     seed, n, noise = args
     return synth.ellipse_scene(seed, n, n, scale=n / 512.0, noise=noise).astype(np.float32)
 
@@ -189,10 +189,11 @@ def experiment(n: int = 128, n_train: int = 2048, n_eval: int = 32, t_ref: int =
 
     from scipy import ndimage
 
-    from . import synth
+    from paper_2003_12693_gb300 import synth
+    from paper_2003_12693_gb300 import warmstart as this   # picklable by module path
     with mp.get_context("spawn").Pool(procs) as pool:
-        tr = np.stack(pool.map(_scene, [(20000 + k, n, 0.1) for k in range(n_train)], 16))
-        ev = np.stack(pool.map(_scene, [(90000 + k, n, 0.1) for k in range(n_eval)], 2))
+        tr = np.stack(pool.map(this._scene, [(20000 + k, n, 0.1) for k in range(n_train)], 16))
+        ev = np.stack(pool.map(this._scene, [(90000 + k, n, 0.1) for k in range(n_eval)], 2))
     torch.cuda.set_device(torch.cuda.current_device())
     prm = dict(synth.WORKLOADS["ellipses_512"].params())
     prm.update(rho=rho, sigma=sigma)
