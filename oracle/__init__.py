@@ -220,6 +220,43 @@ def w_b_update(phi1, g, w1, w2, b1, b2, p: Params, return_shrunk=False):
     return w1, w2, b1, b2
 
 
+def w_b_fixed_point(phi1, g, w1, w2, b1, b2, p: Params, sweeps: int):
+    """Eqs. (38)-(40) swept ``sweeps`` times from w^{k+1,0} = w^k, then
+    Eq. (23): returns w^{k+1}, b^{k+1}.
+
+    Each sweep forms v^{k+1,r} from the current w (Eq. (38), the window sum of
+    Sec. 4 with h(phi^{k+1})), evaluates Eq. (39) with its denominator
+    gamma g delta + mu, and projects by Eq. (40) (the zero vector kept at
+    zero)."""
+    phi1, g = _f64(phi1), _f64(g)
+    w1, w2, b1, b2 = (_f64(a) for a in (w1, w2, b1, b2))
+    d1, d2 = grad(phi1)
+    flat = phi1.ravel()
+    h = np.array([band(x, p.eps, p.band_l) for x in flat]).reshape(phi1.shape)
+    dl = np.array([delta(x, p.eps) for x in flat]).reshape(phi1.shape)
+    c1, c2 = w1, w2
+    for _ in range(int(sweeps)):
+        v1, v2 = repulsion(phi1, c1, c2, p)
+        den = p.gamma * g * dl + p.mu
+        t1 = (p.mu * d1 + p.mu * b1 + 2.0 * p.beta * h * v1) / den
+        t2 = (p.mu * d2 + p.mu * b2 + 2.0 * p.beta * h * v2) / den
+        n = np.hypot(t1, t2)
+        safe = np.where(n > 0.0, n, 1.0)
+        c1 = np.where(n > 0.0, t1 / safe, 0.0)
+        c2 = np.where(n > 0.0, t2 / safe, 0.0)
+    return c1, c2, b1 + d1 - c1, b2 + d2 - c2
+
+
+def outer_iteration_fixed_point(state: "State", g, p: Params, sweeps: int) -> None:
+    """One outer iteration of Alg. 1 in place with the w sub-problem solved
+    by Eqs. (38)-(40) (``sweeps`` sweeps) instead of Eqs. (41)-(42)."""
+    psi = state.phi
+    for _ in range(p.S):
+        psi = phi_step(psi, g, state.w1, state.w2, state.b1, state.b2, p)
+    w1, w2, b1, b2 = w_b_fixed_point(psi, g, state.w1, state.w2, state.b1, state.b2, p, sweeps)
+    state.phi, state.w1, state.w2, state.b1, state.b2 = psi, w1, w2, b1, b2
+
+
 def init(phi0):
     """Alg. 1 initialisation: w0 = grad phi0, b0 = 0."""
     phi0 = _f64(phi0)

@@ -493,3 +493,69 @@ def test_two_disks_energy_decreases(two_disks_run):
 def test_mask_is_sign_of_phi(oracle_lib):
     phi = np.array([[-1.0, 0.0], [1e-300, -1e-300]])
     assert oracle.mask(phi).tolist() == [[1, 0], [0, 1]]
+
+
+# ----------------------------------------------------------------------------
+# The iterated w sub-problem, Eqs. (38)-(40)
+# ----------------------------------------------------------------------------
+def _wb_inputs(seed, H=24, W=20):
+    from paper_2003_12693_gb300 import synth
+    phi, w1, w2, b1, b2, g = synth.random_state(H, W, seed=seed)
+    return phi, g, w1, w2, b1, b2
+
+
+def test_fixed_point_one_sweep_is_the_unthresholded_shrink(oracle_lib):
+    """With gamma = 0 the threshold of Eq. (42) vanishes and Eqs. (41)-(42)
+    reduce to B / |B| with v from w^k: one sweep of Eqs. (38)-(40)."""
+    phi, g, w1, w2, b1, b2 = _wb_inputs(1)
+    p = Params(gamma=0.0, R=3, d=3.0)
+    a = oracle.w_b_fixed_point(phi, g, w1, w2, b1, b2, p, 1)
+    r = oracle.w_b_update(phi, g, w1, w2, b1, b2, p)
+    for x, y in zip(a, r):
+        assert np.allclose(x, y, atol=1e-12)
+
+
+def test_fixed_point_denominator_cancels(oracle_lib):
+    """The positive scalar gamma g delta + mu of Eq. (39) drops out under the
+    projection (40): the result does not depend on gamma or g."""
+    phi, g, w1, w2, b1, b2 = _wb_inputs(2)
+    a = oracle.w_b_fixed_point(phi, g, w1, w2, b1, b2, Params(gamma=4.0, R=3, d=3.0), 2)
+    b = oracle.w_b_fixed_point(phi, 0.3 * g, w1, w2, b1, b2, Params(gamma=0.5, R=3, d=3.0), 2)
+    for x, y in zip(a, b):
+        assert np.allclose(x, y, atol=1e-12)
+
+
+def test_fixed_point_without_repulsion_is_one_sweep(oracle_lib):
+    """beta = 0: v does not enter, so every sweep gives the same w."""
+    phi, g, w1, w2, b1, b2 = _wb_inputs(3)
+    p = Params(beta=0.0, R=3, d=3.0)
+    one = oracle.w_b_fixed_point(phi, g, w1, w2, b1, b2, p, 1)
+    five = oracle.w_b_fixed_point(phi, g, w1, w2, b1, b2, p, 5)
+    for x, y in zip(one, five):
+        assert np.allclose(x, y, atol=1e-13)
+
+
+def test_fixed_point_sweeps_converge_for_weak_repulsion(oracle_lib):
+    """For small beta the map w -> B(w)/|B(w)| contracts: the sweeps settle
+    on a fixed point, unit vectors (or zero) with b from Eq. (23)."""
+    phi, g, w1, w2, b1, b2 = _wb_inputs(4)
+    p = Params(beta=0.02, R=3, d=3.0)
+    a = oracle.w_b_fixed_point(phi, g, w1, w2, b1, b2, p, 30)
+    b = oracle.w_b_fixed_point(phi, g, w1, w2, b1, b2, p, 31)
+    assert np.abs(a[0] - b[0]).max() < 1e-9 and np.abs(a[1] - b[1]).max() < 1e-9
+    n = np.hypot(a[0], a[1])
+    assert np.all((n == 0) | (np.abs(n - 1) < 1e-12))
+    d1, d2 = oracle.grad(phi)
+    assert np.allclose(a[2], b1 + d1 - a[0]) and np.allclose(a[3], b2 + d2 - a[1])
+
+
+def test_outer_iteration_with_one_sweep_and_no_threshold_is_alg1(oracle_lib):
+    """gamma = 0, one sweep: the variant's outer iteration equals Alg. 1's."""
+    phi, g, w1, w2, b1, b2 = _wb_inputs(5, 32, 32)
+    p = Params(gamma=0.0, R=3, d=3.0)
+    st = oracle.State(phi.copy(), w1.copy(), w2.copy(), b1.copy(), b2.copy())
+    ref = st.copy()
+    oracle.outer_iteration_fixed_point(st, g, p, 1)
+    oracle.iterate(ref, g, 1, p)
+    for x, y in zip((st.phi, st.w1, st.w2, st.b1, st.b2), (ref.phi, ref.w1, ref.w2, ref.b1, ref.b2)):
+        assert np.allclose(x, y, atol=1e-11)
