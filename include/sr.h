@@ -170,6 +170,27 @@ sr_status sr_w_b_update(sr_ctx* ctx, const float* phi1, const float* w1_in,
                         const float* w2_in, const float* b1_in, const float* b2_in,
                         float* w1_out, float* w2_out, float* b1_out, float* b2_out);
 
+/* The iterated w sub-problem, Eqs. (38)-(40), then Eq. (23): from
+ * w^{k+1,0} = w^k, `sweeps` times (1 <= sweeps <= 64)
+ *     w <- B / |B|,  B = grad phi^{k+1} + b^k + (2 beta / mu) h(phi^{k+1}) v(w),
+ * v(w) the window sum of Eq. (38) over h(phi^{k+1}) w (terms outside the
+ * image dropped), the zero vector kept at zero; then b^{k+1} = b^k +
+ * grad phi^{k+1} - w^{k+1}.  The denominator gamma g delta + mu of Eq. (39) is
+ * a positive scalar, so the projection (40) removes it: this variant has no
+ * threshold, unlike Eqs. (41)-(42).  Aliasing rules as sr_w_b_update.  The
+ * first call allocates two image planes in the context. */
+sr_status sr_w_b_fixed_point(sr_ctx* ctx, const float* phi1, const float* w1_in,
+                             const float* w2_in, const float* b1_in, const float* b2_in,
+                             int sweeps, float* w1_out, float* w2_out, float* b1_out,
+                             float* b2_out);
+
+/* Choose how sr_iterate (and a group created afterwards) solves the w
+ * sub-problem: sweeps = 0 the generalised soft threshold of Eqs. (41)-(42)
+ * (the default), 1 <= sweeps <= 64 that many sweeps of Eqs. (38)-(40) as in
+ * sr_w_b_fixed_point.  The context's graphs are rebuilt on the next
+ * sr_iterate; groups capture the setting when they are created. */
+sr_status sr_set_w_sweeps(sr_ctx* ctx, int sweeps);
+
 /* One inner step of the phi update, like sr_phi_step, for callers that
  * cannot allocate device memory.  The paper has no counterpart: this entry
  * point exists for hosts that hand out all GPU memory from their own fixed

@@ -19,6 +19,7 @@
 
 #include "sr.h"
 #include "sr_internal.h"
+#include "sr_wfix.h"
 
 using srk::Fft;
 using srk::Geo;
@@ -75,6 +76,10 @@ struct sr_ctx {
   long long iters = 0;
 
   // graphs of one outer iteration without the stopping test, per parity
+  // w sub-problem: 0 = soft threshold (41)-(42); >= 1 = sweeps of (38)-(40)
+  int w_sweeps = 0;
+  float* wfx1 = nullptr;   // sweep ping-pong planes, allocated on first use
+  float* wfx2 = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_kernels = 0;
 
@@ -629,6 +634,53 @@ sr_status enqueue_wb(sr_ctx* c, cudaStream_t s, const float* phi1, const float* 
   });
 }
 
+// Eqs. (38)-(40) swept `sweeps` times from w^k, then Eq. (23); the sweeps
+// alternate between (w1o, w2o) and the context's wfx planes so that the last
+// one lands in (w1o, w2o).  (w1o, w2o) must not alias (w1i, w2i).
+sr_status enqueue_wb_fixed(sr_ctx* c, cudaStream_t s, const float* phi1, const float* w1i,
+                           const float* w2i, const float* e1i, const float* e2i, float* w1o,
+                           float* w2o, float* e1o, float* e2o, const float* phi_old, int sweeps) {
+  const float* cw1 = w1i;
+  const float* cw2 = w2i;
+  for (int r = 0; r < sweeps; ++r) {
+    const bool last = r == sweeps - 1;
+    const bool to_out = (sweeps - 1 - r) % 2 == 0;
+    srk::WFixArgs a{};
+    a.geo = c->geo;
+    a.mod = c->mod;
+    a.phi1 = phi1;
+    a.wk1 = w1i;
+    a.wk2 = w2i;
+    a.ek1 = e1i;
+    a.ek2 = e2i;
+    a.cw1 = cw1;
+    a.cw2 = cw2;
+    a.nw1 = to_out ? w1o : c->wfx1;
+    a.nw2 = to_out ? w2o : c->wfx2;
+    a.e1o = last ? e1o : nullptr;
+    a.e2o = last ? e2o : nullptr;
+    a.phi_old = last ? phi_old : nullptr;
+    a.partials = c->partials;
+    sr_status st = run_kernel(c, SR_KCLASS_WB_UPDATE, s, "k_wfix_sweep",
+                              [&] { return srk::launch_wfix_sweep(a, s); });
+    if (st != SR_OK) return st;
+    cw1 = a.nw1;
+    cw2 = a.nw2;
+  }
+  if (!phi_old) return SR_OK;
+  return run_kernel(c, SR_KCLASS_REDUCE, s, "k_reduce", [&] {
+    return srk::launch_reduce(c->partials, c->n_tile32, 2, c->red, s);
+  });
+}
+
+sr_status alloc_wfix(sr_ctx* c) {
+  if (c->wfx1) return SR_OK;
+  const size_t P = (size_t)c->H * c->W;
+  SR_CUDA(c, cudaMalloc(&c->wfx1, sizeof(float) * P));
+  SR_CUDA(c, cudaMalloc(&c->wfx2, sizeof(float) * P));
+  return SR_OK;
+}
+
 // One outer iteration of Alg. 1 from phi[p], w[p] to phi[1-p], w[1-p].
 sr_status enqueue_iteration(sr_ctx* c, cudaStream_t s, int p, bool check) {
   const int q = 1 - p;
@@ -638,6 +690,9 @@ sr_status enqueue_iteration(sr_ctx* c, cudaStream_t s, int p, bool check) {
                                     it == 0 ? 1 : 2);
     if (st != SR_OK) return st;
   }
+  if (c->w_sweeps > 0)
+    return enqueue_wb_fixed(c, s, c->phi[q], c->w1[p], c->w2[p], c->e1, c->e2, c->w1[q], c->w2[q],
+                            c->e1, c->e2, check ? c->phi[p] : nullptr, c->w_sweeps);
   return enqueue_wb(c, s, c->phi[q], c->w1[p], c->w2[p], c->e1, c->e2, c->w1[q], c->w2[q], c->e1,
                     c->e2, check ? c->phi[p] : nullptr);
 }
@@ -749,7 +804,7 @@ void sr_destroy(sr_ctx* c) {
   void* bufs[] = {c->phi[0], c->phi[1], c->w1[0], c->w1[1], c->w2[0], c->w2[1], c->e1, c->e2,
                   c->g, c->tmp1, c->tmp2, c->stage, c->G, c->divE, c->mask_dev, c->X, c->tw_row, c->tw_col,
                   c->tw_n, c->aM, c->aN, c->partials, c->red, c->err_dev, c->gen_tab,
-                  c->tws[0], c->tws[1], c->tws[2], c->tws[3]};
+                  c->tws[0], c->tws[1], c->tws[2], c->tws[3], c->wfx1, c->wfx2};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -1153,6 +1208,43 @@ sr_status sr_w_b_update(sr_ctx* c, const float* phi1, const float* w1_in, const 
   if (st != SR_OK) return st;
   SR_CUDA(c, srk::launch_axpb(c->tmp1, w1_out, 1.f, b1_out, P, c->stream));  // b = e + w
   SR_CUDA(c, srk::launch_axpb(c->tmp2, w2_out, 1.f, b2_out, P, c->stream));
+  return SR_OK;
+}
+
+sr_status sr_w_b_fixed_point(sr_ctx* c, const float* phi1, const float* w1_in, const float* w2_in,
+                             const float* b1_in, const float* b2_in, int sweeps, float* w1_out,
+                             float* w2_out, float* b1_out, float* b2_out) {
+  if (!c) return SR_EINVAL;
+  if (sweeps < 1 || sweeps > 64) return fail(c, SR_EINVAL, "sweeps must be in [1, 64]");
+  if (!phi1 || !w1_in || !w2_in || !b1_in || !b2_in || !w1_out || !w2_out || !b1_out || !b2_out)
+    return fail(c, SR_EINVAL, "NULL pointer");
+  if (w1_out == w1_in || w2_out == w2_in || w1_out == w2_in || w2_out == w1_in)
+    return fail(c, SR_EINVAL, "w_out must not alias w_in");
+  sr_status st = alloc_wfix(c);
+  if (st != SR_OK) return st;
+  const size_t P = (size_t)c->H * c->W;
+  c->launches += 4;
+  SR_CUDA(c, srk::launch_axpb(b1_in, w1_in, -1.f, c->tmp1, P, c->stream));  // e = b - w
+  SR_CUDA(c, srk::launch_axpb(b2_in, w2_in, -1.f, c->tmp2, P, c->stream));
+  st = enqueue_wb_fixed(c, c->stream, phi1, w1_in, w2_in, c->tmp1, c->tmp2, w1_out, w2_out,
+                        c->tmp1, c->tmp2, nullptr, sweeps);
+  if (st != SR_OK) return st;
+  SR_CUDA(c, srk::launch_axpb(c->tmp1, w1_out, 1.f, b1_out, P, c->stream));  // b = e + w
+  SR_CUDA(c, srk::launch_axpb(c->tmp2, w2_out, 1.f, b2_out, P, c->stream));
+  return SR_OK;
+}
+
+sr_status sr_set_w_sweeps(sr_ctx* c, int sweeps) {
+  if (!c) return SR_EINVAL;
+  if (sweeps < 0 || sweeps > 64) return fail(c, SR_EINVAL, "sweeps must be in [0, 64]");
+  if (sweeps > 0) {
+    sr_status st = alloc_wfix(c);
+    if (st != SR_OK) return st;
+  }
+  if (sweeps != c->w_sweeps) {
+    c->w_sweeps = sweeps;
+    drop_graphs(c);
+  }
   return SR_OK;
 }
 

@@ -103,6 +103,10 @@ def lib() -> C.CDLL:
     L.sr_fft_solve.argtypes = [_P] * 3
     L.sr_w_b_update.restype = st
     L.sr_w_b_update.argtypes = [_P] * 10
+    L.sr_w_b_fixed_point.restype = st
+    L.sr_w_b_fixed_point.argtypes = [_P] * 6 + [C.c_int] + [_P] * 4
+    L.sr_set_w_sweeps.restype = st
+    L.sr_set_w_sweeps.argtypes = [_P, C.c_int]
     L.sr_kernel_launches.restype = C.c_longlong
     L.sr_kernel_launches.argtypes = [_P, C.c_int]
     L.sr_profile_enable.restype = st
@@ -267,6 +271,15 @@ class Context:
         args = [self._dev(t) for t in (phi1, w1, w2, b1, b2, *outs)]
         _check(lib().sr_w_b_update(self.handle, *args), self)
         return tuple(outs)
+
+    def w_b_fixed_point(self, phi1, w1, w2, b1, b2, sweeps: int):
+        outs = [self._new() for _ in range(4)]
+        _check(lib().sr_w_b_fixed_point(self.handle, *[self._dev(b) for b in (phi1, w1, w2, b1, b2)],
+                                        int(sweeps), *[self._dev(b) for b in outs]), self)
+        return tuple(outs)
+
+    def set_w_sweeps(self, sweeps: int):
+        _check(lib().sr_set_w_sweeps(self.handle, int(sweeps)), self)
 
     def get_schedule(self) -> dict:
         sc = sr_schedule()
