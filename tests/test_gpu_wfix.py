@@ -25,7 +25,7 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-SHAPES = [(96, 80), (64, 64), (40, 136)]
+SHAPES = [(96, 80), (64, 64), (48, 144)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
