@@ -3,7 +3,7 @@ solver, train the network of include/sr_net.h on them, and segment new images
 from the network's phi0 with the plain iteration finishing the solve.
 
 Orchestration only: the iterations, the network's passes and its optimiser
-run in libsr.so's kernels.  The host side chooses batches and judges
+run in libsr.so's kernels.  The host side chooses batches and decides
 convergence the same way for every start: every ``check`` outer iterations
 the mask {phi < 0} (sr_mask) is compared either with a reference mask (the
 image counts as converged once the intersection over union reaches ``iou``)
