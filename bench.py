@@ -360,6 +360,20 @@ def warm_start_net_sample(stream, H: int = 256, W: int = 256, B: int = 32,
                    "peak = measured cuBLAS bf16 (burst)"}
 
 
+def job_rate(local_ms: float, units_per_rank: float, world: int, device) -> tuple[float, float]:
+    """Whole-job throughput of ``world`` replicas: the slowest rank's time (max
+    over ranks, one all-reduce) and the units all ranks processed per second
+    of that time.  Returns (max ms, units / s)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * units_per_rank / (ms / 1e3)
+
+
 def run_gpu(args, wl, rank: int, world: int, local_rank: int):
     import numpy as np
     import torch
@@ -425,12 +439,8 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
         dist.barrier()
     launches = ctx.kernel_launches(reset=True)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = float(t_max.item())
-    value = world * P * args.steps / (total_ms / 1e3) / 1e6
+    total_ms, rate = job_rate(sum(step_ms), P * args.steps, world, dev)
+    value = rate / 1e6
 
     # ---- per-kernel durations (events around every launch, no graph)
     ctx.profile_enable(True)
@@ -479,10 +489,8 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
         t0 = time.perf_counter()
         ctx.segment_host(f_h, phi0_h, e2e_iters, 0.0, mask_h)
         e2e_ms += (time.perf_counter() - t0) * 1e3
-    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * P * e2e_iters * jobs / (float(e2e_t.item()) / 1e3) / 1e6
+    _, e2e_rate = job_rate(e2e_ms, P * e2e_iters * jobs, world, dev)
+    e2e_value = e2e_rate / 1e6
     e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": (f.nbytes + phi0.nbytes) / e2e_iters,
            "d2h_bytes_per_step": P / e2e_iters,
