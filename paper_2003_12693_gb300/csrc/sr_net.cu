@@ -633,33 +633,61 @@ __device__ __forceinline__ void load32(const bf16* p, float* v) {
   }
 }
 
-// y[p] = scale * (b6 + sum_{tap, c} u5[p + s(tap), c] w6[tap, c])
+// y[p] = scale * (b6 + sum_{tap, c} u5[p + s(tap), c] w6[tap, c]).  With u5
+// constant on 2 x 2 blocks, the four outputs p = 2q + (i, j) of a half-
+// resolution pixel q read only the 2 x 2 neighbours q + (i - 1 + ar, j - 1 + br),
+// ar, br in {0, 1}, with the taps that land on the same neighbour summed:
+// wc[i][j][ar][br][c] = sum of w6[dy, dx, c] over floor((i + dy) / 2) = i - 1 + ar
+// and floor((j + dx) / 2) = j - 1 + br.  One thread per q; neighbours outside
+// the half-resolution image are the zero padding of the full-resolution one.
 __global__ void __launch_bounds__(256) k_out_fwd(const bf16* __restrict__ a5,
                                                  const float* __restrict__ w6,
                                                  const float* __restrict__ b6,
                                                  float* __restrict__ y, int B, int H, int W,
                                                  float scale) {
-  __shared__ float ws[288];
-  for (int i = threadIdx.x; i < 288; i += blockDim.x) ws[i] = w6[i];
+  __shared__ float wc[2][2][2][2][32];
+  for (int idx = threadIdx.x; idx < 512; idx += blockDim.x) {
+    const int c = idx % 32, br = (idx / 32) % 2, ar = (idx / 64) % 2, j = (idx / 128) % 2,
+              i = idx / 256;
+    float acc = 0.f;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx)
+        if ((i + dy + 2) / 2 - 1 == i - 1 + ar && (j + dx + 2) / 2 - 1 == j - 1 + br)
+          acc += w6[((dy + 1) * 3 + dx + 1) * 32 + c];
+    wc[i][j][ar][br][c] = acc;
+  }
   __syncthreads();
   const int h = H / 2, w = W / 2;
-  const long long P = (long long)B * H * W;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
-       p += (long long)gridDim.x * blockDim.x) {
-    const long long HW = (long long)H * W;
-    const long long b = p / HW;
-    const int rem = (int)(p - b * HW);
-    const int yy = rem / W, xx = rem % W;
-    float acc = 0.f;
-    for (int t = 0; t < 9; ++t) {
-      const int ys = yy + t / 3 - 1, xs = xx + t % 3 - 1;
-      if (ys < 0 || ys >= H || xs < 0 || xs >= W) continue;
-      float v[32];
-      load32(a5 + ((b * h + ys / 2) * w + xs / 2) * 32, v);
+  const long long Q = (long long)B * h * w;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Q;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long hw = (long long)h * w;
+    const long long b = q / hw;
+    const int rem = (int)(q - b * hw);
+    const int qy = rem / w, qx = rem % w;
+#pragma unroll 1
+    for (int ij = 0; ij < 4; ++ij) {
+      const int i = ij >> 1, j = ij & 1;
+      {
+        float acc = 0.f;
 #pragma unroll
-      for (int c = 0; c < 32; ++c) acc = fmaf(v[c], ws[t * 32 + c], acc);
+        for (int ar = 0; ar < 2; ++ar) {
+#pragma unroll
+          for (int br = 0; br < 2; ++br) {
+            const int ny = qy + i - 1 + ar, nx = qx + j - 1 + br;
+            if (ny < 0 || ny >= h || nx < 0 || nx >= w) continue;
+            const bf16* src = a5 + ((b * h + ny) * w + nx) * 32;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              const V8 v = load8(src + g * 8);
+#pragma unroll
+              for (int k = 0; k < 8; ++k) acc = fmaf(v.v[k], wc[i][j][ar][br][g * 8 + k], acc);
+            }
+          }
+        }
+        y[(b * H + 2 * qy + i) * W + 2 * qx + j] = scale * (acc + b6[0]);
+      }
     }
-    y[p] = scale * (acc + b6[0]);
   }
 }
 
@@ -712,7 +740,10 @@ __global__ void __launch_bounds__(256) k_out_dgrad(const float* __restrict__ dou
   }
 }
 
-// dw6[tap, c] += sum_p dout[p] u5[p + s(tap), c]; one warp per tap, a slab of
+// dw6[tap, c] += sum_p dout[p] u5[p + s(tap), c].  Grouped by the half-
+// resolution pixel q that p + s(tap) falls in: dw6[tap, c] = sum_q a5[q, c]
+// D_tap[q], D_tap[q] = sum over (i, j) in {0, 1}^2 of dout[2q + (i, j) - s(tap)]
+// (zero outside the image).  One warp per tap, a slab of half-resolution
 // pixels per CTA, lane l takes pixels l, l + 32, ...
 __global__ void __launch_bounds__(288) k_out_wgrad(const float* __restrict__ dout,
                                                    const bf16* __restrict__ a5,
@@ -722,29 +753,35 @@ __global__ void __launch_bounds__(288) k_out_wgrad(const float* __restrict__ dou
   const int t = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int dy = t / 3 - 1, dx = t % 3 - 1;
   const int h = H / 2, w = W / 2;
-  const long long HW = (long long)H * W, P = HW * B;
+  const long long hw = (long long)h * w, Q = hw * B;
   const long long pb = (long long)blockIdx.x * pix_per_cta;
-  const long long pe = min(P, pb + pix_per_cta);
+  const long long pe = min(Q, pb + pix_per_cta);
   float acc[32];
 #pragma unroll
   for (int c = 0; c < 32; ++c) acc[c] = 0.f;
-  for (long long p = pb + lane; p < pe; p += 32) {
-    const long long b = p / HW;
-    const int rem = (int)(p - b * HW);
-    const int ys = rem / W + dy, xs = rem % W + dx;
-    if (ys < 0 || ys >= H || xs < 0 || xs >= W) continue;
-    const float d = dout[p];
-    float v[32];
-    load32(a5 + ((b * h + ys / 2) * w + xs / 2) * 32, v);
+  for (long long q = pb + lane; q < pe; q += 32) {
+    const long long b = q / hw;
+    const int rem = (int)(q - b * hw);
+    const int qy = rem / w, qx = rem % w;
+    float D = 0.f;
 #pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = fmaf(d, v[c], acc[c]);
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int yy = 2 * qy + i - dy, xx = 2 * qx + j - dx;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) D += dout[(b * H + yy) * W + xx];
+      }
+    float v[32];
+    load32(a5 + q * 32, v);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = fmaf(D, v[c], acc[c]);
   }
 #pragma unroll
   for (int c = 0; c < 32; ++c) red[t][lane][c] = acc[c];
   __syncthreads();
-  float s = 0.f;
-  for (int l = 0; l < 32; ++l) s += red[t][l][lane];
-  atomicAdd(dw6 + t * 32 + lane, s);
+  float sum = 0.f;
+  for (int l = 0; l < 32; ++l) sum += red[t][l][lane];
+  atomicAdd(dw6 + t * 32 + lane, sum);
 }
 
 // Per-layer weight repacking: forward [CoutP, 9, CinP] and flipped
@@ -1034,8 +1071,9 @@ static sr_status net_forward(sr_net* n, const float* f, int B, float out_scale, 
   k_up2<<<ew_grid((long long)B * H2 * W2 * 8), 256, 0, s>>>(n->a4, n->u4, B, H4, W4, 64);
   NET_TRY(net_conv(n, n->u4, B, H2, W2, 64, n->wf[4], th + n->boff[4], 32, SR_CONV_RELU, nullptr,
                    n->a5));
-  k_out_fwd<<<ew_grid(P0), 256, 0, s>>>(n->a5, th + n->woff[5], th + n->boff[5], yout, B, H, W,
-                                         out_scale);
+  k_out_fwd<<<ew_grid((long long)B * H2 * W2), 256, 0, s>>>(n->a5, th + n->woff[5],
+                                                             th + n->boff[5], yout, B, H, W,
+                                                             out_scale);
   NET_CK(n, cudaGetLastError(), "pool / upsample / output layer");
   n->launches += 4;
   return SR_OK;
@@ -1053,11 +1091,12 @@ static sr_status net_backward(sr_net* n, const float* phi_star, int B, double* l
   // layer 6: y = conv(up2(a5)); weight gradient, then input gradient through
   // the upsampling and a5's ReLU
   {
-    const long long blocks = std::min<long long>(2 * num_sms(), std::max(1LL, P0 / 1024));
-    const long long per = (P0 + blocks - 1) / blocks;
-    k_out_wgrad<<<(unsigned)((P0 + per - 1) / per), 288, 0, s>>>(n->dout, n->a5,
-                                                                 n->grad + n->woff[5], B, H, W,
-                                                                 per);
+    const long long Q = (long long)B * H2 * W2;
+    const long long blocks = std::min<long long>(4 * num_sms(), std::max(1LL, Q / 256));
+    const long long per = (Q + blocks - 1) / blocks;
+    k_out_wgrad<<<(unsigned)((Q + per - 1) / per), 288, 0, s>>>(n->dout, n->a5,
+                                                                n->grad + n->woff[5], B, H, W,
+                                                                per);
   }
   k_out_dgrad<<<ew_grid((long long)B * H2 * W2), 256, 0, s>>>(n->dout, n->theta + n->woff[5],
                                                               n->a5, n->dz5, B, H, W);
