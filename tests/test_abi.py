@@ -64,3 +64,58 @@ def test_null_arguments(srmod):
     L.sr_destroy(None)
     assert L.sr_status_string(3) == b"CUDA error"
     assert L.sr_last_error(None) == b""
+
+
+def test_w_sweep_entry_points_reject_null_context(srmod):
+    L = srmod.lib()
+    assert L.sr_set_w_sweeps(None, 2) == 1
+    assert L.sr_w_b_fixed_point(None, None, None, None, None, None, 1, None, None, None, None) == 1
+
+
+@pytest.fixture(scope="module")
+def netmod(srmod):
+    from paper_2003_12693_gb300 import sr_net
+    sr_net.lib()
+    return sr_net
+
+
+def test_network_layer_table_matches_the_oracle(netmod):
+    from oracle import warmstart as ws
+    assert netmod.layers() == [tuple(x) for x in ws.LAYERS]
+    assert netmod.param_count() == ws.param_count() == 185217
+    import ctypes as C
+    ci, co = C.c_int(), C.c_int()
+    assert netmod.lib().sr_net_layer_shape(6, C.byref(ci), C.byref(co)) == 1
+    assert netmod.lib().sr_net_layer_shape(-1, C.byref(ci), C.byref(co)) == 1
+
+
+@pytest.mark.parametrize("H,W,B,clip", [(30, 32, 1, 4.0), (32, 6, 1, 4.0), (32, 32, 0, 4.0),
+                                        (32, 32, 1, 0.0), (32, 32, 1, float("nan")),
+                                        (8192, 32, 1, 4.0)])
+def test_network_create_rejects_bad_arguments_before_touching_cuda(netmod, H, W, B, clip):
+    import ctypes as C
+    h = C.c_void_p()
+    assert netmod.lib().sr_net_create(H, W, B, clip, None, C.byref(h)) == 1
+    assert not h.value
+    assert netmod.lib().sr_net_create(32, 32, 1, 4.0, None, None) == 1
+
+
+def test_network_layer_calls_reject_bad_shapes_before_touching_cuda(netmod):
+    import ctypes as C
+    L = netmod.lib()
+    p = C.c_void_p(16)   # never dereferenced: validation fails first
+    # cin not a multiple of 16
+    assert L.sr_conv3x3(p, 1, 8, 8, 24, p, p, 32, 0, None, p, 1.0, None) == 1
+    # cout not 16, 32 or a multiple of 64
+    assert L.sr_conv3x3(p, 1, 8, 8, 32, p, p, 48, 0, None, p, 1.0, None) == 1
+    # mask mode without ref, bad mode
+    assert L.sr_conv3x3(p, 1, 8, 8, 32, p, p, 32, 2, None, p, 1.0, None) == 1
+    assert L.sr_conv3x3(p, 1, 8, 8, 32, p, p, 32, 7, None, p, 1.0, None) == 1
+    assert L.sr_conv3x3_dgrad(p, 1, 8, 8, 32, p, 32, 0, None, p, None) == 1   # RELU not allowed
+    assert L.sr_conv3x3_wgrad(p, p, 1, 8, 8, 32, 48, 32, 48, p, None, None) == 1
+    assert L.sr_conv3x3_wgrad(p, p, 1, 8, 8, 32, 32, 33, 32, p, None, None) == 1
+    for name in ("sr_net_set_params", "sr_net_get_params", "sr_net_get_grads"):
+        assert getattr(L, name)(None, p) == 1
+    assert L.sr_net_forward(None, p, 1, p) == 1
+    assert L.sr_net_kernel_launches(None, 0) == -1
+    L.sr_net_destroy(None)
