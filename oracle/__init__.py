@@ -257,6 +257,25 @@ def outer_iteration_fixed_point(state: "State", g, p: Params, sweeps: int) -> No
     state.phi, state.w1, state.w2, state.b1, state.b2 = psi, w1, w2, b1, b2
 
 
+def outer_iteration_inner_tol(state: "State", g, p: Params, tol: float) -> list:
+    """One outer iteration of Alg. 1 in place with the inner exit of Sec. 4:
+    after each inner step s the relative change ||psi^{s+1} - psi^s|| /
+    (||psi^s|| + 1e-6) is formed and the loop stops once it is <= tol, after
+    at most p.S steps; then Eqs. (41), (42), (40), (23).  Returns the relative
+    changes of the steps taken."""
+    psi = state.phi
+    rels = []
+    for _ in range(p.S):
+        nxt = phi_step(psi, g, state.w1, state.w2, state.b1, state.b2, p)
+        rels.append(float(np.linalg.norm(nxt - psi) / (np.linalg.norm(psi) + 1e-6)))
+        psi = nxt
+        if rels[-1] <= tol:
+            break
+    w1, w2, b1, b2 = w_b_update(psi, g, state.w1, state.w2, state.b1, state.b2, p)
+    state.phi, state.w1, state.w2, state.b1, state.b2 = psi, w1, w2, b1, b2
+    return rels
+
+
 def init(phi0):
     """Alg. 1 initialisation: w0 = grad phi0, b0 = 0."""
     phi0 = _f64(phi0)

@@ -41,7 +41,7 @@ def _create(srmod, H, W, **kw):
     (dict(mu=0.0), 1), (dict(tau=-0.1), 1), (dict(eps=0.0), 1), (dict(alpha=float("nan")), 1),
     (dict(beta=float("inf")), 1), (dict(win_radius=9), 1), (dict(win_radius=-1), 1),
     (dict(inner_S=0), 1), (dict(s_pow=3), 1), (dict(check_every=0), 1), (dict(d=0.0), 1),
-    (dict(sigma=11.0), 1), (dict(inner_tol=1e-3), 7),
+    (dict(sigma=11.0), 1), (dict(inner_tol=float("nan")), 1),
 ])
 def test_create_rejects_bad_parameters_before_touching_cuda(srmod, kw, status):
     st, h = _create(srmod, 64, 64, **kw)

@@ -559,3 +559,44 @@ def test_outer_iteration_with_one_sweep_and_no_threshold_is_alg1(oracle_lib):
     oracle.iterate(ref, g, 1, p)
     for x, y in zip((st.phi, st.w1, st.w2, st.b1, st.b2), (ref.phi, ref.w1, ref.w2, ref.b1, ref.b2)):
         assert np.allclose(x, y, atol=1e-11)
+
+
+# ----------------------------------------------------------------------------
+# The inner exit of Sec. 4
+# ----------------------------------------------------------------------------
+def _inner_state(seed=8, H=32, W=32):
+    from paper_2003_12693_gb300 import synth
+    phi, w1, w2, b1, b2, g = synth.random_state(H, W, seed=seed)
+    return oracle.State(phi, w1, w2, b1, b2), g
+
+
+def test_inner_exit_with_zero_tolerance_is_alg1(oracle_lib):
+    st, g = _inner_state()
+    p = Params(R=3, d=3.0)
+    ref = st.copy()
+    rels = oracle.outer_iteration_inner_tol(st, g, p, 0.0)
+    oracle.iterate(ref, g, 1, p)
+    assert len(rels) == p.S
+    for x, y in zip((st.phi, st.w1, st.w2, st.b1, st.b2), (ref.phi, ref.w1, ref.w2, ref.b1, ref.b2)):
+        assert np.allclose(x, y, atol=1e-12)
+
+
+def test_inner_exit_with_a_loose_tolerance_takes_one_step(oracle_lib):
+    st, g = _inner_state()
+    p = Params(R=3, d=3.0, S=5)
+    ref = st.copy()
+    rels = oracle.outer_iteration_inner_tol(st, g, p, 1e9)
+    assert len(rels) == 1
+    psi = oracle.phi_step(ref.phi, g, ref.w1, ref.w2, ref.b1, ref.b2, p)
+    assert np.allclose(st.phi, psi, atol=1e-13)
+    assert rels[0] == pytest.approx(np.linalg.norm(psi - ref.phi) / (np.linalg.norm(ref.phi) + 1e-6))
+
+
+def test_inner_exit_steps_grow_as_the_tolerance_shrinks(oracle_lib):
+    st, g = _inner_state()
+    p = Params(R=3, d=3.0, S=8)
+    full = oracle.outer_iteration_inner_tol(st.copy(), g, p, 0.0)
+    assert all(b < a for a, b in zip(full, full[1:]))          # the inner steps contract
+    counts = [len(oracle.outer_iteration_inner_tol(st.copy(), g, p, t))
+              for t in (full[0] * 1.01, full[2] * 1.01, full[5] * 1.01, 0.0)]
+    assert counts == [1, 3, 6, 8]
