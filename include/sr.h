@@ -57,7 +57,9 @@ typedef struct sr_params {
   float d;           /* Gaussian scale of the repulsion window, Sec. 4 */
   int win_radius;    /* window half width R: offsets p, q in [-R, R], 0 <= R <= 8 */
   int inner_S;       /* inner semi-implicit steps per outer iteration, Eq. (37) */
-  float inner_tol;   /* inner stopping tolerance; must be <= 0 (fixed S) in this build */
+  float inner_tol;   /* inner exit of Sec. 4: > 0 stops the inner loop once the relative
+                        change of phi between inner steps is <= inner_tol (at most
+                        inner_S steps; eager, no graph); <= 0 runs exactly inner_S */
   float rho;         /* edge-detector scale, Eq. (1) */
   float sigma;       /* Gaussian smoothing of the image in Eq. (1); 0 disables */
   int s_pow;         /* exponent s in Eq. (1): 1 or 2 */
@@ -190,6 +192,11 @@ sr_status sr_w_b_fixed_point(sr_ctx* ctx, const float* phi1, const float* w1_in,
  * sr_w_b_fixed_point.  The context's graphs are rebuilt on the next
  * sr_iterate; groups capture the setting when they are created. */
 sr_status sr_set_w_sweeps(sr_ctx* ctx, int sweeps);
+
+/* Inner phi steps sr_iterate has run on this context (all outer iterations;
+ * with inner_tol > 0 the count per iteration depends on the data); reset to
+ * zero when reset != 0.  -1 for a NULL context. */
+long long sr_inner_steps(sr_ctx* ctx, int reset);
 
 /* One inner step of the phi update, like sr_phi_step, for callers that
  * cannot allocate device memory.  The paper has no counterpart: this entry

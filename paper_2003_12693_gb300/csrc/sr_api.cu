@@ -20,6 +20,7 @@
 #include "sr.h"
 #include "sr_internal.h"
 #include "sr_wfix.h"
+#include "sr_inner.h"
 
 using srk::Fft;
 using srk::Geo;
@@ -78,6 +79,7 @@ struct sr_ctx {
   // graphs of one outer iteration without the stopping test, per parity
   // w sub-problem: 0 = soft threshold (41)-(42); >= 1 = sweeps of (38)-(40)
   int w_sweeps = 0;
+  long long inner_steps = 0;  // inner phi steps run by sr_iterate (all modes)
   float* wfx1 = nullptr;   // sweep ping-pong planes, allocated on first use
   float* wfx2 = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -160,9 +162,9 @@ sr_status check_params(const sr_params* p, std::string& why) {
     why = "sigma too large (ceil(3 sigma) must be <= 32)";
     return SR_EINVAL;
   }
-  if (p->inner_tol > 0.f) {
-    why = "inner_tol > 0 (data-dependent inner exit) is not implemented; use a fixed inner_S";
-    return SR_EUNSUPPORTED;
+  if (!std::isfinite(p->inner_tol)) {
+    why = "inner_tol must be finite";
+    return SR_EINVAL;
   }
   return SR_OK;
 }
@@ -681,6 +683,50 @@ sr_status alloc_wfix(sr_ctx* c) {
   return SR_OK;
 }
 
+// The w/b update of an outer iteration, by Eqs. (41)-(42) or by sweeps of
+// Eqs. (38)-(40).
+sr_status enqueue_w_step(sr_ctx* c, cudaStream_t s, int p, bool check) {
+  const int q = 1 - p;
+  if (c->w_sweeps > 0)
+    return enqueue_wb_fixed(c, s, c->phi[q], c->w1[p], c->w2[p], c->e1, c->e2, c->w1[q], c->w2[q],
+                            c->e1, c->e2, check ? c->phi[p] : nullptr, c->w_sweeps);
+  return enqueue_wb(c, s, c->phi[q], c->w1[p], c->w2[p], c->e1, c->e2, c->w1[q], c->w2[q], c->e1,
+                    c->e2, check ? c->phi[p] : nullptr);
+}
+
+sr_status read_residual(sr_ctx* c, double* rel);
+
+// One outer iteration with the inner exit of Sec. 4: after each inner step
+// the relative change ||psi^{s+1} - psi^s|| / (||psi^s|| + 1e-6) is reduced in
+// FP64 and read back; the loop stops once it is <= inner_tol, after at most
+// inner_S steps.  Runs eagerly (the step count is data-dependent).
+sr_status enqueue_iteration_inner_tol(sr_ctx* c, int p, bool check) {
+  const int q = 1 - p;
+  const size_t P = (size_t)c->H * c->W;
+  const int nblocks = std::max(1, std::min(c->n_tile32, 1024));  // partials hold 2 n_tile32
+  for (int it = 0; it < c->prm.inner_S; ++it) {
+    const float* in = it == 0 ? c->phi[p] : c->phi[q];
+    const float* prev = in;
+    if (it > 0) {  // the step overwrites psi in place: keep psi^s
+      SR_CUDA(c, cudaMemcpyAsync(c->tmp1, in, sizeof(float) * P, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+      prev = c->tmp1;
+    }
+    sr_status st = enqueue_phi_step(c, c->stream, in, c->w1[p], c->w2[p], c->e1, c->e2,
+                                    c->phi[q], nullptr, it == 0 ? 1 : 2);
+    if (st != SR_OK) return st;
+    c->inner_steps += 1;
+    c->launches += 2;
+    SR_CUDA(c, srk::launch_change_partials(c->phi[q], prev, P, c->partials, nblocks, c->stream));
+    SR_CUDA(c, srk::launch_reduce(c->partials, nblocks, 2, c->red, c->stream));
+    double rel = 0.0;
+    st = read_residual(c, &rel);
+    if (st != SR_OK) return st;
+    if (rel <= (double)c->prm.inner_tol) break;
+  }
+  return enqueue_w_step(c, c->stream, p, check);
+}
+
 // One outer iteration of Alg. 1 from phi[p], w[p] to phi[1-p], w[1-p].
 sr_status enqueue_iteration(sr_ctx* c, cudaStream_t s, int p, bool check) {
   const int q = 1 - p;
@@ -690,11 +736,7 @@ sr_status enqueue_iteration(sr_ctx* c, cudaStream_t s, int p, bool check) {
                                     it == 0 ? 1 : 2);
     if (st != SR_OK) return st;
   }
-  if (c->w_sweeps > 0)
-    return enqueue_wb_fixed(c, s, c->phi[q], c->w1[p], c->w2[p], c->e1, c->e2, c->w1[q], c->w2[q],
-                            c->e1, c->e2, check ? c->phi[p] : nullptr, c->w_sweeps);
-  return enqueue_wb(c, s, c->phi[q], c->w1[p], c->w2[p], c->e1, c->e2, c->w1[q], c->w2[q], c->e1,
-                    c->e2, check ? c->phi[p] : nullptr);
+  return enqueue_w_step(c, s, p, check);
 }
 
 void drop_graphs(sr_ctx* c) {
@@ -1015,7 +1057,8 @@ sr_status sr_iterate(sr_ctx* c, int max_outer, double tol, int* outer_done, doub
   if (outer_done) *outer_done = 0;
   if (max_outer < 0 || !std::isfinite(tol)) return fail(c, SR_EINVAL, "bad max_outer or tol");
   if (max_outer == 0) return SR_OK;
-  const bool use_graph = !c->profile;
+  const bool inner_exit = c->prm.inner_tol > 0.f;
+  const bool use_graph = !c->profile && !inner_exit;
   if (use_graph) {
     sr_status st = build_graphs(c);
     if (st != SR_OK) return st;
@@ -1032,10 +1075,13 @@ sr_status sr_iterate(sr_ctx* c, int max_outer, double tol, int* outer_done, doub
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
       c->launches += c->graph_kernels;
       st = SR_OK;
+    } else if (inner_exit) {
+      st = enqueue_iteration_inner_tol(c, c->cur, check);
     } else {
       st = enqueue_iteration(c, c->stream, c->cur, check);
     }
     if (st != SR_OK) return st;
+    if (!inner_exit) c->inner_steps += c->prm.inner_S;
     c->cur ^= 1;
     c->iters += 1;
     done = k + 1;
@@ -1234,6 +1280,13 @@ sr_status sr_w_b_fixed_point(sr_ctx* c, const float* phi1, const float* w1_in, c
   return SR_OK;
 }
 
+long long sr_inner_steps(sr_ctx* c, int reset) {
+  if (!c) return -1;
+  const long long v = c->inner_steps;
+  if (reset) c->inner_steps = 0;
+  return v;
+}
+
 sr_status sr_set_w_sweeps(sr_ctx* c, int sweeps) {
   if (!c) return SR_EINVAL;
   if (sweeps < 0 || sweeps > 64) return fail(c, SR_EINVAL, "sweeps must be in [0, 64]");
@@ -1374,6 +1427,9 @@ sr_status sr_group_create(sr_ctx* const* members, int n, sr_group** out) {
   sr_ctx* c0 = members[0];
   for (int k = 0; k < n; ++k)
     if (members[k]->profile) return fail(c0, SR_EINVAL, "group members must not be profiling");
+  for (int k = 0; k < n; ++k)
+    if (members[k]->prm.inner_tol > 0.f)
+      return fail(c0, SR_EUNSUPPORTED, "group members must use a fixed inner_S (inner_tol <= 0)");
   for (int k = 1; k < n; ++k) {
     if (members[k]->stream != c0->stream || members[k]->device != c0->device)
       return fail(c0, SR_EINVAL, "group members must share the device and the stream");

@@ -107,6 +107,8 @@ def lib() -> C.CDLL:
     L.sr_w_b_fixed_point.argtypes = [_P] * 6 + [C.c_int] + [_P] * 4
     L.sr_set_w_sweeps.restype = st
     L.sr_set_w_sweeps.argtypes = [_P, C.c_int]
+    L.sr_inner_steps.restype = C.c_longlong
+    L.sr_inner_steps.argtypes = [_P, C.c_int]
     L.sr_kernel_launches.restype = C.c_longlong
     L.sr_kernel_launches.argtypes = [_P, C.c_int]
     L.sr_profile_enable.restype = st
@@ -289,6 +291,9 @@ class Context:
     def set_schedule(self, row_values_per_thread: int, row_threads: int, col_schedule: int):
         sc = sr_schedule(row_values_per_thread, row_threads, col_schedule, 0.0)
         _check(lib().sr_set_schedule(self.handle, C.byref(sc)), self)
+
+    def inner_steps(self, reset: bool = False) -> int:
+        return int(lib().sr_inner_steps(self.handle, int(reset)))
 
     def kernel_launches(self, reset: bool = False) -> int:
         return int(lib().sr_kernel_launches(self.handle, int(reset)))
