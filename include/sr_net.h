@@ -20,10 +20,11 @@
  * of the batch, c = phi_clip.  Optimiser: Adam with bias correction
  * (beta1 0.9, beta2 0.999, eps 1e-8).
  *
- * Precision.  Activations and their gradients are bfloat16 in NHWC layout;
- * every convolution runs on the tensor cores with bf16 operands and fp32
- * accumulation.  Parameters, their gradients, the Adam moments, the output
- * y and the loss (fp64) are kept in higher precision.
+ * Precision.  Activations and their gradients are bfloat16 in NHWC layout.
+ * Layers 1-5 run on the tensor cores with bf16 operands (weights rounded to
+ * bf16) and fp32 accumulation; the one-channel output layer runs in fp32 on
+ * the float weights.  Parameters, their gradients, the Adam moments, the
+ * output y, dL/dy and the loss (fp64) are kept in higher precision.
  *
  * Parameters.  One flat float32 vector of sr_net_param_count() entries:
  * layer after layer, W in (Cout, 3, 3, Cin) order followed by the Cout
