@@ -112,7 +112,8 @@ sr_status sr_conv3x3_dgrad(const uint16_t* dy, int B, int H, int W, int cout, co
 /* Weight and bias gradients, ADDED into dw [cout_real, 3, 3, cin_real] and
  * db [cout_real] (float32; db may be NULL): dw[o,ky,kx,c] += sum_{b,i,j}
  * dy[b,i,j,o] x[b,i+ky-1,j+kx-1,c] over o < cout_real, c < cin_real, with
- * dy [B, H, W, cout] and x [B, H, W, cin] bf16 (cin, cout multiples of 16). */
+ * dy [B, H, W, cout] and x [B, H, W, cin] bf16 (cin and cout each 16, 32 or a
+ * multiple of 64). */
 sr_status sr_conv3x3_wgrad(const uint16_t* dy, const uint16_t* x, int B, int H, int W, int cin,
                            int cout, int cin_real, int cout_real, float* dw, float* db,
                            void* cuda_stream);
