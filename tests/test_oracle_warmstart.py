@@ -128,3 +128,24 @@ def test_adam_first_step_closed_form():
     # a constant gradient keeps the bias-corrected step at lr g / (|g| + eps)
     th2, m, v = ws.adam(new, g, m, v, 2, lr=1e-2)
     assert np.allclose(th2, new - 1e-2 * g / (np.abs(g) + 1e-8), atol=1e-12)
+
+
+def test_seeded_network_parameters():
+    """He-normal weights per layer (the last layer's scaled by 0.1), zero
+    biases, the same vector for the same seed."""
+    theta = synth.net_init(9, ws.LAYERS)
+    assert theta.size == ws.param_count()
+    assert np.array_equal(theta, synth.net_init(9, ws.LAYERS))
+    for k, ((W, b), (ci, co)) in enumerate(zip(ws.unflatten(theta), ws.LAYERS)):
+        assert np.all(b == 0.0)
+        want = np.sqrt(2.0 / (9 * ci)) * (0.1 if k == len(ws.LAYERS) - 1 else 1.0)
+        if W.size >= 1000:
+            assert W.std() == pytest.approx(want, rel=0.1)
+
+
+def test_bf16_exact_matches_torch_rounding():
+    import torch
+    rng = np.random.default_rng(10)
+    a = rng.normal(size=20000) * np.exp(rng.normal(size=20000) * 4)
+    ref = torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(synth.bf16_exact(a), ref)
