@@ -490,6 +490,90 @@ def test_two_disks_energy_decreases(two_disks_run):
     assert e1[0] < e0[0]
 
 
+# --------------------------------------------------------------------------
+# Discrete energy, Eqs. (7)-(10)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,R,d,seed", [((12, 11), 3, 3.0, 31), ((16, 16), 4, 4.0, 32),
+                                            ((9, 14), 2, 5.0, 33)])
+def test_energy_is_the_split_energy_on_the_constraint(oracle_lib, shape, R, d, seed):
+    """With w = grad phi (forward differences) and b = 0 the splitting penalty
+    of Eq. (22) vanishes and the split energy is the energy of Eq. (7).  The
+    split energy is pinned independently: its finite-difference gradient is
+    the right-hand side of Eq. (37) (test_rhs_is_descent_direction_of_split_energy)."""
+    from paper_2003_12693_gb300.synth import random_state
+    phi, _, _, _, _, g = random_state(*shape, seed=seed, phi_scale=2.0)
+    p = Params(alpha=3.0, beta=0.6, gamma=2.5, mu=8.0, tau=0.1, R=R, d=d)
+    d1 = np.roll(phi, -1, 0) - phi
+    d2 = np.roll(phi, -1, 1) - phi
+    z = np.zeros_like(phi)
+    ref = _split_energy(phi, g, d1, d2, z, z, p)
+    E, Eg, Ea, Er = oracle.energy(phi, g, p)
+    assert E == pytest.approx(ref, rel=1e-12, abs=1e-12)
+    assert E == pytest.approx(p.gamma * Eg + p.alpha * Ea + p.beta * Er, rel=1e-13, abs=1e-13)
+    # each term alone, by switching the other weights off
+    for a, b_, c in ((1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0)):
+        q = Params(alpha=a, beta=b_, gamma=c, mu=8.0, tau=0.1, R=R, d=d)
+        assert oracle.energy(phi, g, q)[0] == pytest.approx(
+            _split_energy(phi, g, d1, d2, z, z, q), rel=1e-12, abs=1e-12)
+
+
+@pytest.mark.parametrize("shape,R,d", [((10, 12), 3, 3.0), ((14, 9), 2, 2.5)])
+def test_energy_repulsion_term_matches_pair_sum(oracle_lib, shape, R, d):
+    """E_r = -sum over all ordered pixel pairs (x, y), both inside the image and
+    within the R-window, of K(x - y) h(phi_x) h(phi_y) grad phi_x . grad phi_y:
+    an O(P^2) loop over every pair."""
+    from paper_2003_12693_gb300.synth import random_state
+    phi, _, _, _, _, g = random_state(*shape, seed=41, phi_scale=1.5)
+    p = Params(R=R, d=d)
+    M, N = shape
+    d1 = np.roll(phi, -1, 0) - phi
+    d2 = np.roll(phi, -1, 1) - phi
+    hb = np.vectorize(lambda x: oracle.band(x, p.eps, p.band_l))(phi)
+    pts = [(i, j) for i in range(M) for j in range(N)]
+    Er = 0.0
+    for x1, x2 in pts:
+        for y1, y2 in pts:
+            if abs(x1 - y1) <= R and abs(x2 - y2) <= R:
+                k = math.exp(-((x1 - y1) ** 2 + (x2 - y2) ** 2) / d ** 2)
+                Er -= k * hb[x1, x2] * hb[y1, y2] * (d1[x1, x2] * d1[y1, y2] +
+                                                     d2[x1, x2] * d2[y1, y2])
+    assert oracle.energy(phi, g, p)[3] == pytest.approx(Er, rel=1e-12, abs=1e-12)
+
+
+def test_energy_of_constant_level_sets(oracle_lib):
+    """Far from the contour (|phi| > eps) delta and h vanish, so E_g = E_r = 0;
+    E_a counts the g-weighted inside: sum g where phi < -eps, 0 where phi > eps."""
+    rng = np.random.default_rng(5)
+    g = rng.uniform(0.1, 1.0, (11, 13))
+    p = Params()
+    for c, area in ((-3.0, g.sum()), (3.0, 0.0)):
+        E, Eg, Ea, Er = oracle.energy(np.full(g.shape, c), g, p)
+        assert Eg == 0.0 and Er == 0.0
+        assert Ea == pytest.approx(area, rel=1e-14)
+        assert E == pytest.approx(p.alpha * area, rel=1e-14)
+
+
+@pytest.mark.parametrize("eps,offset", [(1.0, 0.5), (1.0, 0.3), (2.0, 0.5)])
+def test_energy_of_a_straight_edge(oracle_lib, eps, offset):
+    """phi = j - c, a signed distance to the vertical line j = c (inside to the
+    left).  With g = 1 the geodesic term is the contour's length: the raised
+    cosine delta of Eq. (6) sampled at unit spacing sums to exactly 1 across the
+    edge when 2 eps is an integer, so E_g = M (rows).  The area term is the
+    inside's area, c + 1/2 per row: its derivative in c is that same delta sum
+    (= 1), and at a half-integer c the samples of the odd function
+    1 - H(x) - [x < 0] cancel in pairs.  Periodic forward differences wrap only
+    at the last column, where phi is far outside the band."""
+    M, N = 10, 24
+    c = 9 + offset
+    phi = np.tile(np.arange(N, dtype=np.float64) - c, (M, 1))
+    g = np.ones((M, N))
+    p = Params(eps=eps)
+    _, Eg, Ea, _ = oracle.energy(phi, g, p)
+    assert Eg == pytest.approx(M * 1.0, rel=1e-13)
+    assert Ea == pytest.approx(M * (c + 0.5), rel=1e-13)
+
+
 def test_mask_is_sign_of_phi(oracle_lib):
     phi = np.array([[-1.0, 0.0], [1e-300, -1e-300]])
     assert oracle.mask(phi).tolist() == [[1, 0], [0, 1]]
