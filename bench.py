@@ -66,7 +66,8 @@ def _peaks():
 
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("sr_kernels.cu", "sr_fft.cu", "sr_tma.cuh", "sr_internal.h"):
+    for name in ("sr_kernels.cu", "sr_fft.cu", "sr_colrec.cu", "sr_tma.cuh", "sr_internal.h",
+                 "sr_dft.cuh"):
         with open(os.path.join(ROOT, "paper_2003_12693_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -461,9 +462,12 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
                         "achieved_gbs": bytes_launch / avg_s / 1e9 if avg_s else None}
     dom = max(kstats, key=lambda k: kstats[k]["share"] or 0)
     ach = kstats[dom]["achieved_gbs"]
-    roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": ach, "peak": hbm_peak,
+    names = dict(KERNEL_NAMES)
+    if schedule.get("col_schedule") == 7:
+        names["colsolve"] = "k_colsolve_rec"
+    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": hbm_peak,
                 "unit": "GB/s", "frac": ach / hbm_peak, "peak_kind": peak_kind,
-                "traffic": _ncu_traffic(KERNEL_NAMES[dom], wl.name)}
+                "traffic": _ncu_traffic(names[dom], wl.name)}
     if dom in ("rowfft", "colsolve", "rowifft"):
         roofline["note"] = ("FFT pass on the L2-resident half spectrum (16.8 MB at 2048^2): bound by "
                             "instruction issue, shared memory and barriers, not by DRAM; the "

@@ -238,7 +238,13 @@ sr_status sr_phi_step_noalloc(int H, int W, const sr_params* p, const float* g,
  *                 box loads/stores, double buffered), 4 columns, 16 values;
  *                 4 = 2 columns, 16 values; 5 = 4 columns, 16 values with
  *                 double-buffered exchanges; 6 = 4 columns, 16 values with
- *                 registers capped for two CTAs per SM
+ *                 registers capped for two CTAs per SM; 7 = no column FFT:
+ *                 the column operator of Eq. (32) for row frequency k is
+ *                 the periodic tridiagonal c_k - tau mu (S + S^-1), solved
+ *                 exactly by its scalar factorisation into a forward and a
+ *                 backward first-order recursion (warm-up long enough that
+ *                 the truncated start is below 2^-27 relative; available
+ *                 when tau mu <= about 8)
  *   tuned_us: measured microseconds of one row pair plus one column pass
  *             when the autotuner chose the schedule, else 0.
  * Sizes below W = 32 use fixed kernels and report row_threads = 0.
@@ -274,6 +280,28 @@ long long sr_kernel_launches(const sr_ctx* ctx, int reset);
 #define SR_KCLASS_COUNT 6
 sr_status sr_profile_enable(sr_ctx* ctx, int enable);
 sr_status sr_kernel_times(sr_ctx* ctx, int kclass, double* total_ms, long long* launches);
+
+/* ---- Failure-path test hooks (not needed in normal use) ----
+ * They let tests drive the library's error paths without faulting, hanging
+ * or exhausting a GPU.
+ *
+ * sr_test_stall_waits: with cycles > 0, every CTA of the TMA column pass
+ * (col_schedule 3 of sr_schedule) makes its first wait on a shared-memory
+ * barrier that no transfer arrives on, gives up after `cycles` clock cycles,
+ * records a timeout in the context's device error flag, waits (bounded by the
+ * normal limit of about 2^31 cycles) for its own transfers in flight, and
+ * returns.  The next synchronising call (sr_iterate with tol > 0 or a
+ * rel_change pointer) then returns SR_ETIMEOUT and clears the flag; the
+ * context stays usable, and cycles = 0 restores normal waits.  Other column
+ * schedules have no device-side waits and ignore the setting.  SR_EINVAL for
+ * a NULL context or cycles < 0.
+ *
+ * sr_test_fail_allocations: process-wide; after n more successful device or
+ * pinned-host allocations by the library, every further one fails as if
+ * memory had run out, so the calling entry point returns SR_ENOMEM after
+ * freeing what it had allocated.  n < 0 removes the limit (the default). */
+sr_status sr_test_stall_waits(sr_ctx* ctx, long long cycles);
+sr_status sr_test_fail_allocations(long long n);
 
 /* Batched iteration (many images, uneven sizes).  A group holds n contexts
  * created on the same device with the same stream (sizes may differ; every

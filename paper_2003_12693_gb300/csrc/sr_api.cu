@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <new>
@@ -47,6 +48,7 @@ struct sr_ctx {
   bool tm_X_ok = false;
   int col_tma_grid = 0;
   int* err_dev = nullptr;  // device error flag of the bounded waits
+  long long stall_cycles = 0;  // failure-path tests: TMA column waits that run out (sr_test_stall_waits)
   int n_tile = 0;    // CTAs of the 32 x 8 tile kernels (energy)
   int n_tile32 = 0;  // CTAs of the 32 x 32 tile kernels (w/b update)
 
@@ -64,6 +66,9 @@ struct sr_ctx {
   float* divE = nullptr;      // div e of the current outer iteration (fixed over the inner loop)
   unsigned char* mask_dev = nullptr;
   float2* X = nullptr;
+  float2* X2 = nullptr;       // output of the recursion column pass (schedule 7)
+  float4* rec = nullptr;      // per-column (r, s) pairs of that pass
+  int rec_R = 0;              // its warm-up length; 0 if it is not available
   float2* tw_row = nullptr;
   float2* tw_col = nullptr;
   float2* tw_n = nullptr;
@@ -258,9 +263,35 @@ std::vector<float2> stage_twiddle_table(int len, int logE) {
   return v;
 }
 
+// Failure injection for tests (sr_test_fail_allocations): the number of
+// device or pinned-host allocations the library may still make before the
+// next ones fail as if memory had run out; negative = no limit.
+std::atomic<long long> g_alloc_budget{-1};
+
+bool take_alloc() {
+  long long b = g_alloc_budget.load();
+  while (b >= 0) {
+    if (b == 0) return false;
+    if (g_alloc_budget.compare_exchange_weak(b, b - 1)) return true;
+  }
+  return true;
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  if (!take_alloc()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_alloc(void** p, size_t bytes) {
+  if (!take_alloc()) return cudaErrorMemoryAllocation;
+  return cudaMallocHost(p, bytes);
+}
+
 template <class T>
 sr_status upload(sr_ctx* c, T** dst, const std::vector<T>& v) {
-  SR_CUDA(c, cudaMalloc((void**)dst, v.size() * sizeof(T)));
+  const cudaError_t e = dev_alloc((void**)dst, v.size() * sizeof(T));
+  if (e == cudaErrorMemoryAllocation) return fail(c, SR_ENOMEM, "device allocation failed");
+  SR_CUDA(c, e);
   SR_CUDA(c, cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
   return SR_OK;
 }
@@ -322,9 +353,13 @@ int sched_rows(const sr_ctx* c, const sr_schedule& sc) {
 bool sched_valid(const sr_ctx* c, const sr_schedule& sc) {
   if (!c->fft2) return false;
   if (sc.row_values_per_thread != 8 && sc.row_values_per_thread != 16) return false;
-  if (sc.col_schedule < 0 || sc.col_schedule > 6) return false;
-  if (sc.col_schedule == 3 && !c->tm_X_ok) return false;
-  if (srk::colsolve2_threads(c->H, sc.col_schedule) > 1024) return false;
+  if (sc.col_schedule == srk::kColRec) {
+    if (c->rec_R <= 0) return false;
+  } else {
+    if (sc.col_schedule < 0 || sc.col_schedule > 6) return false;
+    if (sc.col_schedule == 3 && !c->tm_X_ok) return false;
+    if (srk::colsolve2_threads(c->H, sc.col_schedule) > 1024) return false;
+  }
   if (sc.row_threads < 1 || sc.row_threads > 512) return false;
   const long long prod = (long long)sc.row_threads * sc.row_values_per_thread;
   if (prod % c->L) return false;
@@ -348,6 +383,7 @@ cudaError_t sched_configure(sr_ctx* c, const sr_schedule& sc) {
   cudaError_t e = srk::launch_rowfft2(fa, le, sc.row_threads, nullptr, true);
   if (e == cudaSuccess) e = srk::launch_rowifft2(ia, true, le, sc.row_threads, nullptr, true);
   if (e != cudaSuccess) return e;
+  if (sc.col_schedule == srk::kColRec) return cudaSuccess;
   if (sc.col_schedule == 3) {
     e = srk::launch_colsolve_tma(ca, c->tm_X, 0, nullptr, true);
     int per_sm = 0;
@@ -500,7 +536,7 @@ sr_status autotune(sr_ctx* c) {
       }
     }
   float best_col = 1e30f;
-  for (int cs = 0; cs < 7 && err == cudaSuccess; ++cs) {
+  for (int cs = 0; cs <= srk::kColRec && err == cudaSuccess; ++cs) {
     sr_schedule sc = best;
     sc.col_schedule = cs;
     if (!sched_valid(c, sc)) continue;
@@ -512,8 +548,12 @@ sr_status autotune(sr_ctx* c) {
     ca.aN = c->aN;
     ca.X = c->X;
     ca.err = c->err_dev;
+    ca.rec = c->rec;
+    ca.rec_R = c->rec_R;
+    ca.Xout = c->X2;
     float us = 0.f;
     err = time_it([&] {
+      if (cs == srk::kColRec) return srk::launch_colsolve_rec(ca, s);
       return cs == 3 ? srk::launch_colsolve_tma(ca, c->tm_X, c->col_tma_grid, s, false)
                      : srk::launch_colsolve2(ca, cs, s, false);
     }, &us);
@@ -583,9 +623,15 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
   ca.aN = c->aN;
   ca.X = c->X;
   ca.err = c->err_dev;
+  ca.stall_cycles = c->stall_cycles;
+  ca.rec = c->rec;
+  ca.rec_R = c->rec_R;
+  ca.Xout = c->X2;
+  const bool col_rec = c->fft2 && c->sched.col_schedule == srk::kColRec;
   st = run_kernel(c, SR_KCLASS_COLSOLVE, s, "k_colsolve", [&] {
     if (c->fftgen) return srk::launch_colsolve_gen(ca, c->plan_col, c->gen_batched, s);
     if (!c->fft2) return srk::launch_colsolve(ca, s);
+    if (col_rec) return srk::launch_colsolve_rec(ca, s);
     if (c->sched.col_schedule == 3)
       return srk::launch_colsolve_tma(ca, c->tm_X, c->col_tma_grid, s, false);
     return srk::launch_colsolve2(ca, c->sched.col_schedule, s, false);
@@ -595,7 +641,7 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
   ia.geo = c->geo;
   ia.fft = c->fft_row;
   ia.twN = c->tw_n;
-  ia.X = c->X;
+  ia.X = col_rec ? c->X2 : c->X;
   ia.psi_in = psi_in;
   ia.out = psi_out;
   ia.T = c->fft2 ? sched_rows(c, c->sched) : c->fftgen ? srk::gen_rows_per_cta(c->L, c->H, c->gen_batched) : c->row_T;
@@ -678,8 +724,11 @@ sr_status enqueue_wb_fixed(sr_ctx* c, cudaStream_t s, const float* phi1, const f
 sr_status alloc_wfix(sr_ctx* c) {
   if (c->wfx1) return SR_OK;
   const size_t P = (size_t)c->H * c->W;
-  SR_CUDA(c, cudaMalloc(&c->wfx1, sizeof(float) * P));
-  SR_CUDA(c, cudaMalloc(&c->wfx2, sizeof(float) * P));
+  for (float** pl : {&c->wfx1, &c->wfx2}) {
+    const cudaError_t e = dev_alloc((void**)pl, sizeof(float) * P);
+    if (e == cudaErrorMemoryAllocation) return fail(c, SR_ENOMEM, "device allocation failed");
+    SR_CUDA(c, e);
+  }
   return SR_OK;
 }
 
@@ -846,7 +895,8 @@ void sr_destroy(sr_ctx* c) {
   void* bufs[] = {c->phi[0], c->phi[1], c->w1[0], c->w1[1], c->w2[0], c->w2[1], c->e1, c->e2,
                   c->g, c->tmp1, c->tmp2, c->stage, c->G, c->divE, c->mask_dev, c->X, c->tw_row, c->tw_col,
                   c->tw_n, c->aM, c->aN, c->partials, c->red, c->err_dev, c->gen_tab,
-                  c->tws[0], c->tws[1], c->tws[2], c->tws[3], c->wfx1, c->wfx2};
+                  c->tws[0], c->tws[1], c->tws[2], c->tws[3], c->wfx1, c->wfx2,
+                  c->X2, c->rec};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -928,17 +978,8 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   // CTA with T * (W/2) = 16 * threads
   const int L = c->L;
   if (pow2) {
-    int NT = L >= 2048 ? 512 : 256;
-    int T = 16 * NT / L;
-    while (NT > 64 && T > 1 && (H + T - 1) / T < 2 * c->nsm) {
-      NT /= 2;
-      T = 16 * NT / L;
-    }
-    if (T > H) {
-      T = H;
-      NT = T * L / 16;
-    }
-    if (T < 1 || NT < 1 || NT * 16 != T * L) return bail(SR_EUNSUPPORTED);
+    int NT = 0, T = 0;
+    if (!srk::row_shape(H, L, c->nsm, &NT, &T)) return bail(SR_EUNSUPPORTED);
     c->row_T = T;
     c->row_NT = NT;
   }
@@ -950,19 +991,19 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   float** planes[] = {&c->phi[0], &c->phi[1], &c->w1[0], &c->w1[1], &c->w2[0], &c->w2[1],
                       &c->e1,     &c->e2,     &c->g,     &c->tmp1,  &c->tmp2,  &c->stage,
                       &c->G,      &c->divE};
-  for (float** pl : planes) CREATE_CUDA(cudaMalloc((void**)pl, P * sizeof(float)));
-  CREATE_CUDA(cudaMalloc((void**)&c->mask_dev, P));
-  CREATE_CUDA(cudaMalloc((void**)&c->X, (size_t)H * L * sizeof(float2)));
-  CREATE_CUDA(cudaMalloc((void**)&c->partials, (size_t)c->n_tile * 3 * sizeof(double)));
-  CREATE_CUDA(cudaMalloc((void**)&c->red, 4 * sizeof(double)));
-  CREATE_CUDA(cudaMallocHost((void**)&c->red_host, 4 * sizeof(double)));
+  for (float** pl : planes) CREATE_CUDA(dev_alloc((void**)pl, P * sizeof(float)));
+  CREATE_CUDA(dev_alloc((void**)&c->mask_dev, P));
+  CREATE_CUDA(dev_alloc((void**)&c->X, (size_t)H * L * sizeof(float2)));
+  CREATE_CUDA(dev_alloc((void**)&c->partials, (size_t)c->n_tile * 3 * sizeof(double)));
+  CREATE_CUDA(dev_alloc((void**)&c->red, 4 * sizeof(double)));
+  CREATE_CUDA(host_alloc((void**)&c->red_host, 4 * sizeof(double)));
   for (float** pl : planes) CREATE_CUDA(cudaMemset(*pl, 0, P * sizeof(float)));
 
   // tables: FFT twiddles, the post/pre-processing twiddles of the real row
   // transform, and the two halves of the symbol of Eq. (32)
-  if (upload(c, &c->tw_row, twiddles(L, L)) != SR_OK) return bail(SR_ECUDA);
-  if (upload(c, &c->tw_col, twiddles(H, H)) != SR_OK) return bail(SR_ECUDA);
-  if (upload(c, &c->tw_n, twiddles(L, W)) != SR_OK) return bail(SR_ECUDA);
+  if ((st = upload(c, &c->tw_row, twiddles(L, L))) != SR_OK) return bail(st);
+  if ((st = upload(c, &c->tw_col, twiddles(H, H))) != SR_OK) return bail(st);
+  if ((st = upload(c, &c->tw_n, twiddles(L, W))) != SR_OK) return bail(st);
   std::vector<float> aM(H), aN(L + 1);
   const double tm = (double)p->tau * (double)p->mu;
   for (int l = 0; l < H; ++l) {
@@ -973,8 +1014,8 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
     const double s = std::sin(M_PI * (double)k / (double)W);
     aN[k] = (float)(tm * 4.0 * s * s);
   }
-  if (upload(c, &c->aM, aM) != SR_OK) return bail(SR_ECUDA);
-  if (upload(c, &c->aN, aN) != SR_OK) return bail(SR_ECUDA);
+  if ((st = upload(c, &c->aM, aM)) != SR_OK) return bail(st);
+  if ((st = upload(c, &c->aN, aN)) != SR_OK) return bail(st);
   make_fft(c->fft_row, L, c->tw_row);
   make_fft(c->fft_col, H, c->tw_col);
   if (pow2) {
@@ -983,14 +1024,36 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
       std::vector<float2> tb = stage_twiddle_table(lens[q], loges[q]);
       const int want = srk::stage_twiddles(lens[q], loges[q]);
       if (want > 0 && (int)tb.size() != want) return bail(SR_ECUDA);
-      if (upload(c, &c->tws[q], tb) != SR_OK) return bail(SR_ECUDA);
+      if ((st = upload(c, &c->tws[q], tb)) != SR_OK) return bail(st);
     }
     c->fft_row.tws16 = c->tws[0];
     c->fft_row.tws8 = c->tws[1];
     c->fft_col.tws16 = c->tws[2];
     c->fft_col.tws8 = c->tws[3];
   }
-  CREATE_CUDA(cudaMalloc((void**)&c->err_dev, sizeof(int)));
+  {
+    // the recursion column pass (schedule 7): per column the root r in (0, 1)
+    // of tau mu r^2 - c r + tau mu = 0, c = 1 + 2 tau mu + tau mu 4 sin^2(pi k / W),
+    // and s = r / (tau mu W); column 0 carries k = 0 and k = W / 2
+    const double a = tm;
+    std::vector<double> rk(L + 1), sk(L + 1);
+    for (int k = 0; k <= L; ++k) {
+      const double sn = std::sin(M_PI * (double)k / (double)W);
+      const double cc = 1.0 + 2.0 * a + a * 4.0 * sn * sn;
+      rk[k] = 2.0 * a / (cc + std::sqrt(cc * cc - 4.0 * a * a));
+      sk[k] = rk[k] / (a * (double)W);
+    }
+    c->rec_R = srk::colsolve_rec_radius(rk[0]);
+    if (c->rec_R > 0) {
+      std::vector<float4> tab(L);
+      for (int k = 0; k < L; ++k)
+        tab[k] = make_float4((float)rk[k], (float)sk[k], (float)rk[k == 0 ? L : k],
+                             (float)sk[k == 0 ? L : k]);
+      if ((st = upload(c, &c->rec, tab)) != SR_OK) return bail(st);
+      CREATE_CUDA(dev_alloc((void**)&c->X2, (size_t)H * L * sizeof(float2)));
+    }
+  }
+  CREATE_CUDA(dev_alloc((void**)&c->err_dev, sizeof(int)));
   CREATE_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
   c->fft2 = pow2 && srk::fft2_supported(c->geo);
   if (!pow2) {
@@ -998,7 +1061,7 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
     std::vector<int> at(srk::kGenMaxRadix, -1);
     gen_plan(W / 2, c->plan_row, tab, at);
     gen_plan(H, c->plan_col, tab, at);
-    if (upload(c, &c->gen_tab, tab) != SR_OK) return bail(SR_ECUDA);
+    if ((st = upload(c, &c->gen_tab, tab)) != SR_OK) return bail(st);
     c->plan_row.tw = c->plan_row.roots = c->gen_tab;
     c->plan_col.tw = c->plan_col.roots = c->gen_tab;
     CREATE_CUDA(srk::configure_fftgen());
@@ -1327,6 +1390,18 @@ long long sr_kernel_launches(const sr_ctx* c, int reset) {
   const long long n = c->launches;
   if (reset) const_cast<sr_ctx*>(c)->launches = 0;
   return n;
+}
+
+sr_status sr_test_stall_waits(sr_ctx* c, long long cycles) {
+  if (!c || cycles < 0) return SR_EINVAL;
+  c->stall_cycles = cycles;
+  drop_graphs(c);  // the graphs hold the column pass's arguments by value
+  return SR_OK;
+}
+
+sr_status sr_test_fail_allocations(long long n) {
+  g_alloc_budget.store(n < 0 ? -1 : n);
+  return SR_OK;
 }
 
 sr_status sr_profile_enable(sr_ctx* c, int enable) {

@@ -121,6 +121,13 @@ struct ColArgs {
   const float* aN;         // tau mu 4 sin^2(pi k / N), k in [0, L]
   float2* X;
   int* err;                // device error flag (bounded waits), may be null
+  long long stall_cycles;  // failure-path tests only: > 0 makes the TMA column pass wait
+                           // this long on a barrier nothing arrives on, then time out
+  // column solve by recursions (k_colsolve_rec): per column k, (r, s) of the
+  // real part and (r, s) of the imaginary part; warm-up length; output buffer
+  const float4* rec;
+  int rec_R;
+  float2* Xout;
 };
 
 // Row pass, inverse: half spectrum to real rows; ADD mode adds psi_in.
@@ -214,6 +221,11 @@ cudaError_t launch_rowinv(const RowInvArgs& a, int mode, int nthreads, cudaStrea
 cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s);
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 int tile32_blocks(const Geo& geo);  // CTAs of the 32 x 32 tile kernels
+// Row-pass shape of the fixed power-of-two passes (k_rowfwd, k_rowinv) for an
+// H-row image with row transforms of complex length L on a device with nsm
+// SMs: *T rows per CTA and *NT threads, with T * L = 16 * NT.  Returns false
+// (and leaves the outputs alone) when no such shape exists.
+bool row_shape(int H, int L, int nsm, int* NT, int* T);
 cudaError_t launch_repulsion(const RepArgs& a, cudaStream_t s);
 cudaError_t launch_energy(const EnergyArgs& a, cudaStream_t s);
 cudaError_t launch_reduce(const double* partials, int nblocks, int ncomp, double* out,
@@ -258,6 +270,16 @@ cudaError_t launch_colsolve_tma(const ColArgs& a, const CUtensorMap& tm, int gri
                                 bool set_attr);
 int colsolve_tma_cb(int M);
 cudaError_t colsolve_tma_occupancy(int M, int* blocks_per_sm);  // after set_attr
+// Column solve by a forward and a backward first-order recursion per column
+// (sr_colrec.cu, column schedule 7): kRecRows rows per thread, kRecChunks
+// threads of one column per CTA row; reads a.X, writes a.Xout (a.X != a.Xout).
+constexpr int kRecRows = 32;
+constexpr int kRecChunks = 4;
+constexpr int kColRec = 7;
+// warm-up length for the slowest decay r_max (0 if none of the buckets suffices)
+int colsolve_rec_radius(double r_max);
+cudaError_t launch_colsolve_rec(const ColArgs& a, cudaStream_t s);
+
 int tile_blocks(const Geo& geo);   // CTAs of the 2-D tile kernels
 
 }  // namespace srk

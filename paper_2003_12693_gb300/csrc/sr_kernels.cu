@@ -1241,6 +1241,25 @@ static dim3 tile32_grid(const Geo& geo) { return dim3((geo.N + kT - 1) / kT, (ge
 
 int tile32_blocks(const Geo& geo) { return ((geo.N + kT - 1) / kT) * ((geo.M + kT - 1) / kT); }
 
+bool row_shape(int H, int L, int nsm, int* NT_out, int* T_out) {
+  if (H < 1 || L < 1) return false;
+  int NT = L >= 2048 ? 512 : 256;
+  int T = 16 * NT / L;
+  // smaller CTAs while the grid would not fill two CTAs per SM
+  while (NT > 64 && T > 1 && (H + T - 1) / T < 2 * nsm) {
+    NT /= 2;
+    T = 16 * NT / L;
+  }
+  if (T > H) {
+    T = H;
+    NT = T * L / 16;
+  }
+  if (T < 1 || NT < 1 || NT * 16 != T * L) return false;
+  *NT_out = NT;
+  *T_out = T;
+  return true;
+}
+
 cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s) {
   const dim3 g = tile32_grid(a.geo), b(kTBX, kTBY);
   const size_t sm = tile32_smem(a.mod.R);

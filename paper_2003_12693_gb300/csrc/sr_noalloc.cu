@@ -156,19 +156,15 @@ extern "C" sr_status sr_phi_step_noalloc(int H, int W, const sr_params* p, const
   for (int t = -m.R; t <= m.R; ++t)
     m.kw[t + m.R] = (float)std::exp(-(double)(t * t) / ((double)p->d * (double)p->d));
 
-  // the same row-pass shape as a context of this size uses
-  int NT = L >= 2048 ? 512 : 256;
-  int T = 16 * NT / L;
-  while (NT > 64 && T > 1 && (H + T - 1) / T < 2 * nsm) {
-    NT /= 2;
-    T = 16 * NT / L;
-  }
-  if (T > H) {
-    T = H;
-    NT = T * L / 16;
-  }
-  srk::Fft frow{L, log2i(L), log2i(L) / 4, 1 << (log2i(L) % 4), tw_row};
-  srk::Fft fcol{H, log2i(H), log2i(H) / 4, 1 << (log2i(H) % 4), tw_col};
+  // the same row-pass shape as a context of this size uses (one rule for both)
+  int NT = 0, T = 0;
+  if (!srk::row_shape(H, L, nsm, &NT, &T)) return SR_EUNSUPPORTED;
+  // Only the shared-memory passes of sr_kernels.cu (k_rowfwd, k_colsolve,
+  // k_rowinv) may run this plan: they read the flat twiddle table `tw` alone.
+  // The register passes of sr_fft.cu need the per-stage tables, which this
+  // entry point does not build, so they stay null here.
+  srk::Fft frow{L, log2i(L), log2i(L) / 4, 1 << (log2i(L) % 4), tw_row, nullptr, nullptr};
+  srk::Fft fcol{H, log2i(H), log2i(H) / 4, 1 << (log2i(H) % 4), tw_col, nullptr, nullptr};
 
   srk::RowFwdArgs fa{};
   fa.geo = geo;

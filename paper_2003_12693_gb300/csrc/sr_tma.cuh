@@ -49,18 +49,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the given phase; false after the cycle budget is spent.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the given phase; false after `limit` cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = kWaitCycles) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 
-// Record a timeout (first writer wins) and drain the barrier once more.
+// Record a timeout (first writer wins) and drain the barrier once more, with
+// the full bound whatever limit the failed wait had.
 __device__ __forceinline__ void on_timeout(uint64_t* bar, uint32_t parity, int* err) {
   if (err) atomicCAS(err, 0, kErrTimeout);
-  mbar_wait(bar, parity);
+  mbar_wait(bar, parity, kWaitCycles);
 }
 
 // 2-D tiled load of the box at (x, y) (x innermost, in elements) into dst.

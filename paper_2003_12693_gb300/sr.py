@@ -130,6 +130,10 @@ def lib() -> C.CDLL:
     L.sr_group_iterate.argtypes = [_P, C.c_int]
     L.sr_group_destroy.restype = None
     L.sr_group_destroy.argtypes = [_P]
+    L.sr_test_stall_waits.restype = st
+    L.sr_test_stall_waits.argtypes = [_P, C.c_longlong]
+    L.sr_test_fail_allocations.restype = st
+    L.sr_test_fail_allocations.argtypes = [C.c_longlong]
     _lib = L
     return L
 

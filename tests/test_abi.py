@@ -119,3 +119,9 @@ def test_network_layer_calls_reject_bad_shapes_before_touching_cuda(netmod):
     assert L.sr_net_forward(None, p, 1, p) == 1
     assert L.sr_net_kernel_launches(None, 0) == -1
     L.sr_net_destroy(None)
+
+
+def test_failure_hooks_validate_without_a_gpu(srmod):
+    L = srmod.lib()
+    assert L.sr_test_stall_waits(None, 10) == 1
+    assert L.sr_test_fail_allocations(-1) == 0

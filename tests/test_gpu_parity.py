@@ -52,7 +52,8 @@ def test_fft_solve_eigenfunctions():
     ctx.close()
 
 
-@pytest.mark.parametrize("shape", [(64, 32), (128, 256), (512, 512), (256, 2048), (4096, 64)])
+@pytest.mark.parametrize("shape", [(64, 32), (128, 256), (512, 512), (256, 2048), (4096, 64),
+                                   (1024, 256), (2048, 64)])
 def test_every_fft_schedule_matches_oracle(shape):
     """The autotuner may pick any schedule; each one must compute the same solve."""
     H, W = shape
@@ -68,7 +69,7 @@ def test_every_fft_schedule_matches_oracle(shape):
     tried = 0
     for vpt in (16, 8):
         for threads in (32, 64, 128, 256, 512):
-            for col in range(7):
+            for col in range(8):
                 try:
                     ctx.set_schedule(vpt, threads, col)
                 except sr.SRError as e:
@@ -81,6 +82,39 @@ def test_every_fft_schedule_matches_oracle(shape):
                 assert np.abs(step - ref_step).max() <= PHI_TOL
     assert tried >= 6
     report("schedules", shape=f"{H}x{W}", tried=tried, tuned=str(tuned))
+    ctx.close()
+
+
+@pytest.mark.parametrize("shape", [(16, 32), (48, 32), (64, 32), (256, 64), (2048, 32),
+                                   (4096, 32)])
+@pytest.mark.parametrize("tau,mu", [(0.1, 8.0), (1.0, 8.0), (0.01, 1.0)])
+def test_column_recursion_eigenfunctions(shape, tau, mu):
+    """Column schedule 7 replaces the column FFT by the forward and backward
+    recursions that factor the column operator.  Pure Fourier modes must come
+    out divided by their own symbol of Eq. (32), including the packed DC and
+    Nyquist column (b = 0, W/2), the Nyquist row (a = H/2) and conjugate
+    partners (a, H - a); tau mu = 8 needs the longest warm-up (r_0 = 0.70),
+    and H = 16 or 48 is shorter than the warm-up (it wraps)."""
+    H, W = shape
+    ctx = context(H, W, tau=tau, mu=mu)
+    tuned = ctx.get_schedule()
+    if tuned["row_threads"] == 0:
+        pytest.skip("sizes below W = 32 use the fixed passes")
+    ctx.set_schedule(tuned["row_values_per_thread"], tuned["row_threads"], 7)
+    i, j = np.mgrid[0:H, 0:W].astype(float)
+    modes = [(0, 0), (1, 0), (0, W // 2), (H // 2, W // 2), (H // 2, 0), (5, 3), (H - 5, 3),
+             (H - 1, W // 2 - 1), (3, W // 2), (H // 3, 1)]
+    for a, b in modes:
+        ph = 2 * np.pi * (a * i / H + b * j / W)
+        F = np.cos(ph) + 0.5 * np.sin(ph)
+        ref = oracle.solve(f32(F), tau, mu)
+        out = host(ctx.fft_solve(dev(F)))
+        assert np.abs(out - ref).max() < 2e-6, (a, b, np.abs(out - ref).max())
+    rng = np.random.default_rng(H + W)
+    rhs = f32(rng.normal(size=shape) * 3.0 + 1.0)
+    ref = oracle.solve(rhs, tau, mu)
+    out = host(ctx.fft_solve(dev(rhs)))
+    assert np.abs(out - ref).max() <= 4e-7 * math.log2(H * W) * np.abs(rhs).max()
     ctx.close()
 
 
@@ -249,18 +283,15 @@ def test_two_disks_run_invariants(two_disks_full):
     assert np.all((n == 0) | (np.abs(n - 1) < 1e-5))
     assert r["e1"][0] < r["e0"][0]
     assert np.array_equal(r["mask"], (r["gpu"][0] < 0).astype(np.float64))
-    # the FP32 and FP64 runs agree on the segmentation to within the oracle's
-    # own rounding sensitivity
+    # the segmentation against the oracle's, bounded by the oracle's own
+    # rounding sensitivity, is checked in test_gpu_whole_run.py; recorded here
     m_gpu = r["gpu"][0] < 0
     m_ref = r["ref"].phi < 0
     m_refT = r["refT"].phi.T < 0
-    d_gpu = int((m_gpu != m_ref).sum())
-    d_self = int((m_ref != m_refT).sum())
-    report("two_disks_200_iterations", mask_diff_gpu_vs_oracle=d_gpu,
-           mask_diff_oracle_vs_transposed_oracle=d_self,
+    report("two_disks_200_iterations", mask_diff_gpu_vs_oracle=int((m_gpu != m_ref).sum()),
+           mask_diff_oracle_vs_transposed_oracle=int((m_ref != m_refT).sum()),
            max_abs_dphi=np.abs(r["gpu"][0] - r["ref"].phi).max(),
            max_abs_dphi_oracle_vs_transposed=np.abs(r["ref"].phi - r["refT"].phi.T).max())
-    assert d_gpu <= max(3 * d_self, 100)
 
 
 def test_energy_matches_oracle(two_disks_full):

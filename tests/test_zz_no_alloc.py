@@ -4,10 +4,12 @@ Some hosts own all GPU memory through their own arena, capture streams into
 CUDA graphs in modes that forbid allocation, or run real-time loops that
 cannot take the device synchronisation of cudaMalloc / cudaFree.  This entry
 point serves them from a fixed device array inside the library.  The test
-calls it through the C-ABI twice in a row, with different sizes and windows,
-and checks each result against the context-based sr_phi_step within the
-tolerance the other tests use for phi (1e-4).  It is collected last so that a
-run stopping at the first failure has run every other test before it.
+calls it through the C-ABI several times in a row, with different sizes and
+windows (down to 16 x 16 and up to the array's limit of 512 x 512, and the
+ragged 512 x 16), and checks each result against the FP64 oracle's inner step
+and against the context-based sr_phi_step, within the tolerance the other
+tests use for phi (1e-4).  It is collected last so that a run stopping at the
+first failure has run every other test before it.
 """
 import ctypes as C
 
@@ -31,20 +33,27 @@ def srmod():
 
 
 def _inputs(H, W, seed):
+    """Seeded fields (phi, w1, w2, b1, b2, g), rounded to FP32 once so that the
+    oracle and the GPU start from the same numbers."""
     from paper_2003_12693_gb300 import synth
-    arrs = synth.random_state(H, W, seed=seed)
-    return [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda() for a in arrs]
+    return [np.ascontiguousarray(a, dtype=np.float32) for a in synth.random_state(H, W, seed=seed)]
 
 
-def test_noalloc_step_matches_context_step_on_two_calls(srmod):
+# (H, W, R, d, seed): the smallest side, the array's largest image with the
+# widest window (the largest shared-memory footprint of the fused row pass),
+# a ragged 512 x 16 (rows of complex length 8), and two middle shapes
+CASES = [(128, 128, 3, 3.0, 1), (16, 16, 0, 3.0, 3), (512, 512, 8, 8.0, 4),
+         (512, 16, 4, 4.0, 5), (256, 64, 4, 4.0, 2)]
+
+
+def test_noalloc_step_matches_oracle_and_context_step_on_calls_in_a_row(srmod):
+    import oracle
     lib = srmod.lib()
     stream = torch.cuda.current_stream()
-    for H, W, R, d, seed in [(128, 128, 3, 3.0, 1), (256, 64, 4, 4.0, 2)]:
-        phi, w1, w2, b1, b2, g = _inputs(H, W, seed)
+    for H, W, R, d, seed in CASES:
+        arrs = _inputs(H, W, seed)
+        phi, w1, w2, b1, b2, g = [torch.from_numpy(a).cuda() for a in arrs]
         params = srmod.make_params(win_radius=R, d=d)
-        ctx = srmod.Context(H, W, params)
-        ctx.set_g(g)
-        ref = ctx.phi_step(phi, w1, w2, b1, b2)
         out = torch.full_like(phi, float("nan"))
         st = lib.sr_phi_step_noalloc(H, W, C.byref(params),
                                      *[C.c_void_p(t.data_ptr())
@@ -52,8 +61,17 @@ def test_noalloc_step_matches_context_step_on_two_calls(srmod):
                                      C.c_void_p(stream.cuda_stream))
         assert st == srmod.SR_OK
         torch.cuda.synchronize()
-        err = float((out - ref).abs().max())
-        assert err <= PHI_TOL, (H, W, err)
+        got = out.cpu().numpy().astype(np.float64)
+        a64 = [a.astype(np.float64) for a in arrs]
+        ref = oracle.phi_step(a64[0], a64[5], a64[1], a64[2], a64[3], a64[4],
+                              oracle.Params(R=R, d=d))
+        err = float(np.abs(got - ref).max())
+        assert err <= PHI_TOL, (H, W, R, "vs oracle", err)
+        ctx = srmod.Context(H, W, params)
+        ctx.set_g(g)
+        alt = ctx.phi_step(phi, w1, w2, b1, b2)
+        err_ctx = float((out - alt).abs().max())
+        assert err_ctx <= PHI_TOL, (H, W, R, "vs sr_phi_step", err_ctx)
         ctx.close()
 
 
