@@ -193,6 +193,44 @@ sr_status sr_w_b_fixed_point(sr_ctx* ctx, const float* phi1, const float* w1_in,
  * sr_iterate; groups capture the setting when they are created. */
 sr_status sr_set_w_sweeps(sr_ctx* ctx, int sweeps);
 
+/* How the phi sub-problem of each inner step is solved: solver 0 = the FFT
+ * solve of Eqs. (31)-(33) (the default); 1 = additive operator splitting, the
+ * alternative named at the end of Sec. 4 in the form of Eqs. (19)-(20):
+ *     phi = 1/2 [ (I - 2 tau mu A_1)^{-1} F + (I - 2 tau mu A_2)^{-1} F ],
+ * A_1, A_2 the periodic second differences down the columns and along the
+ * rows; each factor is a cyclic tridiagonal solve with constant coefficients,
+ * factored once into a forward and a backward first-order recursion.  AOS is
+ * a first-order splitting of the exact solve, so its phi differs from the FFT
+ * solve's by O((tau mu)^2).  The first call with solver 1 allocates two image
+ * planes.  SR_EUNSUPPORTED if 2 tau mu is so large (above about 30) that the
+ * recursions' warm-up would exceed 128 places; graphs are rebuilt on the next
+ * sr_iterate. */
+sr_status sr_set_phi_solver(sr_ctx* ctx, int solver);
+
+/* Boundary reading.  neumann = 0 (the default): periodic differences, as the
+ * symbol of Eq. (32) diagonalises.  neumann = 1: Eq. (27) read literally with
+ * the homogeneous condition d phi / dn = 0 -- forward differences are zero
+ * across the last row and the last column, the backward divergence is minus
+ * the adjoint of that gradient, the Laplacian their product (the reflective
+ * 5-point stencil), and (1 - tau mu Lap) phi = F is solved in the basis of the
+ * type-II DCT, which diagonalises it with the symbol
+ * 1 + tau mu (4 sin^2(pi l / 2M) + 4 sin^2(pi k / 2N)).  On the GPU the row
+ * direction is transformed by the periodic FFT of each row's even extension
+ * (length 2W) and each column is solved with reflective ends by the
+ * recursions of column schedule 7 on its even extension; sr_fft_solve,
+ * sr_phi_step, sr_w_b_update, sr_set_phi (w^0 = grad phi^0), sr_energy and
+ * sr_iterate all follow the setting.  The window sum of Sec. 4 drops the
+ * terms outside the image either way.  SR_EUNSUPPORTED unless H and W are
+ * powers of two with W <= 2048, or together with the AOS solver or the
+ * iterated w variant.  The first call with neumann = 1 allocates about five
+ * image planes; graphs are rebuilt on the next sr_iterate. */
+sr_status sr_set_boundary(sr_ctx* ctx, int neumann);
+
+/* The AOS solve alone (device buffers, contiguous H x W, not aliased):
+ * out = 1/2 [ (I - 2 tau mu A_1)^{-1} rhs + (I - 2 tau mu A_2)^{-1} rhs ].
+ * The first call allocates two image planes in the context. */
+sr_status sr_aos_solve(sr_ctx* ctx, const float* rhs, float* out);
+
 /* Inner phi steps sr_iterate has run on this context (all outer iterations;
  * with inner_tol > 0 the count per iteration depends on the data); reset to
  * zero when reset != 0.  -1 for a NULL context. */

@@ -1,8 +1,8 @@
 """FP64 oracle of the AOS solve of the phi sub-problem (the alternative the
 paper mentions at the end of Sec. 4).
 
-TEST INFRASTRUCTURE ONLY (like the rest of ``oracle/``); the CUDA path does
-not implement this solver yet.
+TEST INFRASTRUCTURE ONLY (like the rest of ``oracle/``).  The CUDA path's
+version (sr_aos.cu) is checked against it by tests/test_gpu_aos.py.
 
 The semi-implicit step (1 - tau mu Lap) phi = F of Eqs. (30)-(33) is replaced
 by additive operator splitting in the form of Eqs. (19)-(20): with A_1, A_2

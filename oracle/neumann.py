@@ -1,8 +1,8 @@
 """FP64 oracle of the Neumann-boundary variant of the phi sub-problem.
 
 TEST INFRASTRUCTURE ONLY (like the rest of ``oracle/``): the tests may import
-it; the product path never does.  The CUDA path does not implement this
-variant yet.
+it; the product path never does.  The CUDA path's version (sr_set_boundary)
+is checked against it by tests/test_gpu_neumann.py.
 
 Eq. (27) states a Neumann-type boundary condition, while the symbol of
 Eq. (32) diagonalises the periodic Laplacian (the default reading).  This

@@ -86,6 +86,24 @@ struct sr_ctx {
   int w_sweeps = 0;
   long long inner_steps = 0;  // inner phi steps run by sr_iterate (all modes)
   float* wfx1 = nullptr;   // sweep ping-pong planes, allocated on first use
+  // phi sub-problem solver: 0 = FFT (Eqs. (31)-(33)), 1 = AOS (end of Sec. 4)
+  int phi_solver = 0;
+  float* aos_T1 = nullptr;  // AOS scratch planes, allocated on first use
+  float* aos_X2 = nullptr;
+  srk::AosArgs aos{};       // AOS constants (k, r, s, warm-up, powers of r)
+  // Neumann reading of Eq. (27) (sr_set_boundary): the solve runs on the even
+  // extension of each row (length 2W) and the reflected columns
+  srk::Geo geo2{};          // M x 2W, complex row length W
+  srk::Fft fft_row2{};
+  float2* tw_row2 = nullptr;
+  float2* tw_n2 = nullptr;
+  float2* tws2[2] = {nullptr, nullptr};  // stage twiddles of length W: 16 and 8 values
+  float* G2 = nullptr;      // M x 2W: the extended rows, then the inverse transform
+  float2* Xn = nullptr;     // M x W: their half spectrum
+  float2* Xn2 = nullptr;    // M x W: after the column solve
+  float4* rec2 = nullptr;   // per-column (r, s) of the reflected column solve
+  int rec2_R = 0;
+  int row2_T = 0, row2_threads = 0;
   float* wfx2 = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_kernels = 0;
@@ -599,6 +617,60 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
     st = run_kernel(c, SR_KCLASS_PREP, s, "k_prep", [&] { return srk::launch_prep(pa, s); });
     if (st != SR_OK) return st;
     src = c->G;
+    if (c->phi_solver == 1) {
+      srk::AosArgs aa = c->aos;
+      aa.G = c->G;
+      aa.psi = psi_in;
+      aa.phi = psi_out;
+      aa.T1 = c->aos_T1;
+      aa.X2 = c->aos_X2;
+      // the AOS line solves count as the column pass and the row pass
+      c->launches += 1;
+      return run_kernel(c, SR_KCLASS_COLSOLVE, s, "k_aos", [&] { return srk::launch_aos(aa, s, false); });
+    }
+  }
+  if (c->geo.neumann) {
+    // (1 - tau mu Lap_N) delta = src with the reflective Laplacian: the even
+    // extension of each row diagonalises the row direction with the periodic
+    // FFT of length 2W (its spectrum is the DCT-II's, rotated), and each
+    // column is solved with reflective ends by the recursions on its even
+    // extension of length 2M; the first W columns of the result are kept
+    st = run_kernel(c, SR_KCLASS_ROWFFT, s, "k_mirror_rows",
+                    [&] { return srk::launch_mirror_rows(src, c->G2, c->geo, s); });
+    if (st != SR_OK) return st;
+    srk::RowFwdArgs na{};
+    na.geo = c->geo2;
+    na.fft = c->fft_row2;
+    na.twN = c->tw_n2;
+    na.src = c->G2;
+    na.X = c->Xn;
+    na.T = c->row2_T;
+    st = run_kernel(c, SR_KCLASS_ROWFFT, s, "k_rowfft",
+                    [&] { return srk::launch_rowfft2(na, 4, c->row2_threads, s, false); });
+    if (st != SR_OK) return st;
+    srk::ColArgs nc{};
+    nc.geo = c->geo2;
+    nc.X = c->Xn;
+    nc.Xout = c->Xn2;
+    nc.rec = c->rec2;
+    nc.rec_R = c->rec2_R;
+    nc.mirror = 1;
+    st = run_kernel(c, SR_KCLASS_COLSOLVE, s, "k_colsolve_rec",
+                    [&] { return srk::launch_colsolve_rec(nc, s); });
+    if (st != SR_OK) return st;
+    srk::RowInvArgs ni{};
+    ni.geo = c->geo2;
+    ni.fft = c->fft_row2;
+    ni.twN = c->tw_n2;
+    ni.X = c->Xn2;
+    ni.out = c->G2;
+    ni.T = c->row2_T;
+    st = run_kernel(c, SR_KCLASS_ROWIFFT, s, "k_rowifft",
+                    [&] { return srk::launch_rowifft2(ni, false, 4, c->row2_threads, s, false); });
+    if (st != SR_OK) return st;
+    return run_kernel(c, SR_KCLASS_ROWIFFT, s, "k_add_half", [&] {
+      return srk::launch_add_half(load_src ? nullptr : psi_in, c->G2, psi_out, c->geo, s);
+    });
   }
   srk::RowFwdArgs fa{};
   fa.geo = c->geo;
@@ -896,7 +968,8 @@ void sr_destroy(sr_ctx* c) {
                   c->g, c->tmp1, c->tmp2, c->stage, c->G, c->divE, c->mask_dev, c->X, c->tw_row, c->tw_col,
                   c->tw_n, c->aM, c->aN, c->partials, c->red, c->err_dev, c->gen_tab,
                   c->tws[0], c->tws[1], c->tws[2], c->tws[3], c->wfx1, c->wfx2,
-                  c->X2, c->rec};
+                  c->X2, c->rec, c->aos_T1, c->aos_X2, c->tw_row2, c->tw_n2,
+                  c->tws2[0], c->tws2[1], c->G2, c->Xn, c->Xn2, c->rec2};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -1051,6 +1124,23 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
                              (float)sk[k == 0 ? L : k]);
       if ((st = upload(c, &c->rec, tab)) != SR_OK) return bail(st);
       CREATE_CUDA(dev_alloc((void**)&c->X2, (size_t)H * L * sizeof(float2)));
+    }
+  }
+  {
+    // AOS constants: k = 2 tau mu, r the root in (0, 1) of k r^2 - (1 + 2k) r + k = 0
+    const double k = 2.0 * tm, cc = 1.0 + 2.0 * k;
+    const double r = 2.0 * k / (cc + std::sqrt(cc * cc - 4.0 * k * k));
+    c->aos.geo = c->geo;
+    c->aos.k = (float)k;
+    c->aos.tm = (float)tm;
+    c->aos.r = (float)r;
+    c->aos.s = (float)(r / k);
+    c->aos.R = srk::aos_radius(r);
+    c->aos.warm_blocks = (c->aos.R + 31) / 32 + 1;
+    double pw = 1.0;
+    for (int m = 0; m <= 32; ++m) {
+      c->aos.pw[m] = (float)pw;
+      pw *= r;
     }
   }
   CREATE_CUDA(dev_alloc((void**)&c->err_dev, sizeof(int)));
@@ -1353,6 +1443,8 @@ long long sr_inner_steps(sr_ctx* c, int reset) {
 sr_status sr_set_w_sweeps(sr_ctx* c, int sweeps) {
   if (!c) return SR_EINVAL;
   if (sweeps < 0 || sweeps > 64) return fail(c, SR_EINVAL, "sweeps must be in [0, 64]");
+  if (sweeps > 0 && c->geo.neumann)
+    return fail(c, SR_EUNSUPPORTED, "the iterated w variant is built for the periodic reading");
   if (sweeps > 0) {
     sr_status st = alloc_wfix(c);
     if (st != SR_OK) return st;
@@ -1390,6 +1482,109 @@ long long sr_kernel_launches(const sr_ctx* c, int reset) {
   const long long n = c->launches;
   if (reset) const_cast<sr_ctx*>(c)->launches = 0;
   return n;
+}
+
+sr_status sr_set_phi_solver(sr_ctx* c, int solver) {
+  if (!c || solver < 0 || solver > 1) return SR_EINVAL;
+  if (solver == 1 && c->geo.neumann)
+    return fail(c, SR_EUNSUPPORTED, "the AOS solve is built for the periodic reading");
+  if (solver == 1) {
+    if (c->aos.R <= 0)
+      return fail(c, SR_EUNSUPPORTED, "2 tau mu too large for the AOS recursions' warm-up");
+    for (float** pl : {&c->aos_T1, &c->aos_X2}) {
+      if (*pl) continue;
+      const cudaError_t e = dev_alloc((void**)pl, sizeof(float) * (size_t)c->H * c->W);
+      if (e == cudaErrorMemoryAllocation) return fail(c, SR_ENOMEM, "device allocation failed");
+      SR_CUDA(c, e);
+    }
+    SR_CUDA(c, srk::launch_aos(c->aos, nullptr, true));
+  }
+  c->phi_solver = solver;
+  drop_graphs(c);
+  return SR_OK;
+}
+
+sr_status sr_set_boundary(sr_ctx* c, int neumann) {
+  if (!c || neumann < 0 || neumann > 1) return SR_EINVAL;
+  if (neumann && (!is_pow2(c->H) || !is_pow2(c->W) || c->W > 2048))
+    return fail(c, SR_EUNSUPPORTED, "the Neumann solve needs power-of-two sides with W <= 2048");
+  if (neumann && (c->phi_solver != 0 || c->w_sweeps != 0))
+    return fail(c, SR_EUNSUPPORTED, "the Neumann reading is built for the FFT solve and Eqs. (41)-(42)");
+  if (neumann && !c->G2) {
+    const int H = c->H, W = c->W;
+    const double a = (double)c->prm.tau * (double)c->prm.mu;
+    c->geo2 = srk::Geo{H, 2 * W, W, ilog2(2 * W), 0};
+    sr_status st;
+    if ((st = upload(c, &c->tw_row2, twiddles(W, W))) != SR_OK) return st;
+    if ((st = upload(c, &c->tw_n2, twiddles(W, 2 * W))) != SR_OK) return st;
+    const int loges[2] = {4, 3};
+    for (int q = 0; q < 2; ++q) {
+      std::vector<float2> tb = stage_twiddle_table(W, loges[q]);
+      if ((st = upload(c, &c->tws2[q], tb)) != SR_OK) return st;
+    }
+    make_fft(c->fft_row2, W, c->tw_row2);
+    c->fft_row2.tws16 = c->tws2[0];
+    c->fft_row2.tws8 = c->tws2[1];
+    // column k of the extended rows' half spectrum holds DCT index k (and the
+    // packed column 0 holds W in its imaginary part): c = 1 + 2a + a 4 sin^2(pi k / (2W))
+    std::vector<double> rk(W + 1), sk(W + 1);
+    for (int k = 0; k <= W; ++k) {
+      const double sn = std::sin(M_PI * (double)k / (2.0 * (double)W));
+      const double cc = 1.0 + 2.0 * a + a * 4.0 * sn * sn;
+      rk[k] = 2.0 * a / (cc + std::sqrt(cc * cc - 4.0 * a * a));
+      sk[k] = rk[k] / (a * 2.0 * (double)W);
+    }
+    c->rec2_R = srk::colsolve_rec_radius(rk[0]);
+    if (c->rec2_R <= 0) return fail(c, SR_EUNSUPPORTED, "tau mu too large for the recursions' warm-up");
+    std::vector<float4> tab(W);
+    for (int k = 0; k < W; ++k)
+      tab[k] = make_float4((float)rk[k], (float)sk[k], (float)rk[k == 0 ? W : k],
+                           (float)sk[k == 0 ? W : k]);
+    if ((st = upload(c, &c->rec2, tab)) != SR_OK) return st;
+    const size_t P = (size_t)H * W;
+    for (void** pl : {(void**)&c->G2, (void**)&c->Xn, (void**)&c->Xn2}) {
+      const cudaError_t e = dev_alloc(pl, 2 * P * sizeof(float));
+      if (e == cudaErrorMemoryAllocation) return fail(c, SR_ENOMEM, "device allocation failed");
+      SR_CUDA(c, e);
+    }
+    // row passes of length W: 16 values per thread, about 2048 values per CTA
+    c->row2_T = std::max(1, std::min(H, 2048 / W));
+    c->row2_threads = c->row2_T * W / 16;
+    srk::RowFwdArgs fa{};
+    fa.geo = c->geo2;
+    fa.T = c->row2_T;
+    srk::RowInvArgs ia{};
+    ia.geo = c->geo2;
+    ia.T = c->row2_T;
+    SR_CUDA(c, srk::launch_rowfft2(fa, 4, c->row2_threads, nullptr, true));
+    SR_CUDA(c, srk::launch_rowifft2(ia, false, 4, c->row2_threads, nullptr, true));
+  }
+  c->geo.neumann = neumann;
+  drop_graphs(c);
+  return SR_OK;
+}
+
+sr_status sr_aos_solve(sr_ctx* c, const float* rhs, float* out) {
+  if (!c) return SR_EINVAL;
+  if (!rhs || !out) return fail(c, SR_EINVAL, "NULL buffer");
+  if (rhs == out) return fail(c, SR_EINVAL, "rhs and out must not alias");
+  if (c->aos.R <= 0)
+    return fail(c, SR_EUNSUPPORTED, "2 tau mu too large for the AOS recursions' warm-up");
+  if (c->phi_solver != 1) {  // allocates the scratch plane and sets the kernel attributes
+    const int keep = c->phi_solver;
+    sr_status st = sr_set_phi_solver(c, 1);
+    if (st != SR_OK) return st;
+    c->phi_solver = keep;
+  }
+  srk::AosArgs aa = c->aos;
+  aa.G = rhs;
+  aa.psi = nullptr;
+  aa.phi = out;
+  aa.T1 = c->aos_T1;
+  aa.X2 = c->aos_X2;
+  c->launches += 2;
+  SR_CUDA(c, srk::launch_aos(aa, c->stream, false));
+  return SR_OK;
 }
 
 sr_status sr_test_stall_waits(sr_ctx* c, long long cycles) {

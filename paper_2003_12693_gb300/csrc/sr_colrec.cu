@@ -31,10 +31,15 @@
 
 namespace srk {
 
-template <int R>
+// MIRROR: the column is read as its even extension of length 2M (rows
+// 0..M-1, then M-1..0), whose periodic solve is the solve with reflective
+// ends (the Neumann reading of Eq. (27)); only rows 0..M-1 are written.
+template <int R, bool MIRROR>
 __global__ void __launch_bounds__(32 * kRecChunks) k_colsolve_rec(const ColArgs a) {
   constexpr int TR = kRecRows;
   const int L = a.geo.L, M = a.geo.M;
+  const int Mv = MIRROR ? 2 * M : M;  // length of the periodic sequence
+  auto at = [M](int n) { return (MIRROR && n >= M) ? 2 * M - 1 - n : n; };
   const int k = blockIdx.x * 32 + threadIdx.x;
   const int i0 = (blockIdx.y * kRecChunks + threadIdx.y) * TR;
   pdl_wait();
@@ -45,21 +50,21 @@ __global__ void __launch_bounds__(32 * kRecChunks) k_colsolve_rec(const ColArgs 
   const float2* __restrict__ src = a.X + k;
   float2* __restrict__ dst = a.Xout + k;
   int row = i0 - R;
-  while (row < 0) row += M;
+  while (row < 0) row += Mv;
   // forward recursion: R rows of warm-up, then the run and the R rows after it
   float ux = 0.f, uy = 0.f;
 #pragma unroll
   for (int j = 0; j < R; ++j) {
-    const float2 x = src[(size_t)row * L];
+    const float2 x = src[(size_t)at(row) * L];
     ux = fmaf(rr, ux, x.x);
     uy = fmaf(ri, uy, x.y);
-    row = row + 1 == M ? 0 : row + 1;
+    row = row + 1 == Mv ? 0 : row + 1;
   }
   float2 b[TR + R];
 #pragma unroll
   for (int j = 0; j < TR + R; ++j) {
-    b[j] = src[(size_t)row * L];
-    row = row + 1 == M ? 0 : row + 1;
+    b[j] = src[(size_t)at(row) * L];
+    row = row + 1 == Mv ? 0 : row + 1;
   }
 #pragma unroll
   for (int j = 0; j < TR + R; ++j) {
@@ -102,13 +107,45 @@ cudaError_t launch_colsolve_rec(const ColArgs& a, cudaStream_t s) {
   const dim3 block(32, kRecChunks);
   const dim3 grid((a.geo.L + 31) / 32, (a.geo.M + kRecRows * kRecChunks - 1) / (kRecRows * kRecChunks));
   switch (a.rec_R) {
-#define SR_REC(r) \
-  case r: return launch_k(k_colsolve_rec<r>, grid, block, 0, s, a);
+#define SR_REC(r)                                                                \
+  case r:                                                                        \
+    return a.mirror ? launch_k(k_colsolve_rec<r, true>, grid, block, 0, s, a)    \
+                    : launch_k(k_colsolve_rec<r, false>, grid, block, 0, s, a);
     SR_REC(8) SR_REC(12) SR_REC(16) SR_REC(20) SR_REC(24) SR_REC(32) SR_REC(40) SR_REC(48)
     SR_REC(64)
 #undef SR_REC
   }
   return cudaErrorInvalidValue;
+}
+
+__global__ void k_mirror_rows(const float* __restrict__ in, float* __restrict__ out, Geo geo) {
+  const int i = blockIdx.y, N = geo.N;
+  pdl_wait();
+  pdl_trigger();
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < 2 * N; j += gridDim.x * blockDim.x)
+    out[(size_t)i * 2 * N + j] = in[(size_t)i * N + (j < N ? j : 2 * N - 1 - j)];
+}
+
+__global__ void k_add_half(const float* __restrict__ psi, const float* __restrict__ T,
+                           float* __restrict__ out, Geo geo) {
+  const int i = blockIdx.y, N = geo.N;
+  pdl_wait();
+  pdl_trigger();
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+    const size_t o = (size_t)i * N + j;
+    out[o] = (psi ? psi[o] : 0.f) + T[(size_t)i * 2 * N + j];
+  }
+}
+
+cudaError_t launch_mirror_rows(const float* in, float* out, const Geo& geo, cudaStream_t s) {
+  const int bx = (2 * geo.N + 255) / 256;
+  return launch_k(k_mirror_rows, dim3(bx, geo.M), dim3(256), 0, s, in, out, geo);
+}
+
+cudaError_t launch_add_half(const float* psi, const float* T, float* out, const Geo& geo,
+                            cudaStream_t s) {
+  const int bx = (geo.N + 255) / 256;
+  return launch_k(k_add_half, dim3(bx, geo.M), dim3(256), 0, s, psi, T, out, geo);
 }
 
 }  // namespace srk

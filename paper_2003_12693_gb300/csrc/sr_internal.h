@@ -75,6 +75,8 @@ struct Geo {
   int M, N;     // rows, columns
   int L;        // N / 2: complex length of a row transform
   int logN;
+  int neumann;  // 1: Eq. (27) read literally (no difference across the last row /
+                // column, reflective Laplacian); 0: periodic (the default reading)
 };
 
 // Row pass, forward: build the right-hand side of one inner step (or load it)
@@ -128,6 +130,7 @@ struct ColArgs {
   const float4* rec;
   int rec_R;
   float2* Xout;
+  int mirror;              // 1: the column is the even extension of length 2M (Neumann)
 };
 
 // Row pass, inverse: half spectrum to real rows; ADD mode adds psi_in.
@@ -279,6 +282,34 @@ constexpr int kColRec = 7;
 // warm-up length for the slowest decay r_max (0 if none of the buckets suffices)
 int colsolve_rec_radius(double r_max);
 cudaError_t launch_colsolve_rec(const ColArgs& a, cudaStream_t s);
+// Neumann solve helpers: the even extension of each row (out is M x 2N) and
+// out = psi + T[:, :N] (T is M x 2N; psi may be null)
+cudaError_t launch_mirror_rows(const float* in, float* out, const Geo& geo, cudaStream_t s);
+cudaError_t launch_add_half(const float* psi, const float* T, float* out, const Geo& geo,
+                            cudaStream_t s);
+
+// AOS solve of the phi sub-problem (sr_aos.cu): phi = psi + 1/2 [T1 + T2],
+// T1 = (I - k A_1)^{-1} (G + tau mu (A_1 - A_2) psi), T2 the same with A_1 and
+// A_2 swapped, k = 2 tau mu, A_1 / A_2 the periodic second differences down
+// the columns / along the rows.  psi may be null (then
+// phi = 1/2 [(I - k A_1)^{-1} G + (I - k A_2)^{-1} G]).
+constexpr int kAosRowWarps = 4;
+struct AosArgs {
+  Geo geo;
+  const float* G;
+  const float* psi;
+  float* T1;          // H x W scratch: the column-direction solve
+  float* X2;          // H x W scratch: the row-direction input
+  float* phi;         // output; may alias psi (the row pass reads psi only at the element it writes)
+  float k;            // 2 tau mu
+  float tm;           // tau mu
+  float r, s;         // factor root and scale r / k
+  int R;              // warm-up of the column recursion (template bucket)
+  int warm_blocks;    // warm-up blocks of 32 of the row recursion
+  float pw[33];       // r^m, m = 0..32
+};
+int aos_radius(double r);  // 0 if no bucket suffices
+cudaError_t launch_aos(const AosArgs& a, cudaStream_t s, bool set_attr);
 
 int tile_blocks(const Geo& geo);   // CTAs of the 2-D tile kernels
 

@@ -888,10 +888,25 @@ __global__ void __launch_bounds__(kTN, 4) k_prep(const PrepArgs a) {
       const float sel = __shfl_up_sync(0xffffffffu, E2.w, 1);
       if (!q.up_g) E1u = se;
       if (!q.lf_g) e2l = sel;
+      if (a.geo.neumann) {
+        // div = -(grad)^T for the gradient with no difference across the
+        // last row / column: e1 of the last row and e2 of the last column
+        // drop out, and nothing comes from before the first row / column
+        if (q.i == 0) E1u = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q.i == a.geo.M - 1) E1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q.j == 0) e2l = 0.f;
+        if (q.j + 4 == N) E2.w = 0.f;
+      }
       Dv = make_float4(div_e(E1.x, E1u.x, E2.x, e2l), div_e(E1.y, E1u.y, E2.y, E2.x),
                        div_e(E1.z, E1u.z, E2.z, E2.y), div_e(E1.w, E1u.w, E2.w, E2.z));
       if (DIV == kDivStore && q.live) st4(a.D + q.o, Dv);
     }
+  }
+  if (a.geo.neumann) {  // reflective Laplacian: the missing neighbour mirrors the pixel
+    if (q.i == 0) UP = X;
+    if (q.i == a.geo.M - 1) DN = X;
+    if (q.j == 0) LF = X.x;
+    if (q.j + 4 == N) RT = X.w;
   }
   // the stencil part of the force first, so that only psi and the force stay
   // live across the narrow-band work
@@ -948,6 +963,10 @@ __global__ void __launch_bounds__(kTN, 4) k_wb_update(const WBArgs a) {
     const float sr = __shfl_down_sync(0xffffffffu, X.x, 1);
     if (!q.dn_g) DN = sd;
     if (!q.rt_g) RT = sr;
+  }
+  if (a.geo.neumann) {  // no difference across the last row / column
+    if (q.i == a.geo.M - 1) DN = X;
+    if (q.j + 4 == N) RT = X.w;
   }
   float v1[4], v2[4];
   float4 G4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1024,8 +1043,8 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_energy(const EnergyArgs a) {
   const Model& m = a.mod;
   auto grad = [&](int i, int j, float& d1, float& d2) {
     const float x = a.phi[(size_t)i * N + j];
-    d1 = a.phi[(size_t)(i == M - 1 ? 0 : i + 1) * N + j] - x;
-    d2 = a.phi[(size_t)i * N + (j == N - 1 ? 0 : j + 1)] - x;
+    d1 = (a.geo.neumann && i == M - 1) ? 0.f : a.phi[(size_t)(i == M - 1 ? 0 : i + 1) * N + j] - x;
+    d2 = (a.geo.neumann && j == N - 1) ? 0.f : a.phi[(size_t)i * N + (j == N - 1 ? 0 : j + 1)] - x;
   };
   float v1, v2;
   tile_window_sum(sm, a.geo, m, i0, j0,
@@ -1083,8 +1102,12 @@ __global__ void k_init_wb(const float* __restrict__ phi, float* __restrict__ w1,
   if (j >= geo.N) return;
   const size_t o = (size_t)i * geo.N + j;
   const float x = phi[o];
-  const float d1 = phi[(size_t)(i == geo.M - 1 ? 0 : i + 1) * geo.N + j] - x;
-  const float d2 = phi[(size_t)i * geo.N + (j == geo.N - 1 ? 0 : j + 1)] - x;
+  float d1 = phi[(size_t)(i == geo.M - 1 ? 0 : i + 1) * geo.N + j] - x;
+  float d2 = phi[(size_t)i * geo.N + (j == geo.N - 1 ? 0 : j + 1)] - x;
+  if (geo.neumann) {
+    if (i == geo.M - 1) d1 = 0.f;
+    if (j == geo.N - 1) d2 = 0.f;
+  }
   w1[o] = d1;
   w2[o] = d2;
   e1[o] = -d1;

@@ -130,6 +130,12 @@ def lib() -> C.CDLL:
     L.sr_group_iterate.argtypes = [_P, C.c_int]
     L.sr_group_destroy.restype = None
     L.sr_group_destroy.argtypes = [_P]
+    L.sr_set_phi_solver.restype = st
+    L.sr_set_phi_solver.argtypes = [_P, C.c_int]
+    L.sr_set_boundary.restype = st
+    L.sr_set_boundary.argtypes = [_P, C.c_int]
+    L.sr_aos_solve.restype = st
+    L.sr_aos_solve.argtypes = [_P, _P, _P]
     L.sr_test_stall_waits.restype = st
     L.sr_test_stall_waits.argtypes = [_P, C.c_longlong]
     L.sr_test_fail_allocations.restype = st
@@ -271,6 +277,19 @@ class Context:
         out = self._new() if out is None else out
         _check(lib().sr_fft_solve(self.handle, self._dev(rhs), self._dev(out)), self)
         return out
+
+    def aos_solve(self, rhs, out: torch.Tensor | None = None):
+        out = self._new() if out is None else out
+        _check(lib().sr_aos_solve(self.handle, self._dev(rhs), self._dev(out)), self)
+        return out
+
+    def set_boundary(self, boundary: str):
+        """'periodic' (the default reading) or 'neumann' (Eq. (27) literally)."""
+        _check(lib().sr_set_boundary(self.handle, {"periodic": 0, "neumann": 1}[boundary]), self)
+
+    def set_phi_solver(self, solver: str):
+        """'fft' (Eqs. (31)-(33), default) or 'aos' (Eqs. (19)-(20) form)."""
+        _check(lib().sr_set_phi_solver(self.handle, {"fft": 0, "aos": 1}[solver]), self)
 
     def w_b_update(self, phi1, w1, w2, b1, b2):
         outs = [self._new() for _ in range(4)]
