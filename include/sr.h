@@ -78,9 +78,11 @@ sr_status sr_params_default(sr_params* p);
  * Supported sizes: H and W multiples of 16 in [16, 4096] such that H and
  * W/2 have no prime factor above 31 (SR_EUNSUPPORTED otherwise).  Powers of
  * two use register-resident FFT passes with an autotuned schedule, other
- * sides (e.g. 96, 160, 224) mixed-radix shared-memory passes with radices 16,
- * 8, 4, 2, 3, 5 and direct DFTs of the other primes.  cuda_stream is a
- * cudaStream_t (may be 0). */
+ * sides (e.g. 96, 160, 224) mixed-radix shared-memory row passes with radices
+ * 16, 8, 4, 2, 3, 5 and direct DFTs of the other primes, and the column solve
+ * by the recursions of column schedule 7 (the environment variable
+ * SR_GEN_FFT_COLS=1 at sr_create selects a mixed-radix column FFT instead).
+ * cuda_stream is a cudaStream_t (may be 0). */
 sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx** out);
 
 /* Release everything the context owns.  NULL is ignored. */
@@ -317,6 +319,10 @@ long long sr_kernel_launches(const sr_ctx* ctx, int reset);
 #define SR_KCLASS_PREP 5         /* repulsion window sum + right-hand side */
 #define SR_KCLASS_COUNT 6
 sr_status sr_profile_enable(sr_ctx* ctx, int enable);
+/* Microseconds the profiling mode's event pair adds to a kernel's measured
+ * time: the median over 65 event pairs around an empty kernel launched the
+ * same way on the context's stream.  Synchronises. */
+sr_status sr_profile_overhead(sr_ctx* ctx, double* us);
 sr_status sr_kernel_times(sr_ctx* ctx, int kclass, double* total_ms, long long* launches);
 
 /* ---- Failure-path test hooks (not needed in normal use) ----

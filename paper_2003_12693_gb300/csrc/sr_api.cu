@@ -42,6 +42,7 @@ struct sr_ctx {
   bool fftgen = false;  // mixed-radix passes (sr_fftgen.cu): a side is not a power of two
   srk::GenPlan plan_row{}, plan_col{};
   bool gen_batched = false;  // member of a group: launch shapes for many images at once
+  bool gen_fft_cols = false; // mixed-radix sides: column FFT instead of the recursions (SR_GEN_FFT_COLS=1)
   float2* gen_tab = nullptr;  // stage twiddles and roots of both plans
   sr_schedule sched{};  // schedule of the fft2 passes
   CUtensorMap tm_X{};   // X as a float32 matrix, boxes for the TMA column pass
@@ -250,36 +251,8 @@ void make_fft(Fft& f, int L, const float2* tw) {
   f.tail = 1 << (f.logL % 4);
 }
 
-std::vector<float2> twiddles(int n, int len) {
-  // exp(-2 pi i q / len), q in [0, n), computed in double and rounded once
-  std::vector<float2> t(n);
-  for (int q = 0; q < n; ++q) {
-    const double a = -2.0 * M_PI * (double)q / (double)len;
-    t[q] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
-  return t;
-}
-
-// Stage twiddles of the register FFT for a length-len transform with 2^logE
-// values per thread: stage q >= 1 has Ns = 2^(logE q) and radix 2^logE (the
-// last stage 2^(log2(len) mod logE) if that is not 1); its entries
-// exp(-2 pi i k t / (Ns R)) are stored at [t - 1][k].
-std::vector<float2> stage_twiddle_table(int len, int logE) {
-  const int logL = ilog2(len);
-  const int nst = (logL + logE - 1) / logE;
-  std::vector<float2> v;
-  for (int q = 1; q < nst; ++q) {
-    const int logR = q < logL / logE ? logE : logL % logE;
-    const int R = 1 << logR, Ns = 1 << (logE * q);
-    for (int t = 1; t < R; ++t)
-      for (int k = 0; k < Ns; ++k) {
-        const double ang = -2.0 * M_PI * (double)k * (double)t / ((double)Ns * (double)R);
-        v.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
-      }
-  }
-  if (v.empty()) v.push_back(make_float2(1.f, 0.f));  // keep the allocation non-empty
-  return v;
-}
+std::vector<float2> twiddles(int n, int len) { return srk::twiddle_table(n, len); }
+using srk::stage_twiddle_table;
 
 // Failure injection for tests (sr_test_fail_allocations): the number of
 // device or pinned-host allocations the library may still make before the
@@ -699,8 +672,12 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
   ca.rec = c->rec;
   ca.rec_R = c->rec_R;
   ca.Xout = c->X2;
-  const bool col_rec = c->fft2 && c->sched.col_schedule == srk::kColRec;
+  // the recursion column pass: chosen by the autotuner for power-of-two sides,
+  // always used for other sides (it needs no FFT plan of the column length)
+  const bool col_rec = c->rec_R > 0 && ((c->fft2 && c->sched.col_schedule == srk::kColRec) ||
+                                        (c->fftgen && !c->gen_fft_cols));
   st = run_kernel(c, SR_KCLASS_COLSOLVE, s, "k_colsolve", [&] {
+    if (col_rec) return srk::launch_colsolve_rec(ca, s);
     if (c->fftgen) return srk::launch_colsolve_gen(ca, c->plan_col, c->gen_batched, s);
     if (!c->fft2) return srk::launch_colsolve(ca, s);
     if (col_rec) return srk::launch_colsolve_rec(ca, s);
@@ -1156,6 +1133,8 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
     c->plan_col.tw = c->plan_col.roots = c->gen_tab;
     CREATE_CUDA(srk::configure_fftgen());
     c->fftgen = true;
+    const char* env = std::getenv("SR_GEN_FFT_COLS");
+    c->gen_fft_cols = env && env[0] == '1';
   }
   if (c->fft2) {
     const int cb = srk::colsolve_tma_cb(H);
@@ -1602,6 +1581,29 @@ sr_status sr_test_fail_allocations(long long n) {
 sr_status sr_profile_enable(sr_ctx* c, int enable) {
   if (!c) return SR_EINVAL;
   c->profile = enable != 0;
+  return SR_OK;
+}
+
+sr_status sr_profile_overhead(sr_ctx* c, double* us) {
+  if (!c || !us) return SR_EINVAL;
+  // the event pair of run_kernel around an empty kernel, 65 times: the median
+  const int reps = 65;
+  std::vector<cudaEvent_t> ev(2 * reps, nullptr);
+  for (auto& e : ev) SR_CUDA(c, cudaEventCreate(&e));
+  cudaError_t err = cudaSuccess;
+  for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+    err = cudaEventRecord(ev[2 * r], c->stream);
+    if (err == cudaSuccess) err = srk::launch_empty(c->stream);
+    if (err == cudaSuccess) err = cudaEventRecord(ev[2 * r + 1], c->stream);
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+  std::vector<float> ms(reps, 0.f);
+  for (int r = 0; r < reps && err == cudaSuccess; ++r)
+    err = cudaEventElapsedTime(&ms[r], ev[2 * r], ev[2 * r + 1]);
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (err != cudaSuccess) return cuda_fail(c, err, "profiling overhead");
+  std::nth_element(ms.begin(), ms.begin() + reps / 2, ms.end());
+  *us = 1000.0 * ms[reps / 2];
   return SR_OK;
 }
 

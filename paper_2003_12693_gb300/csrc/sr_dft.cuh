@@ -1,5 +1,6 @@
-// Small complex DFTs held in registers, used by the FFT passes of the phi
-// solve (Eqs. (31)-(33)).  Every dftN<INV> takes x[0..N) in natural order and
+// Small complex DFTs held in registers, and the register-resident Stockham
+// stages built from them, used by the FFT passes of the phi solve (Eqs.
+// (31)-(33)) in 2-D and in 3-D.  Every dftN<INV> takes x[0..N) in natural order and
 // leaves its DFT in natural order: X[k] = sum_n x[n] exp(-+2 pi i n k / N),
 // the minus sign forward (INV = false), plus for the inverse (unnormalised).
 #pragma once
@@ -87,6 +88,94 @@ __device__ __forceinline__ void dft(float2* x) {
   else if constexpr (R == 8) dft8<INV>(x);
   else if constexpr (R == 4) dft4<INV>(x);
   else dft2<INV>(x);
+}
+
+// padded shared-memory position of sequence index a (1 pad per 16 values)
+__device__ __forceinline__ int pad(int a) { return a + (a >> 4); }
+
+// Twiddles of the Stockham stages, laid out per stage as [t - 1][k]
+// (t = 1..R-1, k = 0..Ns-1, value exp(-2 pi i k t / (Ns R))), so that the
+// threads of a warp, which hold consecutive k, read consecutive entries.
+// Stage s >= 1 has Ns = E^s; only the last stage may have a radix below E.
+template <int LOGL, int LOGE>
+struct TwPlan {
+  static constexpr int NST = (LOGL + LOGE - 1) / LOGE;
+  __host__ __device__ static constexpr int log_r(int s) {
+    return s < LOGL / LOGE ? LOGE : LOGL % LOGE;
+  }
+  __host__ __device__ static constexpr int offset(int s) {
+    int o = 0;
+    for (int q = 1; q < s; ++q) o += ((1 << log_r(q)) - 1) << (LOGE * q);
+    return o;
+  }
+  static constexpr int TOTAL = offset(NST);
+};
+
+// Copy a stage-twiddle table into shared memory (the caller synchronises).
+template <int N>
+__device__ __forceinline__ void stage_table(float2* dst, const float2* __restrict__ src) {
+  for (int q = threadIdx.x; q < N; q += blockDim.x) dst[q] = __ldg(src + q);
+}
+
+// Element a of the thread's sequence lives at smem[pad(a) * STRIDE] (STRIDE =
+// 1 for rows, CB for interleaved columns; `base` already includes the
+// sequence offset).  The thread holds E = 2^LOGE values x[m] = seq[u + (L/E) m];
+// stages use radix E, the last one radix 2^(LOGL mod LOGE) if that is not 1.
+// stw is the stage-twiddle table: in shared memory, or with TWG in global
+// memory read through the read-only cache (the row passes: every CTA reads
+// the same table, so it stays in L1 and no per-CTA copy is needed).
+template <int LOGL, int LOGE, int S, bool INV, int STRIDE, bool DB = false, bool TWG = false>
+__device__ __forceinline__ void stages(float2 (&x)[1 << LOGE], float2* base, int u,
+                                       const float2* stw, float2* base2 = nullptr) {
+  using TP = TwPlan<LOGL, LOGE>;
+  constexpr int E = 1 << LOGE;
+  constexpr int NST = TP::NST;
+  if constexpr (S < NST) {
+    constexpr int LOGR = TP::log_r(S);
+    constexpr int R = 1 << LOGR, NB = E / R;
+    constexpr int LOGNS = LOGE * S;
+    constexpr int LOGTP = LOGL - LOGE;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = u + (b << LOGTP);
+      float2 v[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) v[t] = x[b + t * NB];
+      if constexpr (LOGNS > 0) {
+        const int k = j & ((1 << LOGNS) - 1);
+        constexpr int OFF = TP::offset(S);
+#pragma unroll
+        for (int t = 1; t < R; ++t) {
+          const int ti = OFF + ((t - 1) << LOGNS) + k;
+          float2 w = TWG ? __ldg(stw + ti) : stw[ti];
+          if (INV) w.y = -w.y;
+          v[t] = cmul(v[t], w);
+        }
+      }
+      dft<R, INV>(v);
+#pragma unroll
+      for (int t = 0; t < R; ++t) x[b + t * NB] = v[t];
+    }
+    if constexpr (S + 1 < NST) {
+      // with DB the exchanges alternate between two buffers: a buffer is
+      // written again only after the barrier of the exchange in between, so
+      // the barrier after the read-back is not needed
+      float2* buf = (DB && (S & 1)) ? base2 : base;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int j = u + (b << LOGTP);
+        const int k = j & ((1 << LOGNS) - 1);
+        const int o = ((j >> LOGNS) << (LOGNS + LOGR)) + k;
+#pragma unroll
+        for (int t = 0; t < R; ++t) buf[pad(o + (t << LOGNS)) * STRIDE] = x[b + t * NB];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < E; ++m) x[m] = buf[pad(u + (m << LOGTP)) * STRIDE];
+      if constexpr (!DB) __syncthreads();
+      stages<LOGL, LOGE, S + 1, INV, STRIDE, DB, TWG>(x, base, u, stw, base2);
+    }
+  }
 }
 
 }  // namespace cdft

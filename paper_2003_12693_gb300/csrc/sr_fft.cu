@@ -14,6 +14,9 @@
 //   k_colsolve2<..>   columns: FFT_M, multiply by 1/(M N lambda), inverse FFT_M
 //   k_rowifft<LOGL>   rows: rebuild the length-L sequence, inverse FFT_L,
 //                     interleave, add psi (increment form) or store
+#include <cmath>
+#include <vector>
+
 #include "sr_dft.cuh"
 #include "sr_internal.h"
 #include "sr_tma.cuh"
@@ -22,94 +25,6 @@ namespace srk {
 namespace fft2 {
 
 using namespace srk::cdft;
-
-// padded shared-memory position of sequence index a (1 pad per 16 values)
-__device__ __forceinline__ int pad(int a) { return a + (a >> 4); }
-
-// Twiddles of the Stockham stages, laid out per stage as [t - 1][k]
-// (t = 1..R-1, k = 0..Ns-1, value exp(-2 pi i k t / (Ns R))), so that the
-// threads of a warp, which hold consecutive k, read consecutive entries.
-// Stage s >= 1 has Ns = E^s; only the last stage may have a radix below E.
-template <int LOGL, int LOGE>
-struct TwPlan {
-  static constexpr int NST = (LOGL + LOGE - 1) / LOGE;
-  __host__ __device__ static constexpr int log_r(int s) {
-    return s < LOGL / LOGE ? LOGE : LOGL % LOGE;
-  }
-  __host__ __device__ static constexpr int offset(int s) {
-    int o = 0;
-    for (int q = 1; q < s; ++q) o += ((1 << log_r(q)) - 1) << (LOGE * q);
-    return o;
-  }
-  static constexpr int TOTAL = offset(NST);
-};
-
-// Copy a stage-twiddle table into shared memory (the caller synchronises).
-template <int N>
-__device__ __forceinline__ void stage_table(float2* dst, const float2* __restrict__ src) {
-  for (int q = threadIdx.x; q < N; q += blockDim.x) dst[q] = __ldg(src + q);
-}
-
-// Element a of the thread's sequence lives at smem[pad(a) * STRIDE] (STRIDE =
-// 1 for rows, CB for interleaved columns; `base` already includes the
-// sequence offset).  The thread holds E = 2^LOGE values x[m] = seq[u + (L/E) m];
-// stages use radix E, the last one radix 2^(LOGL mod LOGE) if that is not 1.
-// stw is the stage-twiddle table: in shared memory, or with TWG in global
-// memory read through the read-only cache (the row passes: every CTA reads
-// the same table, so it stays in L1 and no per-CTA copy is needed).
-template <int LOGL, int LOGE, int S, bool INV, int STRIDE, bool DB = false, bool TWG = false>
-__device__ __forceinline__ void stages(float2 (&x)[1 << LOGE], float2* base, int u,
-                                       const float2* stw, float2* base2 = nullptr) {
-  using TP = TwPlan<LOGL, LOGE>;
-  constexpr int E = 1 << LOGE;
-  constexpr int NST = TP::NST;
-  if constexpr (S < NST) {
-    constexpr int LOGR = TP::log_r(S);
-    constexpr int R = 1 << LOGR, NB = E / R;
-    constexpr int LOGNS = LOGE * S;
-    constexpr int LOGTP = LOGL - LOGE;
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const int j = u + (b << LOGTP);
-      float2 v[R];
-#pragma unroll
-      for (int t = 0; t < R; ++t) v[t] = x[b + t * NB];
-      if constexpr (LOGNS > 0) {
-        const int k = j & ((1 << LOGNS) - 1);
-        constexpr int OFF = TP::offset(S);
-#pragma unroll
-        for (int t = 1; t < R; ++t) {
-          const int ti = OFF + ((t - 1) << LOGNS) + k;
-          float2 w = TWG ? __ldg(stw + ti) : stw[ti];
-          if (INV) w.y = -w.y;
-          v[t] = cmul(v[t], w);
-        }
-      }
-      dft<R, INV>(v);
-#pragma unroll
-      for (int t = 0; t < R; ++t) x[b + t * NB] = v[t];
-    }
-    if constexpr (S + 1 < NST) {
-      // with DB the exchanges alternate between two buffers: a buffer is
-      // written again only after the barrier of the exchange in between, so
-      // the barrier after the read-back is not needed
-      float2* buf = (DB && (S & 1)) ? base2 : base;
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        const int j = u + (b << LOGTP);
-        const int k = j & ((1 << LOGNS) - 1);
-        const int o = ((j >> LOGNS) << (LOGNS + LOGR)) + k;
-#pragma unroll
-        for (int t = 0; t < R; ++t) buf[pad(o + (t << LOGNS)) * STRIDE] = x[b + t * NB];
-      }
-      __syncthreads();
-#pragma unroll
-      for (int m = 0; m < E; ++m) x[m] = buf[pad(u + (m << LOGTP)) * STRIDE];
-      if constexpr (!DB) __syncthreads();
-      stages<LOGL, LOGE, S + 1, INV, STRIDE, DB, TWG>(x, base, u, stw, base2);
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // rows, forward: packed half spectrum of the real rows of src
@@ -479,6 +394,43 @@ static cudaError_t col_go(const ColArgs& a, cudaStream_t s, bool set_attr) {
   if (set_attr) return set_smem(k_colsolve2<LOGM, CB, LOGE, DB, MINB>, smem);
   return launch_k(k_colsolve2<LOGM, CB, LOGE, DB, MINB>, dim3(a.geo.L / CB),
                   dim3(CB * M / (1 << LOGE)), smem, s, a);
+}
+
+static int ilog2_host(int v) {
+  int r = 0;
+  while ((1 << r) < v) ++r;
+  return r;
+}
+
+std::vector<float2> twiddle_table(int n, int len) {
+  // exp(-2 pi i q / len), q in [0, n), computed in double and rounded once
+  std::vector<float2> t(n);
+  for (int q = 0; q < n; ++q) {
+    const double a = -2.0 * M_PI * (double)q / (double)len;
+    t[q] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  return t;
+}
+
+// Stage twiddles of the register FFT for a length-len transform with 2^logE
+// values per thread: stage q >= 1 has Ns = 2^(logE q) and radix 2^logE (the
+// last stage 2^(log2(len) mod logE) if that is not 1); its entries
+// exp(-2 pi i k t / (Ns R)) are stored at [t - 1][k].
+std::vector<float2> stage_twiddle_table(int len, int logE) {
+  const int logL = ilog2_host(len);
+  const int nst = (logL + logE - 1) / logE;
+  std::vector<float2> v;
+  for (int q = 1; q < nst; ++q) {
+    const int logR = q < logL / logE ? logE : logL % logE;
+    const int R = 1 << logR, Ns = 1 << (logE * q);
+    for (int t = 1; t < R; ++t)
+      for (int k = 0; k < Ns; ++k) {
+        const double ang = -2.0 * M_PI * (double)k * (double)t / ((double)Ns * (double)R);
+        v.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
+      }
+  }
+  if (v.empty()) v.push_back(make_float2(1.f, 0.f));  // keep the allocation non-empty
+  return v;
 }
 
 bool fft2_supported(const Geo& geo) { return geo.L >= 16 && geo.L <= 2048 && geo.M >= 16 && geo.M <= 4096; }

@@ -2,6 +2,8 @@
 // (sr_kernels.cu).  Not part of the public C-ABI.
 #pragma once
 
+#include <vector>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -229,6 +231,12 @@ int tile32_blocks(const Geo& geo);  // CTAs of the 32 x 32 tile kernels
 // SMs: *T rows per CTA and *NT threads, with T * L = 16 * NT.  Returns false
 // (and leaves the outputs alone) when no such shape exists.
 bool row_shape(int H, int L, int nsm, int* NT, int* T);
+cudaError_t launch_empty(cudaStream_t s);  // one warp that only waits and triggers
+// Host tables (double, rounded once): exp(-2 pi i q / len) for q < n, and the
+// per-stage twiddles of the register FFT of length len with 2^logE values
+// per thread (the layout TwPlan in sr_dft.cuh describes).
+std::vector<float2> twiddle_table(int n, int len);
+std::vector<float2> stage_twiddle_table(int len, int logE);
 cudaError_t launch_repulsion(const RepArgs& a, cudaStream_t s);
 cudaError_t launch_energy(const EnergyArgs& a, cudaStream_t s);
 cudaError_t launch_reduce(const double* partials, int nblocks, int ncomp, double* out,

@@ -113,6 +113,8 @@ def lib() -> C.CDLL:
     L.sr_kernel_launches.argtypes = [_P, C.c_int]
     L.sr_profile_enable.restype = st
     L.sr_profile_enable.argtypes = [_P, C.c_int]
+    L.sr_profile_overhead.restype = st
+    L.sr_profile_overhead.argtypes = [_P, C.POINTER(C.c_double)]
     L.sr_kernel_times.restype = st
     L.sr_kernel_times.argtypes = [_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
     L.sr_get_schedule.restype = st
@@ -323,6 +325,11 @@ class Context:
 
     def profile_enable(self, on: bool = True):
         _check(lib().sr_profile_enable(self.handle, int(on)), self)
+
+    def profile_overhead_us(self) -> float:
+        us = C.c_double()
+        _check(lib().sr_profile_overhead(self.handle, C.byref(us)), self)
+        return us.value
 
     def kernel_times(self, kclass) -> tuple[float, int]:
         k = KCLASS[kclass] if isinstance(kclass, str) else int(kclass)

@@ -2,7 +2,9 @@
 
 Same comparisons as test_gpu_parity.py, on shapes whose FFT lengths (H and
 W/2) have the factors 3, 5, 7 and 31 (a direct length-31 DFT), against the
-FP64 oracle, whose transform handles any length."""
+FP64 oracle, whose transform handles any length.  Every test runs twice: with
+the recursion column pass these sizes use by default, and with the
+mixed-radix column FFT (SR_GEN_FFT_COLS=1)."""
 import pytest
 
 from gpu_common import *  # noqa: F401,F403
@@ -15,6 +17,11 @@ MIXED = [(48, 96),     # 16*3, 48 = 16*3
          (224, 64),    # 32*7, 32
          (160, 992),   # 32*5, 496 = 16*31
          (64, 1120)]   # 64, 560 = 16*5*7
+
+
+@pytest.fixture(autouse=True, params=["recursion_columns", "fft_columns"])
+def _column_pass(request, monkeypatch):
+    monkeypatch.setenv("SR_GEN_FFT_COLS", "1" if request.param == "fft_columns" else "0")
 
 
 @pytest.fixture(scope="module", autouse=True)
