@@ -1,8 +1,8 @@
 """FP64 oracle of the Split Bregman SR iteration on volumes (the 3-D use of
 Fig. 6).
 
-TEST INFRASTRUCTURE ONLY (like the rest of ``oracle/``); the CUDA path does
-not implement volumes yet.
+TEST INFRASTRUCTURE ONLY (like the rest of ``oracle/``).  The CUDA path's
+version (include/sr3.h, sr3.cu) is checked against it by tests/test_gpu_sr3.py.
 
 The method is the 2-D one with a third axis everywhere, under the same
 readings: periodic forward differences (Eq. (35)) and backward divergence

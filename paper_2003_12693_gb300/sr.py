@@ -46,7 +46,8 @@ _lib = None
 _P = C.c_void_p
 
 
-HEADERS = [HEADER, os.path.join(os.path.dirname(_HERE), "include", "sr_net.h")]
+HEADERS = [HEADER, os.path.join(os.path.dirname(_HERE), "include", "sr_net.h"),
+           os.path.join(os.path.dirname(_HERE), "include", "sr3.h")]
 
 
 def declared_functions() -> list[str]:
@@ -55,7 +56,7 @@ def declared_functions() -> list[str]:
     for h in HEADERS:
         text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
         text = re.sub(r"#define[^\n]*", "", text)
-        names |= set(re.findall(r"\b(sr_[a-z_0-9]+)\s*\(", text))
+        names |= set(re.findall(r"\b(sr3?_[a-z_0-9]+)\s*\(", text))
     return sorted(names)
 
 
