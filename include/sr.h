@@ -365,6 +365,25 @@ sr_status sr_test_fail_allocations(long long n);
 typedef struct sr_group sr_group;
 sr_status sr_group_create(sr_ctx* const* members, int n, sr_group** out);
 sr_status sr_group_iterate(sr_group* group, int max_outer);
+
+/* Run every member until its own stopping test passes, in one graph launch.
+ * The launched graph holds, per member, a device-side while-loop (a CUDA
+ * graph conditional node) whose body is B outer iterations (B = check_every
+ * rounded up to an even number, so a body leaves the member at its parity)
+ * followed by the member's stopping test: the relative change
+ * ||phi^{k+1} - phi^k|| / (||phi^k|| + 1e-6) of the body's last iteration,
+ * reduced in FP64 on the GPU as sr_iterate's, decides on the device whether
+ * the member runs another body (change > tol and another body fits under
+ * max_outer).  Members stop independently; the others keep the GPU.  Each
+ * member's state equals sr_iterate(member, outer_done[k], 0, ...) bit for bit.
+ * Synchronises.  outer_done and rel_change (n entries each, may be NULL)
+ * receive each member's iterations and last relative change.  Returns
+ * SR_ENOTCONVERGED if some member reached max_outer first, SR_ENONFINITE if a
+ * member's change was NaN or Inf (that member stops), SR_EINVAL for
+ * check_every outside [1, 1000], tol < 0 or max_outer < B.  The first call
+ * (and a call with another check_every or parity) builds the graph. */
+sr_status sr_group_run(sr_group* group, int max_outer, double tol, int check_every,
+                       int* outer_done, double* rel_change);
 void sr_group_destroy(sr_group* group);
 
 /* Convenience for callers with host buffers: copy the image and phi0 from

@@ -1626,6 +1626,12 @@ struct sr_group {
   std::vector<sr_ctx*> m;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // per parity
   int device = 0;
+  // sr_group_run: one graph of per-member while-loops, built for a step and
+  // a starting parity; per-member loop state in device memory
+  cudaGraphExec_t run_graph = nullptr;
+  int run_step = 0, run_parity = -1;
+  srk::LoopState* loop = nullptr;     // device, one per member
+  srk::LoopState* loop_host = nullptr;  // pinned copy
 };
 
 namespace {
@@ -1633,7 +1639,73 @@ namespace {
 void group_release(sr_group* g) {
   for (int p = 0; p < 2; ++p)
     if (g->graph[p]) cudaGraphExecDestroy(g->graph[p]);
+  if (g->run_graph) cudaGraphExecDestroy(g->run_graph);
+  if (g->loop) cudaFree(g->loop);
+  if (g->loop_host) cudaFreeHost(g->loop_host);
   delete g;
+}
+
+// The graph of sr_group_run: for every member a while-node whose body is
+// `step` outer iterations (captured as sr_iterate captures them, the last
+// one with the FP64 change sums) followed by the member's stopping test
+// (k_loop_ctl), which sets the node's condition.  Members converge and leave
+// independently; the nodes are spread over lanes like group_build's.
+cudaError_t group_build_run(sr_group* g, int step, int parity, std::string& why) {
+  const int n = (int)g->m.size();
+  int lanes = 32;
+  if (const char* env = std::getenv("SR_GROUP_LANES")) lanes = std::max(1, std::atoi(env));
+  lanes = std::min(lanes, n);
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (long long)g->m[a]->H * g->m[a]->W > (long long)g->m[b]->H * g->m[b]->W;
+  });
+  std::vector<long long> load(lanes, 0);
+  std::vector<cudaGraphNode_t> last(lanes, nullptr);
+  cudaGraph_t top = nullptr;
+  cudaError_t e = cudaGraphCreate(&top, 0);
+  for (int idx = 0; idx < n && e == cudaSuccess; ++idx) {
+    const int mi = order[idx];
+    sr_ctx* c = g->m[mi];
+    const int lane = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[lane] += (long long)c->H * c->W;
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, top, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) break;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, top, last[lane] ? &last[lane] : nullptr, nullptr,
+                         last[lane] ? 1 : 0, &np);
+    if (e != cudaSuccess) break;
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    const long long before = c->launches;
+    c->gen_batched = true;
+    sr_status st = SR_OK;
+    for (int r = 0; r < step && st == SR_OK; ++r)
+      st = enqueue_iteration(c, c->cap_stream, (parity + r) & 1, r == step - 1);
+    c->gen_batched = false;
+    c->launches = before;
+    cudaError_t e2 = st == SR_OK ? srk::launch_loop_ctl(h, c->red, g->loop + mi, step, c->cap_stream)
+                                 : cudaSuccess;
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &captured);
+    if (st != SR_OK) {
+      why = c->err;
+      if (e == cudaSuccess) e = cudaErrorUnknown;
+    }
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) last[lane] = node;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g->run_graph, top, 0);
+  if (top) cudaGraphDestroy(top);
+  return e;
 }
 
 // One outer iteration of every member (parity p), each captured on its own
@@ -1739,6 +1811,63 @@ sr_status sr_group_iterate(sr_group* g, int max_outer) {
     }
   }
   return SR_OK;
+}
+
+sr_status sr_group_run(sr_group* g, int max_outer, double tol, int check_every, int* outer_done,
+                       double* rel_change) {
+  if (!g) return SR_EINVAL;
+  sr_ctx* c0 = g->m[0];
+  const int n = (int)g->m.size();
+  if (check_every < 1 || check_every > 1000 || !std::isfinite(tol) || tol < 0.0)
+    return fail(c0, SR_EINVAL, "sr_group_run: check_every in [1, 1000] and tol >= 0 required");
+  const int step = check_every + (check_every & 1);  // even: the body keeps the parity
+  if (max_outer < step) return fail(c0, SR_EINVAL, "sr_group_run: max_outer below one body");
+  for (sr_ctx* c : g->m) {
+    if (c->cur != c0->cur) return fail(c0, SR_EINVAL, "group members are at different parities");
+    if (c->profile) return fail(c0, SR_EINVAL, "group members must not be profiling");
+  }
+  if (!g->loop) {
+    SR_CUDA(c0, cudaMalloc((void**)&g->loop, sizeof(srk::LoopState) * n));
+    SR_CUDA(c0, cudaMallocHost((void**)&g->loop_host, sizeof(srk::LoopState) * n));
+  }
+  if (!g->run_graph || g->run_step != step || g->run_parity != c0->cur) {
+    if (g->run_graph) cudaGraphExecDestroy(g->run_graph);
+    g->run_graph = nullptr;
+    std::string why;
+    const cudaError_t e = group_build_run(g, step, c0->cur, why);
+    if (e != cudaSuccess) {
+      if (g->run_graph) cudaGraphExecDestroy(g->run_graph);
+      g->run_graph = nullptr;
+      if (!why.empty()) return fail(c0, SR_ECUDA, "sr_group_run: " + why);
+      return cuda_fail(c0, e, "sr_group_run");
+    }
+    g->run_step = step;
+    g->run_parity = c0->cur;
+  }
+  for (int k = 0; k < n; ++k) g->loop_host[k] = srk::LoopState{tol, 0.0, max_outer, 0};
+  SR_CUDA(c0, cudaMemcpyAsync(g->loop, g->loop_host, sizeof(srk::LoopState) * n,
+                              cudaMemcpyHostToDevice, c0->stream));
+  SR_CUDA(c0, cudaGraphLaunch(g->run_graph, c0->stream));
+  SR_CUDA(c0, cudaMemcpyAsync(g->loop_host, g->loop, sizeof(srk::LoopState) * n,
+                              cudaMemcpyDeviceToHost, c0->stream));
+  SR_CUDA(c0, cudaStreamSynchronize(c0->stream));
+  sr_status st = SR_OK;
+  for (int k = 0; k < n; ++k) {
+    sr_ctx* c = g->m[k];
+    const srk::LoopState& L = g->loop_host[k];
+    c->iters += L.iters;
+    c->inner_steps += (long long)L.iters * c->prm.inner_S;
+    if (outer_done) outer_done[k] = L.iters;
+    if (rel_change) rel_change[k] = L.rel;
+    if (!std::isfinite(L.rel)) st = SR_ENONFINITE;
+    else if (st == SR_OK && !(L.rel <= tol)) st = SR_ENOTCONVERGED;
+  }
+  for (sr_ctx* c : g->m) {
+    sr_status es = check_device_error(c);
+    if (es != SR_OK) return es;
+  }
+  if (st == SR_ENONFINITE) return fail(c0, st, "non-finite value in a member's stopping test");
+  return st;
 }
 
 void sr_group_destroy(sr_group* g) {

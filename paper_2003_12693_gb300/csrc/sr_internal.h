@@ -232,6 +232,15 @@ int tile32_blocks(const Geo& geo);  // CTAs of the 32 x 32 tile kernels
 // (and leaves the outputs alone) when no such shape exists.
 bool row_shape(int H, int L, int nsm, int* NT, int* T);
 cudaError_t launch_empty(cudaStream_t s);  // one warp that only waits and triggers
+// per-member state of a group's device-side stopping loop (sr_group_run)
+struct LoopState {
+  double tol;      // set by the host before the launch
+  double rel;      // last relative change
+  int max_outer;   // set by the host
+  int iters;       // outer iterations run (reset by the host)
+};
+cudaError_t launch_loop_ctl(cudaGraphConditionalHandle h, const double* red, LoopState* st,
+                            int step, cudaStream_t s);
 // Host tables (double, rounded once): exp(-2 pi i q / len) for q < n, and the
 // per-stage twiddles of the register FFT of length len with 2^logE values
 // per thread (the layout TwPlan in sr_dft.cuh describes).

@@ -1273,6 +1273,27 @@ __global__ void k_empty() {
 
 cudaError_t launch_empty(cudaStream_t s) { return launch_k(k_empty, dim3(1), dim3(32), 0, s); }
 
+// The stopping test of one group member inside a graph's while-loop: after a
+// body of `step` outer iterations, from the FP64 sums of the body's last
+// iteration (red[0] = sum (phi^{k+1} - phi^k)^2, red[1] = sum (phi^k)^2),
+// rel = ||phi^{k+1} - phi^k|| / (||phi^k|| + 1e-6); the member goes on while
+// rel > tol and another body fits under max_outer.  A non-finite rel stops
+// it (the host reports SR_ENONFINITE).
+__global__ void k_loop_ctl(cudaGraphConditionalHandle h, const double* __restrict__ red,
+                           LoopState* __restrict__ st, int step) {
+  const double r = sqrt(red[0]) / (sqrt(red[1]) + 1e-6);
+  st->iters += step;
+  st->rel = r;
+  const bool go = isfinite(r) && r > st->tol && st->iters + step <= st->max_outer;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+cudaError_t launch_loop_ctl(cudaGraphConditionalHandle h, const double* red, LoopState* st,
+                            int step, cudaStream_t s) {
+  k_loop_ctl<<<1, 1, 0, s>>>(h, red, st, step);
+  return cudaGetLastError();
+}
+
 bool row_shape(int H, int L, int nsm, int* NT_out, int* T_out) {
   if (H < 1 || L < 1) return false;
   int NT = L >= 2048 ? 512 : 256;

@@ -131,6 +131,9 @@ def lib() -> C.CDLL:
     L.sr_group_create.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(_P)]
     L.sr_group_iterate.restype = st
     L.sr_group_iterate.argtypes = [_P, C.c_int]
+    L.sr_group_run.restype = st
+    L.sr_group_run.argtypes = [_P, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int),
+                               C.POINTER(C.c_double)]
     L.sr_group_destroy.restype = None
     L.sr_group_destroy.argtypes = [_P]
     L.sr_set_phi_solver.restype = st
@@ -378,6 +381,16 @@ class Group:
 
     def iterate(self, max_outer: int):
         _check(lib().sr_group_iterate(self.handle, int(max_outer)), self.members[0])
+
+    def run(self, max_outer: int, tol: float, check_every: int = 10):
+        """sr_group_run: per-member device-side stopping; returns (outer_done,
+        rel_change, all_converged)."""
+        n = len(self.members)
+        done = (C.c_int * n)()
+        rel = (C.c_double * n)()
+        st = lib().sr_group_run(self.handle, int(max_outer), float(tol), int(check_every), done, rel)
+        _check(st, self.members[0])
+        return list(done), list(rel), st == SR_OK
 
     def close(self):
         if getattr(self, "handle", None):

@@ -1,0 +1,93 @@
+"""sr_group_run: many images of uneven sizes in one graph launch, each with its
+own device-side stopping test (a CUDA graph while-loop per member).
+
+The stopping decisions are taken on the GPU from the same FP64 sums that
+sr_iterate's stopping test reads, so they are predictable exactly: each member
+is first iterated alone in bodies of B outer iterations, reading its
+relative change after every body; a tolerance between those traces makes the
+members stop after different numbers of bodies.  The group run must stop each
+member exactly where its own trace crosses the tolerance and leave it
+bit-identical to the member iterated alone for that many iterations."""
+import pytest
+
+from gpu_common import *  # noqa: F401,F403
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(128, 128), (96, 160), (256, 64), (64, 96), (160, 224), (64, 64)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_12693_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _members(seed0):
+    ctxs = []
+    for k, (H, W) in enumerate(SIZES):
+        img = synth.ellipse_scene(seed0 + k, H=H, W=W, scale=max(min(H, W) / 512.0, 0.125))
+        ctx = context(H, W, R=4, d=4.0)
+        ctx.edge_function(dev(img))
+        ctx.set_phi(dev(synth.inset_rect_sdf(H, W)))
+        ctxs.append(ctx)
+    return ctxs
+
+
+def test_group_run_stops_each_member_at_its_own_tolerance():
+    B, bodies = 4, 6
+    # traces: relative change after every body of B iterations, member alone
+    alone = _members(300)
+    traces = []
+    for ctx in alone:
+        tr = []
+        for _ in range(bodies):
+            _, rel, _ = ctx.iterate(B, want_rel=True)
+            tr.append(rel)
+        traces.append(tr)
+    for ctx in alone:
+        ctx.close()
+    # a tolerance that the members cross at different bodies
+    flat = sorted(r for tr in traces for r in tr)
+    tol = flat[len(flat) // 2]
+    expect = []
+    for tr in traces:
+        n = next((b + 1 for b, r in enumerate(tr) if r <= tol), bodies)
+        expect.append(n * B)
+    assert len(set(expect)) > 1, "the members should stop at different iterations"
+    grouped = _members(300)
+    grp = sr.Group(grouped)
+    done, rel, converged = grp.run(bodies * B, tol, check_every=B)
+    assert done == expect, (done, expect)
+    for k, (d, r) in enumerate(zip(done, rel)):
+        assert r == traces[k][d // B - 1]
+    assert converged == all(tr[e // B - 1] <= tol for tr, e in zip(traces, expect))
+    # each member equals the member iterated alone for as many iterations
+    ref = _members(300)
+    for ctx, d in zip(ref, done):
+        ctx.iterate(d)
+    for a, b in zip(ref, grouped):
+        for x, y in zip(a.get_state(), b.get_state()):
+            assert np.array_equal(host(x), host(y))
+    report("group_run", members=len(SIZES), tol=tol, outer_done=str(done))
+    grp.close()
+    for ctx in ref + grouped:
+        ctx.close()
+
+
+def test_group_run_reports_unconverged_and_odd_check_every():
+    grouped = _members(400)
+    grp = sr.Group(grouped)
+    # check_every 3 runs bodies of 4 (parity-neutral); tol 0 never converges
+    done, rel, converged = grp.run(8, 0.0, check_every=3)
+    assert done == [8] * len(SIZES) and not converged
+    assert all(np.isfinite(r) and r > 0 for r in rel)
+    with pytest.raises(sr.SRError) as e:
+        grp.run(2, 1e-3, check_every=3)  # max_outer below one body
+    assert e.value.status == sr.SR_EINVAL
+    grp.close()
+    for ctx in grouped:
+        ctx.close()
