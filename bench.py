@@ -272,6 +272,7 @@ def batched_sample(stream, n_images: int = 256, iters: int = 100) -> dict:
         ctxs.append(c)
         P += H * W
     grp = sr.Group(ctxs)
+    lanes = grp.tune()
     grp.iterate(10)
     for c in ctxs:
         c.iterate(2)
@@ -294,8 +295,10 @@ def batched_sample(stream, n_images: int = 256, iters: int = 100) -> dict:
     return {"images": n_images, "pixels": P, "sides": "64, 96, ..., 1024", "iterations": iters,
             "value": P * iters / t_group / 1e6, "unit": UNIT,
             "one_by_one": P * iters / t_seq / 1e6, "speedup": t_seq / t_group,
+            "lanes": lanes,
             "how": "sr_group_iterate: one CUDA graph per parity, members' iterations as "
-                   "child graphs on up to 32 concurrent lanes; one_by_one = sr_iterate per "
+                   "child graphs on concurrent lanes (count chosen by sr_group_tune); "
+                   "one_by_one = sr_iterate per "
                    "image in turn; CUDA events on the stream, no L2 flush (state "
                    f"about {P * 14 * 4 / 1e9:.1f} GB)"}
 

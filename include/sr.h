@@ -384,6 +384,15 @@ sr_status sr_group_iterate(sr_group* group, int max_outer);
  * (and a call with another check_every or parity) builds the graph. */
 sr_status sr_group_run(sr_group* group, int max_outer, double tol, int check_every,
                        int* outer_done, double* rel_change);
+/* Choose how many members run concurrently in the group's graphs (its
+ * "lanes": 4, 8, 16, 32 or 64, at most the member count) by timing two outer
+ * iterations of the whole group with each and keeping the fastest; the
+ * members' states are saved before and restored after every timing, so the
+ * call leaves them as it found them (it allocates room for five image planes
+ * per member for the time of the call).  Synchronises.  lanes_out (may be
+ * NULL) receives the choice.  Without this call a group uses 32 lanes, or the
+ * count in the environment variable SR_GROUP_LANES at sr_group_create. */
+sr_status sr_group_tune(sr_group* group, int* lanes_out);
 void sr_group_destroy(sr_group* group);
 
 /* Convenience for callers with host buffers: copy the image and phi0 from

@@ -1632,6 +1632,7 @@ struct sr_group {
   int run_step = 0, run_parity = -1;
   srk::LoopState* loop = nullptr;     // device, one per member
   srk::LoopState* loop_host = nullptr;  // pinned copy
+  int lanes = 32;  // concurrent chains of members (sr_group_tune)
 };
 
 namespace {
@@ -1652,8 +1653,7 @@ void group_release(sr_group* g) {
 // independently; the nodes are spread over lanes like group_build's.
 cudaError_t group_build_run(sr_group* g, int step, int parity, std::string& why) {
   const int n = (int)g->m.size();
-  int lanes = 32;
-  if (const char* env = std::getenv("SR_GROUP_LANES")) lanes = std::max(1, std::atoi(env));
+  int lanes = g->lanes;
   lanes = std::min(lanes, n);
   std::vector<int> order(n);
   for (int k = 0; k < n; ++k) order[k] = k;
@@ -1716,8 +1716,7 @@ cudaError_t group_build_run(sr_group* g, int step, int parity, std::string& why)
 // member's message.
 cudaError_t group_build(sr_group* g, int p, std::string& why) {
   const int n = (int)g->m.size();
-  int lanes = 32;  // measured best of 8, 16, 32 on 64-256 images of 64..1024 px sides
-  if (const char* env = std::getenv("SR_GROUP_LANES")) lanes = std::max(1, std::atoi(env));
+  int lanes = g->lanes;
   lanes = std::min(lanes, n);
   std::vector<int> order(n);
   for (int k = 0; k < n; ++k) order[k] = k;
@@ -1781,6 +1780,7 @@ sr_status sr_group_create(sr_ctx* const* members, int n, sr_group** out) {
   sr_group* g = new sr_group;
   g->m.assign(members, members + n);
   g->device = c0->device;
+  if (const char* env = std::getenv("SR_GROUP_LANES")) g->lanes = std::max(1, std::atoi(env));
   cudaError_t e = cudaSuccess;
   std::string why;
   for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = group_build(g, p, why);
@@ -1868,6 +1868,101 @@ sr_status sr_group_run(sr_group* g, int max_outer, double tol, int check_every, 
   }
   if (st == SR_ENONFINITE) return fail(c0, st, "non-finite value in a member's stopping test");
   return st;
+}
+
+sr_status sr_group_tune(sr_group* g, int* lanes_out) {
+  if (!g) return SR_EINVAL;
+  sr_ctx* c0 = g->m[0];
+  const int n = (int)g->m.size();
+  for (sr_ctx* c : g->m)
+    if (c->cur != c0->cur) return fail(c0, SR_EINVAL, "group members are at different parities");
+  // save every member's state (phi, w at the current parity, e) to restore it
+  std::vector<float*> saved;
+  auto release = [&] {
+    for (float* q : saved) cudaFree(q);
+  };
+  for (sr_ctx* c : g->m) {
+    const size_t bytes = (size_t)c->H * c->W * sizeof(float);
+    const float* src[5] = {c->phi[c->cur], c->w1[c->cur], c->w2[c->cur], c->e1, c->e2};
+    for (const float* sp : src) {
+      float* q = nullptr;
+      const cudaError_t e = dev_alloc((void**)&q, bytes);
+      if (e != cudaSuccess) {
+        release();
+        return e == cudaErrorMemoryAllocation ? fail(c0, SR_ENOMEM, "sr_group_tune: no room to save the states")
+                                              : cuda_fail(c0, e, "sr_group_tune");
+      }
+      saved.push_back(q);
+      SR_CUDA(c0, cudaMemcpyAsync(q, sp, bytes, cudaMemcpyDeviceToDevice, c0->stream));
+    }
+  }
+  auto restore = [&]() -> cudaError_t {
+    size_t k = 0;
+    for (sr_ctx* c : g->m) {
+      const size_t bytes = (size_t)c->H * c->W * sizeof(float);
+      float* dst[5] = {c->phi[c->cur], c->w1[c->cur], c->w2[c->cur], c->e1, c->e2};
+      for (float* dp : dst) {
+        const cudaError_t e = cudaMemcpyAsync(dp, saved[k++], bytes, cudaMemcpyDeviceToDevice, c0->stream);
+        if (e != cudaSuccess) return e;
+      }
+    }
+    return cudaSuccess;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  const int cands[] = {4, 8, 16, 32, 64};
+  int best = g->lanes;
+  float best_ms = 1e30f;
+  const int p = c0->cur;
+  for (int L : cands) {
+    if (err != cudaSuccess) break;
+    if (L > n && L != cands[0]) continue;
+    for (int q = 0; q < 2; ++q)
+      if (g->graph[q]) {
+        cudaGraphExecDestroy(g->graph[q]);
+        g->graph[q] = nullptr;
+      }
+    g->lanes = L;
+    std::string why;
+    for (int q = 0; q < 2 && err == cudaSuccess; ++q) err = group_build(g, q, why);
+    if (err != cudaSuccess) break;
+    // one warm-up pair, then a timed pair of outer iterations (both parities)
+    for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {
+      if (rep == 1) err = cudaEventRecord(e0, c0->stream);
+      if (err == cudaSuccess) err = cudaGraphLaunch(g->graph[p], c0->stream);
+      if (err == cudaSuccess) err = cudaGraphLaunch(g->graph[1 - p], c0->stream);
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(e1, c0->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess) err = restore();
+    if (err == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best = L;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(c0->stream);
+  release();
+  if (err != cudaSuccess) return cuda_fail(c0, err, "sr_group_tune");
+  for (int q = 0; q < 2; ++q)
+    if (g->graph[q]) {
+      cudaGraphExecDestroy(g->graph[q]);
+      g->graph[q] = nullptr;
+    }
+  if (g->run_graph) {
+    cudaGraphExecDestroy(g->run_graph);
+    g->run_graph = nullptr;
+  }
+  g->lanes = best;
+  std::string why;
+  for (int q = 0; q < 2 && err == cudaSuccess; ++q) err = group_build(g, q, why);
+  if (err != cudaSuccess) return cuda_fail(c0, err, "sr_group_tune");
+  if (lanes_out) *lanes_out = best;
+  return SR_OK;
 }
 
 void sr_group_destroy(sr_group* g) {

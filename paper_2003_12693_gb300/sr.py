@@ -131,6 +131,8 @@ def lib() -> C.CDLL:
     L.sr_group_create.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(_P)]
     L.sr_group_iterate.restype = st
     L.sr_group_iterate.argtypes = [_P, C.c_int]
+    L.sr_group_tune.restype = st
+    L.sr_group_tune.argtypes = [_P, C.POINTER(C.c_int)]
     L.sr_group_run.restype = st
     L.sr_group_run.argtypes = [_P, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int),
                                C.POINTER(C.c_double)]
@@ -381,6 +383,12 @@ class Group:
 
     def iterate(self, max_outer: int):
         _check(lib().sr_group_iterate(self.handle, int(max_outer)), self.members[0])
+
+    def tune(self) -> int:
+        """sr_group_tune: the lane count chosen by timing."""
+        lanes = C.c_int()
+        _check(lib().sr_group_tune(self.handle, C.byref(lanes)), self.members[0])
+        return lanes.value
 
     def run(self, max_outer: int, tol: float, check_every: int = 10):
         """sr_group_run: per-member device-side stopping; returns (outer_done,

@@ -91,3 +91,28 @@ def test_group_run_reports_unconverged_and_odd_check_every():
     grp.close()
     for ctx in grouped:
         ctx.close()
+
+
+def test_group_tune_picks_a_lane_count_and_leaves_the_states():
+    """sr_group_tune times the group at several lane counts; the members'
+    states come back bit for bit, and the tuned group still iterates every
+    member exactly as alone."""
+    grouped = _members(500)
+    before = [[host(t) for t in c.get_state()] for c in grouped]
+    grp = sr.Group(grouped)
+    lanes = grp.tune()
+    assert lanes in (4, 8, 16, 32, 64)
+    for c, ref in zip(grouped, before):
+        for x, y in zip(c.get_state(), ref):
+            assert np.array_equal(host(x), y)
+    grp.iterate(5)
+    alone = _members(500)
+    for c in alone:
+        c.iterate(5)
+    for a, b in zip(alone, grouped):
+        for x, y in zip(a.get_state(), b.get_state()):
+            assert np.array_equal(host(x), host(y))
+    report("group_tune", members=len(SIZES), lanes=lanes)
+    grp.close()
+    for c in alone + grouped:
+        c.close()

@@ -199,7 +199,8 @@ def test_net_gradients_match_oracle(B, H, W):
     bf16 roundings of eleven stages (forward and backward); the sums cancel
     (|sum| is about a tenth of sum |.| here), which magnifies their relative
     error.  So the error is bounded against the norm of the sum of absolute
-    terms, wgrad(|x|, |delta|), computed by the oracle."""
+    terms, wgrad(|x|, |delta|), computed by the oracle, and, per block, the
+    relative L2 distance to the oracle's gradient is bounded too."""
     S = sn()
     theta, f, phi = net_inputs(23 + W, B, H, W)
     net = S.Net(H, W, max_batch=B, phi_clip=4.0)
@@ -224,8 +225,12 @@ def test_net_gradients_match_oracle(B, H, W):
             cos = np.dot(a, r) / max(np.linalg.norm(a) * np.linalg.norm(r), 1e-30)
             report("net_grad", shape=f"{B}x{H}x{W}", layer=li + 1, part=name, rel_l2=rel(a, r),
                    err_vs_abs=err, cos=cos)
-            if not (err <= 3e-2 and cos >= 0.99):
-                bad.append((li + 1, name, err, cos))
+            # and per block against the oracle itself: bf16 rounding of eleven
+            # stages magnified by the cancellation (|sum| ~ sum|.| / 8) gives
+            # up to about 11 % here (measured on GB300); 20 % is the bound, so
+            # a dropped or doubled term that carries a fifth of a block fails
+            if not (err <= 3e-2 and cos >= 0.99 and rel(a, r) <= 0.2):
+                bad.append((li + 1, name, err, cos, rel(a, r)))
             k += n
     assert k == g.size
     assert not bad, bad
