@@ -248,6 +248,97 @@ def experiment(n: int = 128, n_train: int = 2048, n_eval: int = 32, t_ref: int =
         topology_agree=int(sum(comps(a) == comps(b) for a, b in zip(plain.masks, lb.masks))))
 
 
+def experiment_scale(n: int = 256, n_train: int = 20000, n_heldout: int = 1000, n_solve: int = 64,
+                     t_ref: int = 3000, steps: int = 6000, batch: int = 32, lr: float = 2e-3,
+                     rho: float = 1e4, sigma: float = 3.0, check: int = 50, iou: float = 0.9,
+                     procs: int = 16) -> dict:
+    """The warm start at its configured scale: n_train (image, phi after t_ref
+    plain iterations) pairs of n x n six-ellipse scenes (seeds 20000 + k,
+    noise drawn from U[0.05, 0.15]), training on all of them, then
+    * on n_heldout held-out scenes (seeds 40000 + k): the network's loss and
+      the overlap (IoU) of its start mask with the plain solver's mask after
+      t_ref iterations, against the inset rectangle's;
+    * on the first n_solve of them, "the same accuracy" read as reaching IoU
+      >= iou with that plain mask: outer iterations and GPU-seconds per image
+      until each image gets there, (a) plain from the rectangle one image at a
+      time, (b) batched from the rectangle, (c) batched from the network's
+      phi0 (network time included), at most 2 t_ref iterations; and the
+      component counts of the final masks against the plain ones."""
+    import multiprocessing as mp
+
+    from scipy import ndimage
+
+    from paper_2003_12693_gb300 import synth
+    from paper_2003_12693_gb300 import warmstart as this
+    rng = np.random.default_rng(12)
+    noises = rng.uniform(0.05, 0.15, n_train + n_heldout)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        tr = np.stack(pool.map(this._scene, [(20000 + k, n, float(noises[k])) for k in range(n_train)], 64))
+        ev = np.stack(pool.map(this._scene, [(40000 + k, n, float(noises[n_train + k]))
+                                             for k in range(n_heldout)], 16))
+    prm = dict(synth.WORKLOADS["ellipses_512"].params())
+    prm.update(rho=rho, sigma=sigma)
+    p = sr.make_params(**prm)
+    rect = torch.from_numpy(synth.inset_rect_sdf(n, n).astype(np.float32)).cuda()
+    trd, evd = torch.from_numpy(tr).cuda(), torch.from_numpy(ev).cuda()
+    del tr, ev
+    t0 = time.perf_counter()
+    phis = generate_pairs(trd, rect, p, t_ref)
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    net = sr_net.Net(n, n, max_batch=max(batch, n_solve), phi_clip=4.0)
+    layers = sr_net.layers()
+    net.set_params(torch.from_numpy(synth.net_init(7, layers).astype(np.float32)).cuda())
+    t0 = time.perf_counter()
+    hist = train(net, trd, phis, steps, batch, lr)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del phis
+    ref_phi = generate_pairs(evd, rect, p, t_ref)
+    ref_m = (ref_phi < 0).to(torch.uint8)
+    rect_m = (rect < 0).to(torch.uint8)
+    losses, start_iou_net, start_iou_rect, rect_losses = [], [], [], []
+    tgt = torch.clamp(ref_phi, -4.0, 4.0) / 4.0
+    lossd = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for s in range(0, n_heldout, n_solve):
+        e = min(n_heldout, s + n_solve)
+        phi0 = net.forward(evd[s:e])
+        net.gradients(evd[s:e], ref_phi[s:e], lossd)
+        losses.append(lossd.item() * (e - s))
+        for k in range(e - s):
+            start_iou_net.append(_iou((phi0[k] < 0).to(torch.uint8), ref_m[s + k]))
+            start_iou_rect.append(_iou(rect_m, ref_m[s + k]))
+        rect_losses.append(0.5 * torch.mean((torch.clamp(rect, -4.0, 4.0) / 4.0 - tgt[s:e]) ** 2).item()
+                           * (e - s))
+    mx = 2 * t_ref
+    ev_s, ref_s = evd[:n_solve], [ref_m[k] for k in range(n_solve)]
+    plain = solve_plain(ev_s, rect, p, check=check, thr=0, max_iters=mx, ref=ref_s, iou=iou)
+    rb = solve_batched(ev_s, rect, p, check=check, thr=0, max_iters=mx, ref=ref_s, iou=iou)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    phi0 = net.forward(ev_s)
+    lb = solve_batched(ev_s, phi0, p, check=check, thr=0, max_iters=mx, ref=ref_s, iou=iou)
+    torch.cuda.synchronize()
+    t_lb = time.perf_counter() - t0
+    comps = lambda m: ndimage.label(m.cpu().numpy() > 0)[1]  # noqa: E731
+    return dict(
+        size=n, train_pairs=n_train, heldout=n_heldout, solved=n_solve, t_ref=t_ref,
+        train_steps=steps, batch=batch, rho=rho, sigma=sigma, pairs_s=t_pairs, train_s=t_train,
+        loss_first=hist[0], loss_last=float(np.mean(hist[-100:])),
+        heldout_loss=sum(losses) / n_heldout, heldout_rect_loss=sum(rect_losses) / n_heldout,
+        start_iou_net=float(np.mean(start_iou_net)), start_iou_rect=float(np.mean(start_iou_rect)),
+        accuracy=f"IoU >= {iou} with the plain mask after {t_ref} iterations", check=check,
+        max_iters=mx,
+        plain_iters=float(np.mean(plain.iters)), plain_reached=int(sum(plain.settled)),
+        plain_s_per_image=plain.seconds / n_solve,
+        rect_batched_iters=float(np.mean(rb.iters)), rect_batched_reached=int(sum(rb.settled)),
+        rect_batched_s_per_image=rb.seconds / n_solve,
+        learned_batched_iters=float(np.mean(lb.iters)), learned_batched_reached=int(sum(lb.settled)),
+        learned_batched_s_per_image=t_lb / n_solve,
+        speedup_learned_batched_vs_plain=(plain.seconds / n_solve) / (t_lb / n_solve),
+        topology_agree=int(sum(comps(a) == comps(b) for a, b in zip(plain.masks, lb.masks))))
+
+
 if __name__ == "__main__":
     import argparse
     import json
@@ -256,5 +347,10 @@ if __name__ == "__main__":
     ap.add_argument("--train", type=int, default=2048)
     ap.add_argument("--t-ref", type=int, default=3000)
     ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--scale", action="store_true",
+                    help="the configured scale: 20k pairs at 256^2, 1000 held-out images")
     a = ap.parse_args()
-    print(json.dumps(experiment(n=a.size, n_train=a.train, t_ref=a.t_ref, steps=a.steps)))
+    if a.scale:
+        print(json.dumps(experiment_scale(n=a.size, n_train=a.train, t_ref=a.t_ref, steps=a.steps)))
+    else:
+        print(json.dumps(experiment(n=a.size, n_train=a.train, t_ref=a.t_ref, steps=a.steps)))
