@@ -53,6 +53,22 @@ BYTES_PER_ITER_PX = {"prep": 44, "rowfft": 24, "colsolve": 24, "rowifft": 36, "w
 LAUNCHES_PER_ITER = {"prep": 3, "rowfft": 3, "colsolve": 3, "rowifft": 3, "wb_update": 1}
 KERNEL_NAMES = {"prep": "k_prep", "rowfft": "k_rowfft", "colsolve": "k_colsolve2",
                 "rowifft": "k_rowifft", "wb_update": "k_wb_update"}
+# column schedule 8 (small images): one kernel per inner step reads G and psi
+# and writes phi (12 B/px), in the colsolve class; no row-pass launches
+BYTES_PER_ITER_PX_SMALL = {"prep": 44, "colsolve": 36, "wb_update": 36}
+
+
+def _kernel_tables(schedule):
+    """Algorithmic bytes per pixel and iteration, launches per iteration and
+    kernel names of the solve path the schedule selects."""
+    names = dict(KERNEL_NAMES)
+    if schedule.get("col_schedule") == 7:
+        names["colsolve"] = "k_colsolve_rec"
+    if schedule.get("col_schedule") == 8:
+        names["colsolve"] = "k_solve_small"
+        return dict(BYTES_PER_ITER_PX_SMALL), {k: LAUNCHES_PER_ITER[k] for k in
+                                               BYTES_PER_ITER_PX_SMALL}, names
+    return dict(BYTES_PER_ITER_PX), dict(LAUNCHES_PER_ITER), names
 
 
 def _peaks():
@@ -67,7 +83,7 @@ def _peaks():
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
     for name in ("sr_kernels.cu", "sr_fft.cu", "sr_colrec.cu", "sr_tma.cuh", "sr_internal.h",
-                 "sr_dft.cuh"):
+                 "sr_dft.cuh", "sr_small.cu"):
         with open(os.path.join(ROOT, "paper_2003_12693_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -469,7 +485,8 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
     for k in range(args.steps):
         flush_l2(float(k))
         ctx.iterate(1)
-    ktimes = {name: ctx.kernel_times(name) for name in BYTES_PER_ITER_PX}
+    bytes_px, launches_it, names = _kernel_tables(schedule)
+    ktimes = {name: ctx.kernel_times(name) for name in bytes_px}
     ctx.kernel_times("reduce")
     ctx.profile_enable(False)
     event_overhead_us = ctx.profile_overhead_us()
@@ -477,21 +494,18 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
     kstats = {}
     step_us = 1e3 * total_ms / args.steps
     net = {name: max(1e3 * ms / max(n, 1) - event_overhead_us, 0.05) for name, (ms, n) in ktimes.items()}
-    net_sum = sum(net[name] * LAUNCHES_PER_ITER[name] for name in net)
+    net_sum = sum(net[name] * launches_it[name] for name in net)
     scale = step_us / net_sum if net_sum else 1.0
     for name, (ms, n) in ktimes.items():
         ev_us = 1e3 * ms / max(n, 1)
         in_graph_us = net[name] * scale
-        bytes_launch = BYTES_PER_ITER_PX[name] * P / LAUNCHES_PER_ITER[name]
+        bytes_launch = bytes_px[name] * P / launches_it[name]
         kstats[name] = {"launches": n, "event_avg_us": ev_us, "avg_us": in_graph_us,
-                        "share": in_graph_us * LAUNCHES_PER_ITER[name] / step_us,
+                        "share": in_graph_us * launches_it[name] / step_us,
                         "algorithmic_bytes_per_launch": bytes_launch,
                         "achieved_gbs": bytes_launch / (in_graph_us * 1e-6) / 1e9}
     dom = max(kstats, key=lambda k: kstats[k]["share"] or 0)
     ach = kstats[dom]["achieved_gbs"]
-    names = dict(KERNEL_NAMES)
-    if schedule.get("col_schedule") == 7:
-        names["colsolve"] = "k_colsolve_rec"
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": hbm_peak,
                 "unit": "GB/s", "frac": ach / hbm_peak, "peak_kind": peak_kind,
                 "traffic": _ncu_traffic(names[dom], wl.name)}
@@ -499,16 +513,19 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
                             "steps minus the event pair's own cost "
                             f"({event_overhead_us:.2f} us, the same pair around an empty kernel), "
                             "scaled so that the classes add up to the graph step")
-    if dom in ("rowfft", "colsolve", "rowifft"):
+    if names[dom] == "k_solve_small":
+        roofline["note"] = ("whole solve of an inner step in one CTA on one SM: bound by that "
+                            "CTA's FFT stages, recursion chains and barriers, not by DRAM")
+    elif dom in ("rowfft", "colsolve", "rowifft"):
         roofline["note"] = ("FFT pass on the L2-resident half spectrum (16.8 MB at 2048^2): bound by "
                             "instruction issue, shared memory and barriers, not by DRAM; the "
                             "iteration_roofline entry gives the whole iteration against HBM")
-    bytes_iter = sum(BYTES_PER_ITER_PX.values())
+    bytes_iter = sum(bytes_px.values())
     it_gbs = bytes_iter * P / (total_ms / 1e3 / args.steps) / 1e9
     iteration_roofline = {"algorithmic_bytes_per_px": bytes_iter, "achieved_gbs": it_gbs,
                           "frac_of_measured_peak": it_gbs / hbm_peak,
                           "frac_of_nominal_8tbs": it_gbs / 8000.0, "kernels": kstats,
-                          "kernels_sum_us": sum(v["avg_us"] * LAUNCHES_PER_ITER[k]
+                          "kernels_sum_us": sum(v["avg_us"] * launches_it[k]
                                                 for k, v in kstats.items()),
                           "event_overhead_us": event_overhead_us,
                           "band_tiles": band_tiles}

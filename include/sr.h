@@ -88,7 +88,8 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
 /* Release everything the context owns.  NULL is ignored. */
 void sr_destroy(sr_ctx* ctx);
 
-/* Message of the last failing call on this context ("" if none). */
+/* Message of the last failing call on this context ("" if none); with NULL,
+ * why the calling thread's last sr_create failed. */
 const char* sr_last_error(const sr_ctx* ctx);
 const char* sr_status_string(sr_status s);
 
@@ -284,7 +285,13 @@ sr_status sr_phi_step_noalloc(int H, int W, const sr_params* p, const float* g,
  *                 exactly by its scalar factorisation into a forward and a
  *                 backward first-order recursion (warm-up long enough that
  *                 the truncated start is below 2^-27 relative; available
- *                 when tau mu <= about 8)
+ *                 when tau mu <= about 8); 8 = the whole solve of one inner
+ *                 step in one CTA (row transforms, the recursions of 7 and
+ *                 the inverse row transforms, the half spectrum kept in
+ *                 shared memory) for power-of-two images with
+ *                 H * W / 32 <= 512 and W <= 1024, where launches and not
+ *                 bytes bound the step; the autotuner compares it with the
+ *                 best row pair plus column pass
  *   tuned_us: measured microseconds of one row pair plus one column pass
  *             when the autotuner chose the schedule, else 0.
  * Sizes below W = 32 use fixed kernels and report row_threads = 0.

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsr.so")
 SOURCES = ["sr_kernels.cu", "sr_fft.cu", "sr_fftgen.cu", "sr_api.cu", "sr_noalloc.cu", "sr_net.cu",
-           "sr_wfix.cu", "sr_inner.cu", "sr_colrec.cu", "sr_aos.cu", "sr3.cu"]
+           "sr_wfix.cu", "sr_inner.cu", "sr_colrec.cu", "sr_aos.cu", "sr3.cu", "sr_small.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 
@@ -30,10 +30,9 @@ def _nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "sr_internal.h"), os.path.join(CSRC, "sr_wfix.h"),
-              os.path.join(CSRC, "sr_inner.h"),
-              os.path.join(INCLUDE, "sr.h"),
-              os.path.join(INCLUDE, "sr_net.h")]
+    # every header the sources may include
+    files += [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".h", ".cuh"))]
+    files += [os.path.join(INCLUDE, f) for f in sorted(os.listdir(INCLUDE)) if f.endswith(".h")]
     return files
 
 

@@ -346,6 +346,8 @@ bool sched_valid(const sr_ctx* c, const sr_schedule& sc) {
   if (sc.row_values_per_thread != 8 && sc.row_values_per_thread != 16) return false;
   if (sc.col_schedule == srk::kColRec) {
     if (c->rec_R <= 0) return false;
+  } else if (sc.col_schedule == srk::kColSmall) {
+    if (c->rec_R <= 0 || !srk::solve_small_supported(c->geo, c->rec_R)) return false;
   } else {
     if (sc.col_schedule < 0 || sc.col_schedule > 6) return false;
     if (sc.col_schedule == 3 && !c->tm_X_ok) return false;
@@ -375,6 +377,12 @@ cudaError_t sched_configure(sr_ctx* c, const sr_schedule& sc) {
   if (e == cudaSuccess) e = srk::launch_rowifft2(ia, true, le, sc.row_threads, nullptr, true);
   if (e != cudaSuccess) return e;
   if (sc.col_schedule == srk::kColRec) return cudaSuccess;
+  if (sc.col_schedule == srk::kColSmall) {
+    srk::SmallArgs sa{};
+    sa.geo = c->geo;
+    sa.rec_R = c->rec_R;
+    return srk::launch_solve_small(sa, nullptr, true);
+  }
   if (sc.col_schedule == 3) {
     e = srk::launch_colsolve_tma(ca, c->tm_X, 0, nullptr, true);
     int per_sm = 0;
@@ -416,6 +424,9 @@ bool make_tensor_map_2d(CUtensorMap* map, const void* base, int rows, int cols, 
              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+// why the calling thread's last sr_create failed (sr_last_error(NULL))
+thread_local std::string g_create_err;
 
 std::mutex g_tune_mutex;
 std::map<std::pair<int, int>, std::pair<int, sr_schedule>> g_tuned;  // (H, W) -> (device, schedule)
@@ -553,10 +564,33 @@ sr_status autotune(sr_ctx* c) {
       best.col_schedule = cs;
     }
   }
+  best.tuned_us = best_row + best_col;
+  // the one-CTA solve of small images replaces the row pair and the column
+  // pass together: it competes with their sum
+  if (err == cudaSuccess) {
+    sr_schedule sc = best;
+    sc.col_schedule = srk::kColSmall;
+    if (sched_valid(c, sc) && (err = sched_configure(c, sc)) == cudaSuccess) {
+      srk::SmallArgs sa{};
+      sa.geo = c->geo;
+      sa.G = c->G;
+      sa.psi_in = c->tmp1;
+      sa.out = c->tmp2;
+      sa.tws16 = c->fft_row.tws16;
+      sa.twN = c->tw_n;
+      sa.rec = c->rec;
+      sa.rec_R = c->rec_R;
+      float us = 0.f;
+      err = time_it([&] { return srk::launch_solve_small(sa, s, false); }, &us);
+      if (err == cudaSuccess && us < best.tuned_us) {
+        best.col_schedule = srk::kColSmall;
+        best.tuned_us = us;
+      }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (err != cudaSuccess) return cuda_fail(c, err, "FFT schedule autotuner");
-  best.tuned_us = best_row + best_col;
   c->sched = best;
   SR_CUDA(c, sched_configure(c, best));
   std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -644,6 +678,19 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
     return run_kernel(c, SR_KCLASS_ROWIFFT, s, "k_add_half", [&] {
       return srk::launch_add_half(load_src ? nullptr : psi_in, c->G2, psi_out, c->geo, s);
     });
+  }
+  if (c->fft2 && c->sched.col_schedule == srk::kColSmall) {
+    srk::SmallArgs sa{};
+    sa.geo = c->geo;
+    sa.G = src;
+    sa.psi_in = load_src ? nullptr : psi_in;
+    sa.out = psi_out;
+    sa.tws16 = c->fft_row.tws16;
+    sa.twN = c->tw_n;
+    sa.rec = c->rec;
+    sa.rec_R = c->rec_R;
+    return run_kernel(c, SR_KCLASS_COLSOLVE, s, "k_solve_small",
+                      [&] { return srk::launch_solve_small(sa, s, false); });
   }
   srk::RowFwdArgs fa{};
   fa.geo = c->geo;
@@ -914,7 +961,7 @@ const char* sr_status_string(sr_status s) {
   return "unknown status";
 }
 
-const char* sr_last_error(const sr_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+const char* sr_last_error(const sr_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
 
 sr_status sr_params_default(sr_params* p) {
   if (!p) return SR_EINVAL;
@@ -986,6 +1033,7 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   c->geo.logN = ilog2(W);  // used by the power-of-two paths only
 
   auto bail = [&](sr_status s) {
+    g_create_err = c->err.empty() ? std::string(sr_status_string(s)) : c->err;
     sr_destroy(c);
     return s;
   };

@@ -299,6 +299,26 @@ constexpr int kColRec = 7;
 // warm-up length for the slowest decay r_max (0 if none of the buckets suffices)
 int colsolve_rec_radius(double r_max);
 cudaError_t launch_colsolve_rec(const ColArgs& a, cudaStream_t s);
+
+// The whole solve of one inner step in one CTA (sr_small.cu, column schedule
+// 8), for power-of-two images whose rows fit one pass of kSmallThreads
+// threads at 16 values each (M * L / 16 <= kSmallThreads, L <= 512): row R2C,
+// column recursions (rec_R in 8..32), row C2R with psi += result.
+constexpr int kSmallThreads = 512;
+constexpr int kColSmall = 8;
+struct SmallArgs {
+  Geo geo;
+  const float* G;        // right-hand side (increment or the full one)
+  const float* psi_in;   // added to the result; null: out = solution
+  float* out;            // may alias psi_in
+  const float2* tws16;   // stage twiddles of the row transform (16 values per thread)
+  const float2* twN;     // exp(-2 pi i k / N), k < L
+  const float4* rec;     // per-column (r, s) pairs of the recursions
+  int rec_R;
+};
+bool solve_small_supported(const Geo& geo, int rec_R);
+size_t solve_small_smem(const Geo& geo);
+cudaError_t launch_solve_small(const SmallArgs& a, cudaStream_t s, bool set_attr);
 // Neumann solve helpers: the even extension of each row (out is M x 2N) and
 // out = psi + T[:, :N] (T is M x 2N; psi may be null)
 cudaError_t launch_mirror_rows(const float* in, float* out, const Geo& geo, cudaStream_t s);

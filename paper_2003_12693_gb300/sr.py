@@ -176,10 +176,10 @@ def _check(status: int, ctx) -> int:
     if status in (SR_OK, SR_ENOTCONVERGED):
         return status
     msg = lib().sr_status_string(status).decode()
-    if ctx is not None and ctx.handle:
-        detail = lib().sr_last_error(ctx.handle).decode()
-        if detail:
-            msg += ": " + detail
+    # without a context: why the last sr_create of this thread failed
+    detail = lib().sr_last_error(ctx.handle if ctx is not None and ctx.handle else None).decode()
+    if detail and detail != msg:
+        msg += ": " + detail
     raise SRError(status, msg)
 
 

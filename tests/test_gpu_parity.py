@@ -53,7 +53,7 @@ def test_fft_solve_eigenfunctions():
 
 
 @pytest.mark.parametrize("shape", [(64, 32), (128, 256), (512, 512), (256, 2048), (4096, 64),
-                                   (1024, 256), (2048, 64)])
+                                   (1024, 256), (2048, 64), (128, 128), (16, 1024)])
 def test_every_fft_schedule_matches_oracle(shape):
     """The autotuner may pick any schedule; each one must compute the same solve."""
     H, W = shape
@@ -69,7 +69,7 @@ def test_every_fft_schedule_matches_oracle(shape):
     tried = 0
     for vpt in (16, 8):
         for threads in (32, 64, 128, 256, 512):
-            for col in range(8):
+            for col in range(9):
                 try:
                     ctx.set_schedule(vpt, threads, col)
                 except sr.SRError as e:
@@ -86,13 +86,15 @@ def test_every_fft_schedule_matches_oracle(shape):
 
 
 @pytest.mark.parametrize("shape", [(16, 32), (48, 32), (64, 32), (256, 64), (2048, 32),
-                                   (4096, 32)])
+                                   (4096, 32), (128, 128), (16, 1024), (32, 64)])
 @pytest.mark.parametrize("tau,mu", [(0.1, 8.0), (1.0, 8.0), (0.01, 1.0)])
-def test_column_recursion_eigenfunctions(shape, tau, mu):
+@pytest.mark.parametrize("col", [7, 8])
+def test_column_recursion_eigenfunctions(shape, tau, mu, col):
     """Column schedule 7 replaces the column FFT by the forward and backward
-    recursions that factor the column operator.  Pure Fourier modes must come
-    out divided by their own symbol of Eq. (32), including the packed DC and
-    Nyquist column (b = 0, W/2), the Nyquist row (a = H/2) and conjugate
+    recursions that factor the column operator; schedule 8 runs the row
+    transforms and the same recursions in one CTA.  Pure Fourier modes must
+    come out divided by their own symbol of Eq. (32), including the packed DC
+    and Nyquist column (b = 0, W/2), the Nyquist row (a = H/2) and conjugate
     partners (a, H - a); tau mu = 8 needs the longest warm-up (r_0 = 0.70),
     and H = 16 or 48 is shorter than the warm-up (it wraps)."""
     H, W = shape
@@ -100,7 +102,11 @@ def test_column_recursion_eigenfunctions(shape, tau, mu):
     tuned = ctx.get_schedule()
     if tuned["row_threads"] == 0:
         pytest.skip("sizes below W = 32 use the fixed passes")
-    ctx.set_schedule(tuned["row_values_per_thread"], tuned["row_threads"], 7)
+    try:
+        ctx.set_schedule(tuned["row_values_per_thread"], tuned["row_threads"], col)
+    except sr.SRError as e:
+        assert e.status == sr.SR_EINVAL
+        pytest.skip("schedule not available at this size and tau mu")
     i, j = np.mgrid[0:H, 0:W].astype(float)
     modes = [(0, 0), (1, 0), (0, W // 2), (H // 2, W // 2), (H // 2, 0), (5, 3), (H - 5, 3),
              (H - 1, W // 2 - 1), (3, W // 2), (H // 3, 1)]
