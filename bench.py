@@ -58,9 +58,17 @@ KERNEL_NAMES = {"prep": "k_prep", "rowfft": "k_rowfft", "colsolve": "k_colsolve2
 BYTES_PER_ITER_PX_SMALL = {"prep": 44, "colsolve": 36, "wb_update": 36}
 
 
-def _kernel_tables(schedule):
+# resident iterations (sr_set_resident): one launch per sr_iterate call loads
+# phi, w1, w2, e1, e2, g (24 B/px) and stores phi, w1, w2, e1, e2 (20 B/px);
+# everything else stays in the cluster's shared memory
+BYTES_PER_ITER_PX_RESIDENT = {"resident": 44}
+
+
+def _kernel_tables(schedule, resident=False):
     """Algorithmic bytes per pixel and iteration, launches per iteration and
     kernel names of the solve path the schedule selects."""
+    if resident:
+        return dict(BYTES_PER_ITER_PX_RESIDENT), {"resident": 1}, {"resident": "k_resident"}
     names = dict(KERNEL_NAMES)
     if schedule.get("col_schedule") == 7:
         names["colsolve"] = "k_colsolve_rec"
@@ -83,7 +91,7 @@ def _peaks():
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
     for name in ("sr_kernels.cu", "sr_fft.cu", "sr_colrec.cu", "sr_tma.cuh", "sr_internal.h",
-                 "sr_dft.cuh", "sr_small.cu"):
+                 "sr_dft.cuh", "sr_small.cu", "sr_point.cuh", "sr_resident.cu"):
         with open(os.path.join(ROOT, "paper_2003_12693_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -425,6 +433,14 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
     params = sr.make_params(win_radius=wl.R, d=wl.d)
     stream = torch.cuda.current_stream()
     ctx = sr.Context(wl.H, wl.W, params, stream)
+    resident = False
+    if args.resident != "off":
+        try:
+            ctx.set_resident(True)
+            resident = True
+        except sr.SRError as e:
+            if args.resident == "on" or e.status != sr.SR_EUNSUPPORTED:
+                raise
     f_d = torch.from_numpy(f).to(dev)
     phi0_d = torch.from_numpy(phi0).to(dev)
     ctx.edge_function(f_d)
@@ -485,7 +501,7 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
     for k in range(args.steps):
         flush_l2(float(k))
         ctx.iterate(1)
-    bytes_px, launches_it, names = _kernel_tables(schedule)
+    bytes_px, launches_it, names = _kernel_tables(schedule, resident)
     ktimes = {name: ctx.kernel_times(name) for name in bytes_px}
     ctx.kernel_times("reduce")
     ctx.profile_enable(False)
@@ -513,7 +529,11 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
                             "steps minus the event pair's own cost "
                             f"({event_overhead_us:.2f} us, the same pair around an empty kernel), "
                             "scaled so that the classes add up to the graph step")
-    if names[dom] == "k_solve_small":
+    if names[dom] == "k_resident":
+        roofline["note"] = ("whole outer iterations in one cluster of 8 CTAs with the state in "
+                            "shared memory: bound by the cluster barriers and on-chip latency of "
+                            "each phase, not by DRAM (it reads and writes the state once per call)")
+    elif names[dom] == "k_solve_small":
         roofline["note"] = ("whole solve of an inner step in one CTA on one SM: bound by that "
                             "CTA's FFT stages, recursion chains and barriers, not by DRAM")
     elif dom in ("rowfft", "colsolve", "rowifft"):
@@ -575,7 +595,7 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
                    "l2": "flushed between timed steps, outside the events: 256 MiB write, "
                          "then 256 MiB read (no dirty flush lines left in L2)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "fft_schedule": schedule},
+                   "fft_schedule": schedule, "resident": resident},
         "roofline": roofline,
         "iteration_roofline": iteration_roofline,
         "cpu_baseline": cpu,
@@ -607,6 +627,9 @@ def main():
                     help="print only the warm-start network sample (profiling runs)")
     ap.add_argument("--net-steps", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--resident", default="auto", choices=["auto", "on", "off"],
+                    help="sr_set_resident: whole iterations in one cluster launch where the "
+                         "image size allows it (auto), always (on: fail otherwise) or never")
     ap.add_argument("--prewarm-s", type=float, default=1.0,
                     help="untimed back-to-back steps before the warm-up steps (clock ramp)")
     args = ap.parse_args()

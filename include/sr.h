@@ -229,6 +229,31 @@ sr_status sr_set_phi_solver(sr_ctx* ctx, int solver);
  * image planes; graphs are rebuilt on the next sr_iterate. */
 sr_status sr_set_boundary(sr_ctx* ctx, int neumann);
 
+/* Resident outer iterations for small images.  on = 1: sr_iterate runs its
+ * outer iterations of Alg. 1 in ONE launch per call, with the whole state
+ * (phi, w at both parities, e, g, div e, the right-hand side and the half
+ * spectrum) held in the shared memory of one cluster of 8 CTAs -- CTA q owns
+ * rows [q H/8, (q+1) H/8) -- for all the iterations of the call; neighbour
+ * rows, window halos and the column recursions' warm-ups are read from the
+ * other CTAs' shared memory (distributed shared memory), and the phases of an
+ * iteration are separated by cluster barriers instead of kernel boundaries.
+ * Global memory is read once and written once per call.  The stopping test
+ * of Sec. 4 (FP64 sums, every check_every iterations and after the last) is
+ * evaluated on the device; sr_iterate reads the iteration count and the
+ * residual back only when tol > 0 or rel_change is requested.  The
+ * per-pixel arithmetic is that of the tiled kernels; the column solve is
+ * the recursion pass of column schedule 7 with one run per CTA, so results
+ * agree with the default path to rounding, not bit for bit.
+ * Supported: W in {32, 64, 128, 256}, H a multiple of 8 with H >= 16, the
+ * state within 220 KB of shared memory per CTA (H * W <= 16384 at R <= 8),
+ * the periodic FFT solve with the column recursions available (tau mu <=
+ * about 8), the soft-threshold w update and no inner exit; otherwise
+ * SR_EUNSUPPORTED.  While the context's configuration is changed to one of
+ * those (sr_set_boundary, sr_set_phi_solver, sr_set_w_sweeps) sr_iterate
+ * uses the default path.  Groups keep the default path.  on = 0 restores
+ * the default path. */
+sr_status sr_set_resident(sr_ctx* ctx, int on);
+
 /* The AOS solve alone (device buffers, contiguous H x W, not aliased):
  * out = 1/2 [ (I - 2 tau mu A_1)^{-1} rhs + (I - 2 tau mu A_2)^{-1} rhs ].
  * The first call allocates two image planes in the context. */
@@ -324,7 +349,8 @@ long long sr_kernel_launches(const sr_ctx* ctx, int reset);
 #define SR_KCLASS_WB_UPDATE 3    /* repulsion + shrink + projection + Bregman */
 #define SR_KCLASS_REDUCE 4       /* FP64 stopping-test reduction */
 #define SR_KCLASS_PREP 5         /* repulsion window sum + right-hand side */
-#define SR_KCLASS_COUNT 6
+#define SR_KCLASS_RESIDENT 6     /* whole outer iterations resident on chip */
+#define SR_KCLASS_COUNT 7
 sr_status sr_profile_enable(sr_ctx* ctx, int enable);
 /* Microseconds the profiling mode's event pair adds to a kernel's measured
  * time: the median over 65 event pairs around an empty kernel launched the

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsr.so")
 SOURCES = ["sr_kernels.cu", "sr_fft.cu", "sr_fftgen.cu", "sr_api.cu", "sr_noalloc.cu", "sr_net.cu",
-           "sr_wfix.cu", "sr_inner.cu", "sr_colrec.cu", "sr_aos.cu", "sr3.cu", "sr_small.cu"]
+           "sr_wfix.cu", "sr_inner.cu", "sr_colrec.cu", "sr_aos.cu", "sr3.cu", "sr_small.cu", "sr_resident.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -108,6 +108,12 @@ struct sr_ctx {
   float* wfx2 = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_kernels = 0;
+  // outer iterations resident in shared memory (sr_set_resident)
+  int resident = 0;
+  size_t res_smem = 0;
+  srk::ResMember* res_dev = nullptr;  // the image's description at parity 0 and 1
+  int* res_done = nullptr;            // iterations the last launch ran
+  int* res_done_host = nullptr;       // pinned copy
 
   long long launches = 0;
   bool profile = false;
@@ -940,6 +946,48 @@ sr_status read_residual(sr_ctx* c, double* rel) {
   return SR_OK;
 }
 
+// the configuration the resident kernel implements
+bool resident_ok(const sr_ctx* c) {
+  return c->fft2 && c->phi_solver == 0 && c->w_sweeps == 0 && c->prm.inner_tol <= 0.f &&
+         srk::resident_supported(c->geo, c->mod.R, c->rec_R);
+}
+
+// sr_iterate with the state resident in shared memory: one launch runs up to
+// max_outer outer iterations with the stopping test of Sec. 4 on the device.
+sr_status iterate_resident(sr_ctx* c, int max_outer, double tol, int* outer_done,
+                           double* rel_change) {
+  srk::ResArgs a{};
+  a.members = c->res_dev + c->cur;
+  a.max_outer = max_outer;
+  a.tol = tol;
+  a.check_every = c->prm.check_every;
+  a.check_last = rel_change != nullptr;
+  sr_status st = run_kernel(c, SR_KCLASS_RESIDENT, c->stream, "k_resident", [&] {
+    return srk::launch_resident(a, 1, c->geo, c->res_smem, c->stream, false);
+  });
+  if (st != SR_OK) return st;
+  int done = max_outer;
+  double rel = NAN;
+  if (tol > 0.0 || rel_change != nullptr) {
+    SR_CUDA(c, cudaMemcpyAsync(c->res_done_host, c->res_done, sizeof(int), cudaMemcpyDeviceToHost,
+                               c->stream));
+    st = read_residual(c, &rel);  // synchronises the stream
+    if (st == SR_OK || st == SR_ENONFINITE) done = *c->res_done_host;
+  }
+  c->cur ^= done & 1;
+  c->iters += done;
+  c->inner_steps += (long long)done * c->prm.inner_S;
+  if (outer_done) *outer_done = done;
+  if (rel_change) *rel_change = rel;
+  if (st != SR_OK) return st;
+  if (c->profile) {
+    st = flush_profile(c);
+    if (st != SR_OK) return st;
+  }
+  if (tol > 0.0 && !(rel <= tol)) return SR_ENOTCONVERGED;
+  return SR_OK;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -993,10 +1041,12 @@ void sr_destroy(sr_ctx* c) {
                   c->tw_n, c->aM, c->aN, c->partials, c->red, c->err_dev, c->gen_tab,
                   c->tws[0], c->tws[1], c->tws[2], c->tws[3], c->wfx1, c->wfx2,
                   c->X2, c->rec, c->aos_T1, c->aos_X2, c->tw_row2, c->tw_n2,
-                  c->tws2[0], c->tws2[1], c->G2, c->Xn, c->Xn2, c->rec2};
+                  c->tws2[0], c->tws2[1], c->G2, c->Xn, c->Xn2, c->rec2, c->res_dev,
+                  c->res_done};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->red_host) cudaFreeHost(c->red_host);
+  if (c->res_done_host) cudaFreeHost(c->res_done_host);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
@@ -1237,6 +1287,7 @@ sr_status sr_iterate(sr_ctx* c, int max_outer, double tol, int* outer_done, doub
   if (outer_done) *outer_done = 0;
   if (max_outer < 0 || !std::isfinite(tol)) return fail(c, SR_EINVAL, "bad max_outer or tol");
   if (max_outer == 0) return SR_OK;
+  if (c->resident && resident_ok(c)) return iterate_resident(c, max_outer, tol, outer_done, rel_change);
   const bool inner_exit = c->prm.inner_tol > 0.f;
   const bool use_graph = !c->profile && !inner_exit;
   if (use_graph) {
@@ -1509,6 +1560,59 @@ long long sr_kernel_launches(const sr_ctx* c, int reset) {
   const long long n = c->launches;
   if (reset) const_cast<sr_ctx*>(c)->launches = 0;
   return n;
+}
+
+sr_status sr_set_resident(sr_ctx* c, int on) {
+  if (!c || on < 0 || on > 1) return SR_EINVAL;
+  if (!on) {
+    c->resident = 0;
+    return SR_OK;
+  }
+  if (!resident_ok(c))
+    return fail(c, SR_EUNSUPPORTED,
+                "resident iterations need W in {32, 64, 128, 256}, H a multiple of 8 (>= 16), "
+                "the state within one cluster's shared memory, the periodic FFT solve with the "
+                "column recursions and Eqs. (41)-(42)");
+  const size_t smem = srk::resident_smem(c->geo, c->mod.R, c->rec_R);
+  srk::ResArgs probe{};
+  const cudaError_t pe = srk::launch_resident(probe, 1, c->geo, smem, nullptr, true);
+  if (pe == cudaErrorNotSupported)
+    return fail(c, SR_EUNSUPPORTED, "a cluster of 8 CTAs with this shared memory does not fit");
+  SR_CUDA(c, pe);
+  if (!c->res_dev) {
+    cudaError_t e = dev_alloc((void**)&c->res_dev, 2 * sizeof(srk::ResMember));
+    if (e == cudaSuccess) e = dev_alloc((void**)&c->res_done, sizeof(int));
+    if (e == cudaSuccess) e = host_alloc((void**)&c->res_done_host, sizeof(int));
+    if (e == cudaErrorMemoryAllocation) return fail(c, SR_ENOMEM, "allocation failed");
+    SR_CUDA(c, e);
+  }
+  srk::ResMember mb[2];
+  for (int p = 0; p < 2; ++p) {
+    srk::ResMember& r = mb[p];
+    r = srk::ResMember{};
+    r.geo = c->geo;
+    r.mod = c->mod;
+    r.inner_S = c->prm.inner_S;
+    r.rec_R = c->rec_R;
+    r.cur = p;
+    r.g = c->g;
+    for (int q = 0; q < 2; ++q) {
+      r.phi[q] = c->phi[q];
+      r.w1[q] = c->w1[q];
+      r.w2[q] = c->w2[q];
+    }
+    r.e1 = c->e1;
+    r.e2 = c->e2;
+    r.tws16 = c->fft_row.tws16;
+    r.twN = c->tw_n;
+    r.rec = c->rec;
+    r.done = c->res_done;
+    r.red = c->red;
+  }
+  SR_CUDA(c, cudaMemcpy(c->res_dev, mb, sizeof(mb), cudaMemcpyHostToDevice));
+  c->res_smem = smem;
+  c->resident = 1;
+  return SR_OK;
 }
 
 sr_status sr_set_phi_solver(sr_ctx* c, int solver) {

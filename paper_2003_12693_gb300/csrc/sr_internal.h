@@ -319,6 +319,45 @@ struct SmallArgs {
 bool solve_small_supported(const Geo& geo, int rec_R);
 size_t solve_small_smem(const Geo& geo);
 cudaError_t launch_solve_small(const SmallArgs& a, cudaStream_t s, bool set_attr);
+
+// Outer iterations with the state resident in shared memory (sr_resident.cu):
+// one cluster of kResC CTAs per image, CTA q owning rows [q M/kResC,
+// (q+1) M/kResC); N in {32, 64, 128, 256}, M a multiple of kResC (>= 2 kResC),
+// the recursion column solve (rec_R > 0), periodic boundary.
+constexpr int kResC = 8;
+constexpr int kResThreads = 512;
+constexpr size_t kResMaxSmem = 220 * 1024;
+struct ResMember {
+  Geo geo;
+  Model mod;
+  int inner_S;
+  int rec_R;
+  int cur;               // parity of the state buffers on entry
+  const float* g;
+  float* phi[2];
+  float* w1[2];
+  float* w2[2];
+  float* e1;             // e = b - w (one buffer, updated in place)
+  float* e2;
+  const float2* tws16;   // stage twiddles of the row transform (16 values per thread)
+  const float2* twN;     // exp(-2 pi i k / N), k < L
+  const float4* rec;     // per-column (r, s) pairs of the column recursions
+  int* done;             // outer iterations run (written once, at the end)
+  double* red;           // last stopping test: ||phi^{k+1} - phi^k||^2, ||phi^k||^2
+};
+struct ResArgs {
+  const ResMember* members;  // one per cluster
+  int max_outer;
+  double tol;                // > 0: stop at the first check with rel <= tol
+  int check_every;           // checks after every check_every-th and the last iteration
+  int check_last;            // tol <= 0: evaluate the test after the last iteration
+};
+size_t resident_smem(const Geo& geo, int R, int rec_R);
+bool resident_supported(const Geo& geo, int R, int rec_R);
+// set_attr: raise the shared-memory limit and check that a cluster fits
+// (cudaErrorNotSupported if not); otherwise launch `members` clusters.
+cudaError_t launch_resident(const ResArgs& a, int members, const Geo& geo, size_t smem,
+                            cudaStream_t s, bool set_attr);
 // Neumann solve helpers: the even extension of each row (out is M x 2N) and
 // out = psi + T[:, :N] (T is M x 2N; psi may be null)
 cudaError_t launch_mirror_rows(const float* in, float* out, const Geo& geo, cudaStream_t s);

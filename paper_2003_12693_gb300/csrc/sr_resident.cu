@@ -1,0 +1,486 @@
+// Whole outer iterations of Alg. 1 for small images in one launch, with the
+// state resident on chip.
+//
+// An image of M x N pixels is owned by one cluster of kResC CTAs; CTA q holds
+// rows [q M/kResC, (q+1) M/kResC) of every plane (phi, w at two parities, e,
+// g, div e, the right-hand side, the half spectrum and the column solve's
+// output) in its shared memory for all the iterations of the launch.  The
+// phases of one outer iteration are those of the tiled kernels, and they use
+// the same per-pixel arithmetic (sr_point.cuh):
+//   per inner step s (Eq. (37), increment form):
+//     right-hand side G of the CTA's rows (window sum of Sec. 4 only when a
+//       pixel of the CTA is in the narrow band, exact as in k_prep)
+//     row R2C transforms of the CTA's rows                      (local)
+//     cluster barrier
+//     column solve by the factored recursions of Eq. (32)'s operator
+//       (sr_colrec.cu), reading the other CTAs' spectrum rows    (DSMEM)
+//     row C2R transforms, psi += result                         (local)
+//     cluster barrier
+//   w/b update of Eqs. (41), (42), (40), (23) into the other w parity, e in
+//   place; on check iterations the FP64 sums of the stopping test
+//   cluster barrier; the stopping decision from the kResC partial sums, taken
+//   identically by every CTA.
+// Neighbour rows of the stencils and the window halos come from the other
+// CTAs' shared memory through the cluster's distributed shared memory.  Global
+// memory is read once at the start and written once at the end, so a launch
+// costs one load and one store of the state plus the on-chip iterations
+// instead of 2S + 1 dependent kernel launches (3S + 1 for the three-pass
+// solve) per iteration with every plane crossing L2.
+//
+// All control flow that contains a cluster barrier is uniform over the
+// cluster: the loop bounds are launch arguments and the stopping decision is
+// computed by every CTA from the same partial sums in the same order.
+#include <cooperative_groups.h>
+
+#include "sr_dft.cuh"
+#include "sr_internal.h"
+#include "sr_point.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace srk {
+namespace res {
+
+using namespace srk::cdft;
+
+// Shared-memory layout of one CTA, identical across the cluster (offsets in
+// floats from the dynamic shared-memory base, each 16-byte aligned).
+struct Lay {
+  int RPC, PL, SW;  // rows per CTA, floats per plane, staged window row width N + 2R
+  int psi, phik, w1[2], w2[2], e1, e2, g, D, G, X, X2, scr, part;
+  int total;
+};
+
+__host__ __device__ inline int lay_take(int& o, int n) {
+  const int r = o;
+  o += (n + 3) & ~3;
+  return r;
+}
+
+__host__ __device__ inline Lay make_lay(int M, int N, int R, int rec_R) {
+  Lay l;
+  l.RPC = M / kResC;
+  l.PL = l.RPC * N;
+  l.SW = N + 2 * R;
+  int o = 0;
+  l.psi = lay_take(o, l.PL);
+  l.phik = lay_take(o, l.PL);
+  l.w1[0] = lay_take(o, l.PL);
+  l.w1[1] = lay_take(o, l.PL);
+  l.w2[0] = lay_take(o, l.PL);
+  l.w2[1] = lay_take(o, l.PL);
+  l.e1 = lay_take(o, l.PL);
+  l.e2 = lay_take(o, l.PL);
+  l.g = lay_take(o, l.PL);
+  l.D = lay_take(o, l.PL);
+  l.G = lay_take(o, l.PL);
+  l.X = lay_take(o, l.PL);   // RPC x L complex = PL floats
+  l.X2 = lay_take(o, l.PL);
+  // scratch, one use per phase: the window's staged u planes and vertical
+  // sums; the row transforms' exchange rows (+1 row for idle thread slots);
+  // the column recursions' forward values of the run and the warm-up after it
+  const int L = N / 2, RS = L + L / 16;
+  const int win = 2 * (l.RPC + 2 * R) * l.SW + 2 * l.RPC * l.SW;
+  const int fft = 2 * (l.RPC + 1) * RS;
+  const int colu = 2 * (l.RPC + rec_R) * L;
+  int sc = win > fft ? win : fft;
+  sc = sc > colu ? sc : colu;
+  l.scr = lay_take(o, sc);
+  l.part = lay_take(o, 4);  // two doubles: this CTA's stopping-test sums
+  l.total = o;
+  return l;
+}
+
+// Fixed-order block reduction of two doubles into out[0..1] (thread 0).
+__device__ __forceinline__ void block_sum2(double a, double b, double* out) {
+  __shared__ double red[2][kResThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    b += __shfl_down_sync(0xffffffffu, b, off);
+  }
+  if (lane == 0) {
+    red[0][warp] = a;
+    red[1][warp] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < kResThreads / 32; ++w) {
+      s0 += red[0][w];
+      s1 += red[1][w];
+    }
+    out[0] = s0;
+    out[1] = s1;
+  }
+}
+
+template <int LOGL>
+__global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
+  constexpr int L = 1 << LOGL, E = 16, LOGTP = LOGL - 4, TP = 1 << LOGTP;
+  constexpr int RS = L + L / 16;
+  constexpr int T = kResThreads;
+  extern __shared__ __align__(16) float sm[];
+  __shared__ ResMember mb;
+  __shared__ float* rbase[kResC];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x;
+  if (tid == 0) mb = a.members[blockIdx.x / kResC];
+  if (tid < kResC) rbase[tid] = cl.map_shared_rank(sm, tid);
+  __syncthreads();
+  const Model& m = mb.mod;
+  const int M = mb.geo.M, N = mb.geo.N, R = m.R;
+  const Lay ly = make_lay(M, N, R, mb.rec_R);
+  const int RPC = ly.RPC, PL = ly.PL, r0 = rank * RPC;
+
+  // row gi (0 <= gi < M) of the plane at offset off, in the owner CTA
+  auto row_at = [&](int off, int gi) -> const float* {
+    const int q = gi / RPC;
+    return rbase[q] + off + (gi - q * RPC) * N;
+  };
+
+  // ---- load the CTA's rows of the state
+  {
+    const int c0 = mb.cur;
+    const size_t gb = (size_t)r0 * N;
+    const float* src[6] = {mb.phi[c0], mb.w1[c0], mb.w2[c0], mb.e1, mb.e2, mb.g};
+    const int dst[6] = {ly.psi, ly.w1[0], ly.w2[0], ly.e1, ly.e2, ly.g};
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      const float4* s4 = reinterpret_cast<const float4*>(src[p] + gb);
+      float4* d4 = reinterpret_cast<float4*>(sm + dst[p]);
+      for (int q = tid; q < PL / 4; q += T) d4[q] = __ldg(s4 + q);
+    }
+  }
+  cl.sync();
+
+  // ---- separable window sum of u = h(x) w over the CTA's rows, Sec. 4:
+  // v1, v2 ([RPC][N]) replace the staged u planes at the start of scr
+  auto window = [&](int off_x, int off_w1, int off_w2) {
+    const int SW = ly.SW, SH = RPC + 2 * R;
+    float* u1 = sm + ly.scr;
+    float* u2 = u1 + SH * SW;
+    float* V1 = u2 + SH * SW;
+    float* V2 = V1 + RPC * SW;
+    for (int idx = tid; idx < SH * SW; idx += T) {
+      const int sr = idx / SW, sc = idx - sr * SW;
+      const int gi = r0 - R + sr, j = sc - R;
+      float h1 = 0.f, h2 = 0.f;
+      if (gi >= 0 && gi < M && j >= 0 && j < N) {
+        const float x = row_at(off_x, gi)[j];
+        const float a1 = row_at(off_w1, gi)[j], a2 = row_at(off_w2, gi)[j];
+        const float h = in_band(x, m) ? band_h(x, m) : 0.f;
+        h1 = h * a1;
+        h2 = h * a2;
+      }
+      u1[idx] = h1;
+      u2[idx] = h2;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < RPC * SW; idx += T) {
+      const int r = idx / SW, c = idx - r * SW;
+      float acc1 = 0.f, acc2 = 0.f;
+      for (int p = 0; p <= 2 * R; ++p) {
+        acc1 = fmaf(m.kw[p], u1[(r + p) * SW + c], acc1);
+        acc2 = fmaf(m.kw[p], u2[(r + p) * SW + c], acc2);
+      }
+      V1[idx] = acc1;
+      V2[idx] = acc2;
+    }
+    __syncthreads();
+    float* v1 = u1;
+    float* v2 = u1 + PL;  // PL <= SH * SW: inside the u1 / u2 area
+    for (int idx = tid; idx < PL; idx += T) {
+      const int r = idx / N, j = idx - r * N;
+      float s1 = 0.f, s2 = 0.f;
+      for (int p = 0; p <= 2 * R; ++p) {
+        s1 = fmaf(m.kw[p], V1[r * SW + j + p], s1);
+        s2 = fmaf(m.kw[p], V2[r * SW + j + p], s2);
+      }
+      v1[idx] = s1;
+      v2[idx] = s2;
+    }
+    __syncthreads();
+  };
+
+  auto any_band = [&](const float* x) {
+    int any = 0;
+    for (int q = tid; q < PL; q += T) any |= in_band(x[q], m);
+    return __syncthreads_or(any) != 0;
+  };
+
+  int wc = 0;    // local parity of the current w
+  int done = 0;
+  for (int k = 0; k < a.max_outer; ++k) {
+    const bool last = k == a.max_outer - 1;
+    const bool check = a.tol > 0.0 ? ((k + 1) % a.check_every == 0 || last)
+                                   : (last && a.check_last != 0);
+    float* psi = sm + ly.psi;
+    if (check)
+      for (int q = tid; q < PL / 4; q += T)
+        reinterpret_cast<float4*>(sm + ly.phik)[q] = reinterpret_cast<const float4*>(psi)[q];
+    const float* W1 = sm + ly.w1[wc];
+    const float* W2 = sm + ly.w2[wc];
+    float* E1 = sm + ly.e1;
+    float* E2 = sm + ly.e2;
+    const float* Gg = sm + ly.g;
+    for (int s = 0; s < mb.inner_S; ++s) {
+      // ---- right-hand side of the inner step, Eq. (37) in increment form
+      {
+        const bool band = any_band(psi);
+        if (band) window(ly.psi, ly.w1[wc], ly.w2[wc]);
+        const float* v1 = sm + ly.scr;
+        const float* v2 = v1 + PL;
+        float* G = sm + ly.G;
+        float* D = sm + ly.D;
+        for (int q = tid; q < PL; q += T) {
+          const int i = q / N, j = q - i * N, gi = r0 + i;
+          const float x = psi[q];
+          const float up = i > 0 ? psi[q - N] : row_at(ly.psi, gi == 0 ? M - 1 : gi - 1)[j];
+          const float dn = i < RPC - 1 ? psi[q + N] : row_at(ly.psi, gi == M - 1 ? 0 : gi + 1)[j];
+          const float lf = psi[i * N + (j == 0 ? N - 1 : j - 1)];
+          const float rt = psi[i * N + (j == N - 1 ? 0 : j + 1)];
+          float dv;
+          if (s == 0) {  // div e, fixed over the inner loop
+            const float e1u = i > 0 ? E1[q - N] : row_at(ly.e1, gi == 0 ? M - 1 : gi - 1)[j];
+            const float e2l = E2[i * N + (j == 0 ? N - 1 : j - 1)];
+            dv = div_e(E1[q], e1u, E2[q], e2l);
+            D[q] = dv;
+          } else {
+            dv = D[q];
+          }
+          const float f = rhs_bulk(m, x, up, dn, lf, rt, dv);
+          G[q] = band ? rhs_band(m, f, x, W1[q], W2[q], Gg[q], v1[q], v2[q]) : m.tau * f;
+        }
+        __syncthreads();
+      }
+      // ---- row R2C: z[n] = G[2n] + i G[2n+1], FFT_L, even/odd split -> X
+      {
+        const int t = tid >> LOGTP, u = tid & (TP - 1);
+        const bool live = t < RPC;
+        float2* base = reinterpret_cast<float2*>(sm + ly.scr) + (size_t)(live ? t : RPC) * RS;
+        const float2* row = reinterpret_cast<const float2*>(sm + ly.G + (live ? t : 0) * N);
+        float2 x[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) x[q] = live ? row[u + (q << LOGTP)] : make_float2(0.f, 0.f);
+        stages<LOGL, 4, 0, false, 1, false, true>(x, base, u, mb.tws16);
+#pragma unroll
+        for (int q = 0; q < E; ++q) base[pad(u + (q << LOGTP))] = x[q];
+        __syncthreads();
+        if (live) {
+          float2* Xrow = reinterpret_cast<float2*>(sm + ly.X) + (size_t)t * L;
+#pragma unroll
+          for (int q = 0; q < E; ++q) {
+            const int kk = u + (q << LOGTP);
+            const float2 Zk = x[q];
+            if (kk == 0) {
+              Xrow[0] = make_float2(Zk.x + Zk.y, Zk.x - Zk.y);
+              continue;
+            }
+            const float2 Zm = base[pad(L - kk)];
+            const float2 Ev = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
+            const float2 Dd = make_float2(0.5f * (Zk.x - Zm.x), 0.5f * (Zk.y + Zm.y));
+            const float2 O = make_float2(Dd.y, -Dd.x);
+            Xrow[kk] = cadd(Ev, cmul(__ldg(&mb.twN[kk]), O));
+          }
+        }
+      }
+      cl.sync();
+      // ---- column solve: forward and backward recursions per column and
+      // real/imaginary part over the CTA's rows, warm-ups from the rows of
+      // the neighbouring CTAs (indices modulo M)
+      {
+        const int Rr = mb.rec_R;
+        float* U = sm + ly.scr;  // [(RPC + Rr)][L][2]
+        float* X2 = sm + ly.X2;
+        for (int task = tid; task < 2 * L; task += T) {
+          const int kk = task >> 1, part = task & 1;
+          const float4 p = __ldg(mb.rec + kk);
+          const float r = part ? p.z : p.x, sc = part ? p.w : p.y;
+          int gi = r0 - Rr;
+          while (gi < 0) gi += M;
+          int q = gi / RPC, li = gi - q * RPC;
+          auto step = [&]() {
+            if (++li == RPC) {
+              li = 0;
+              if (++q == kResC) q = 0;
+            }
+          };
+          float uu = 0.f;
+          for (int j = 0; j < Rr; ++j) {
+            uu = fmaf(r, uu, rbase[q][ly.X + li * N + task]);
+            step();
+          }
+          for (int j = 0; j < RPC + Rr; ++j) {
+            uu = fmaf(r, uu, rbase[q][ly.X + li * N + task]);
+            U[j * 2 * L + task] = uu;
+            step();
+          }
+          float v = 0.f;
+          for (int j = RPC + Rr - 1; j >= RPC; --j) v = fmaf(r, v, U[j * 2 * L + task]);
+          for (int j = RPC - 1; j >= 0; --j) {
+            v = fmaf(r, v, U[j * 2 * L + task]);
+            X2[j * 2 * L + task] = sc * v;
+          }
+        }
+        __syncthreads();
+      }
+      // ---- row C2R of X2, inverse FFT_L, psi += result
+      {
+        const int t = tid >> LOGTP, u = tid & (TP - 1);
+        const bool live = t < RPC;
+        const float2* Xrow = reinterpret_cast<const float2*>(sm + ly.X2) + (size_t)(live ? t : 0) * L;
+        float2 x[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          const int kk = u + (q << LOGTP);
+          const float2 xk = Xrow[kk], xm = Xrow[(L - kk) & (L - 1)];
+          if (kk == 0) {
+            x[q] = make_float2(xk.x + xk.y, xk.x - xk.y);
+            continue;
+          }
+          const float2 Xe = make_float2(xk.x + xm.x, xk.y - xm.y);
+          const float2 Dd = make_float2(xk.x - xm.x, xk.y + xm.y);
+          const float2 Xo = cmul(Dd, cconj(__ldg(&mb.twN[kk])));
+          x[q] = make_float2(Xe.x - Xo.y, Xe.y + Xo.x);
+        }
+        float2* base = reinterpret_cast<float2*>(sm + ly.scr) + (size_t)(live ? t : RPC) * RS;
+        stages<LOGL, 4, 0, true, 1, false, true>(x, base, u, mb.tws16);
+        if (live) {
+          float2* prow = reinterpret_cast<float2*>(psi + t * N);
+#pragma unroll
+          for (int q = 0; q < E; ++q) {
+            const float2 pv = prow[u + (q << LOGTP)];
+            prow[u + (q << LOGTP)] = make_float2(pv.x + x[q].x, pv.y + x[q].y);
+          }
+        }
+      }
+      cl.sync();
+    }
+    // ---- w and b update, Eqs. (41), (42), (40), (23), into the other w parity
+    {
+      const bool band = any_band(psi);
+      if (band) window(ly.psi, ly.w1[wc], ly.w2[wc]);
+      const float* v1 = sm + ly.scr;
+      const float* v2 = v1 + PL;
+      float* W1o = sm + ly.w1[wc ^ 1];
+      float* W2o = sm + ly.w2[wc ^ 1];
+      const float* phik = sm + ly.phik;
+      double n0 = 0.0, n1 = 0.0;
+      for (int q = tid; q < PL; q += T) {
+        const int i = q / N, j = q - i * N, gi = r0 + i;
+        const float x = psi[q];
+        const float dn = i < RPC - 1 ? psi[q + N] : row_at(ly.psi, gi == M - 1 ? 0 : gi + 1)[j];
+        const float rt = psi[i * N + (j == N - 1 ? 0 : j + 1)];
+        const float b1 = E1[q] + W1[q], b2 = E2[q] + W2[q];
+        float wo1, wo2, eo1, eo2;
+        if (band)
+          wb_point<true>(m, x, dn - x, rt - x, b1, b2, Gg[q], v1[q], v2[q], wo1, wo2, eo1, eo2);
+        else
+          wb_point<false>(m, x, dn - x, rt - x, b1, b2, 0.f, 0.f, 0.f, wo1, wo2, eo1, eo2);
+        W1o[q] = wo1;
+        W2o[q] = wo2;
+        E1[q] = eo1;
+        E2[q] = eo2;
+        if (check) {
+          const double df = (double)x - (double)phik[q];
+          n0 += df * df;
+          n1 += (double)phik[q] * (double)phik[q];
+        }
+      }
+      if (check) block_sum2(n0, n1, reinterpret_cast<double*>(sm + ly.part));
+    }
+    cl.sync();
+    wc ^= 1;
+    done = k + 1;
+    if (check) {
+      double num = 0.0, den = 0.0;
+      for (int q = 0; q < kResC; ++q) {
+        const double* p = reinterpret_cast<const double*>(rbase[q] + ly.part);
+        num += p[0];
+        den += p[1];
+      }
+      if (rank == 0 && tid == 0) {
+        mb.red[0] = num;
+        mb.red[1] = den;
+      }
+      const double rel = sqrt(num) / (sqrt(den) + 1e-6);
+      if (a.tol > 0.0 && rel <= a.tol) break;
+    }
+  }
+
+  // ---- store the CTA's rows of the state at parity cur ^ (done & 1)
+  {
+    const int pf = mb.cur ^ (done & 1);
+    const size_t gb = (size_t)r0 * N;
+    float* dst[5] = {mb.phi[pf], mb.w1[pf], mb.w2[pf], mb.e1, mb.e2};
+    const int src[5] = {ly.psi, ly.w1[wc], ly.w2[wc], ly.e1, ly.e2};
+#pragma unroll
+    for (int p = 0; p < 5; ++p) {
+      float4* d4 = reinterpret_cast<float4*>(dst[p] + gb);
+      const float4* s4 = reinterpret_cast<const float4*>(sm + src[p]);
+      for (int q = tid; q < PL / 4; q += T) d4[q] = s4[q];
+    }
+  }
+  if (rank == 0 && tid == 0) *mb.done = done;
+  // no CTA may leave while another can still read its shared memory
+  cl.sync();
+}
+
+template <int LOGL>
+cudaError_t go(const ResArgs& a, int members, size_t smem, cudaStream_t s, bool set_attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kResThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kResC;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (set_attr) {
+    // the largest size any context may use, so that contexts of different
+    // sizes can share the kernel
+    cudaError_t e = cudaFuncSetAttribute(k_resident<LOGL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kResMaxSmem);
+    if (e != cudaSuccess) return e;
+    cfg.gridDim = dim3(kResC);
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, k_resident<LOGL>, &cfg);
+    if (e != cudaSuccess) return e;
+    return clusters > 0 ? cudaSuccess : cudaErrorNotSupported;
+  }
+  cfg.gridDim = dim3(kResC * members);
+  cfg.stream = s;
+  return cudaLaunchKernelEx(&cfg, k_resident<LOGL>, a);
+}
+
+}  // namespace res
+
+size_t resident_smem(const Geo& geo, int R, int rec_R) {
+  const res::Lay l = res::make_lay(geo.M, geo.N, R, rec_R);
+  return (size_t)l.total * sizeof(float);
+}
+
+bool resident_supported(const Geo& geo, int R, int rec_R) {
+  if (geo.neumann || rec_R <= 0 || R < 0 || R > kMaxR) return false;
+  if (geo.N != 32 && geo.N != 64 && geo.N != 128 && geo.N != 256) return false;
+  if (geo.M < 2 * kResC || geo.M % kResC) return false;
+  return resident_smem(geo, R, rec_R) <= kResMaxSmem;
+}
+
+cudaError_t launch_resident(const ResArgs& a, int members, const Geo& geo, size_t smem,
+                            cudaStream_t s, bool set_attr) {
+  switch (geo.L) {
+    case 16: return res::go<4>(a, members, smem, s, set_attr);
+    case 32: return res::go<5>(a, members, smem, s, set_attr);
+    case 64: return res::go<6>(a, members, smem, s, set_attr);
+    case 128: return res::go<7>(a, members, smem, s, set_attr);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace srk

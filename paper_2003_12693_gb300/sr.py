@@ -20,7 +20,8 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "sr.h")
 
 SR_OK, SR_EINVAL, SR_ENOMEM, SR_ECUDA, SR_ENONFINITE = 0, 1, 2, 3, 4
 SR_ENOTCONVERGED, SR_ETIMEOUT, SR_EUNSUPPORTED = 5, 6, 7
-KCLASS = {"rowfft": 0, "colsolve": 1, "rowifft": 2, "wb_update": 3, "reduce": 4, "prep": 5}
+KCLASS = {"rowfft": 0, "colsolve": 1, "rowifft": 2, "wb_update": 3, "reduce": 4, "prep": 5,
+          "resident": 6}
 
 
 class SRError(RuntimeError):
@@ -140,6 +141,8 @@ def lib() -> C.CDLL:
     L.sr_group_destroy.argtypes = [_P]
     L.sr_set_phi_solver.restype = st
     L.sr_set_phi_solver.argtypes = [_P, C.c_int]
+    L.sr_set_resident.restype = st
+    L.sr_set_resident.argtypes = [_P, C.c_int]
     L.sr_set_boundary.restype = st
     L.sr_set_boundary.argtypes = [_P, C.c_int]
     L.sr_aos_solve.restype = st
@@ -294,6 +297,11 @@ class Context:
     def set_boundary(self, boundary: str):
         """'periodic' (the default reading) or 'neumann' (Eq. (27) literally)."""
         _check(lib().sr_set_boundary(self.handle, {"periodic": 0, "neumann": 1}[boundary]), self)
+
+    def set_resident(self, on: bool = True):
+        """sr_set_resident: outer iterations in one launch with the state in one
+        cluster's shared memory (small images)."""
+        _check(lib().sr_set_resident(self.handle, 1 if on else 0), self)
 
     def set_phi_solver(self, solver: str):
         """'fft' (Eqs. (31)-(33), default) or 'aos' (Eqs. (19)-(20) form)."""

@@ -69,8 +69,9 @@ with open(os.path.join(GOLDEN, "early_iterations.json")) as _fh:
     EARLY = json.load(_fh)
 
 
-@pytest.mark.parametrize("name", sorted(EARLY))
-def test_early_iterations_match_oracle(name):
+@pytest.mark.parametrize("name,resident", [(n, False) for n in sorted(EARLY)] +
+                         [("two_disks_128", True)])
+def test_early_iterations_match_oracle(name, resident):
     e = EARLY[name]
     K = int(e["K"])
     if K == 0:
@@ -83,6 +84,8 @@ def test_early_iterations_match_oracle(name):
     phi0 = refs.tie_free_phi0(workload, H, W)
     wl = synth.WORKLOADS[workload]
     ctx = context(H, W, R=wl.R, d=wl.d)
+    if resident:
+        ctx.set_resident(True)
     ctx.edge_function(dev(f))
     ctx.set_phi(dev(phi0))
     ctx.iterate(K)
@@ -90,24 +93,31 @@ def test_early_iterations_match_oracle(name):
     ctx.close()
     ref = oracle_state_after(phi0, oracle.edge(f), K, p).phi
     err = float(np.abs(gpu - ref).max())
-    report("early_iterations", config=name, K=K, max_abs_dphi=err,
+    report("early_iterations", config=name + ("-resident" if resident else ""), K=K,
+           max_abs_dphi=err,
            oracle_P_sensitivity=e["dphi_P"][K - 1])
     assert err <= PHI_TOL, f"{name}: max|dphi| = {err:.3e} after {K} iterations"
 
 
 # ---------------------------------------------------------------- whole runs
-WHOLE = ["two_disks_128", "ellipses_512", "blobs_4096_crop512"]
+# (configuration, resident): 128^2 also runs with the state resident in one
+# cluster's shared memory (sr_set_resident)
+WHOLE = [("two_disks_128", False), ("ellipses_512", False), ("blobs_4096_crop512", False),
+         ("two_disks_128", True)]
 
 
-@pytest.fixture(scope="module", params=WHOLE)
+@pytest.fixture(scope="module", params=WHOLE,
+                ids=[n + ("-resident" if r else "") for n, r in WHOLE])
 def whole(request):
-    name = request.param
+    name, resident = request.param
     meta, masks = _golden(name)
     workload, crop, K = meta["workload"], meta["crop"], int(meta["K"])
     f, phi0, p = refs.inputs(workload, tuple(crop) if crop else None)
     H, W = f.shape
     wl = synth.WORKLOADS[workload]
     ctx = context(H, W, R=wl.R, d=wl.d)
+    if resident:
+        ctx.set_resident(True)
     ctx.edge_function(dev(f))
     ctx.set_phi(dev(phi0))
     ks = meta["trace"]["k"]
@@ -120,7 +130,8 @@ def whole(request):
         islands.append(n_isl)
     state = [host(t) for t in ctx.get_state()]
     ctx.close()
-    return dict(name=name, meta=meta, masks=masks, state=state, energies=energies,
+    return dict(name=name + ("-resident" if resident else ""), workload_name=name, meta=meta,
+                masks=masks, state=state, energies=energies,
                 comps=comps, islands=islands, K=K)
 
 
@@ -163,7 +174,7 @@ def test_whole_run_topology_follows_oracle(whole):
     # oracle's P run itself shows a second, one-pixel component at k = 250 and
     # 350 at 512^2); on the blob crop the contour fragments and the count is
     # rounding-sensitive almost everywhere
-    if whole["name"] != "blobs_4096_crop512":
+    if whole["workload_name"] != "blobs_4096_crop512":
         assert checked >= 0.8 * len(tr["k"])
 
 
@@ -180,7 +191,7 @@ def test_whole_run_energy_falls_and_does_not_rise(whole):
     # on the blob crop the contour fragments (the oracle goes from one to
     # hundreds of components within 100 iterations) and the oracle's own
     # energy rises by 2% between k = 100 and 200: no monotonicity there
-    monotone = whole["name"] != "blobs_4096_crop512"
+    monotone = whole["workload_name"] != "blobs_4096_crop512"
     for e in (tr["energy"], e_gpu) if monotone else ():
         for k0, k1, a, b in zip(tr["k"][:-1], tr["k"][1:], e[:-1], e[1:]):
             if k0 >= 50:
