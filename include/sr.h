@@ -250,8 +250,10 @@ sr_status sr_set_boundary(sr_ctx* ctx, int neumann);
  * about 8), the soft-threshold w update and no inner exit; otherwise
  * SR_EUNSUPPORTED.  While the context's configuration is changed to one of
  * those (sr_set_boundary, sr_set_phi_solver, sr_set_w_sweeps) sr_iterate
- * uses the default path.  Groups keep the default path.  on = 0 restores
- * the default path. */
+ * uses the default path.  In a group (sr_group_create), members with
+ * resident iterations on run together in one launch per row length, one
+ * cluster each, with their own stopping tests in sr_group_run; the other
+ * members run in the group's graphs.  on = 0 restores the default path. */
 sr_status sr_set_resident(sr_ctx* ctx, int on);
 
 /* The AOS solve alone (device buffers, contiguous H x W, not aliased):
@@ -387,7 +389,10 @@ sr_status sr_test_fail_allocations(long long n);
  * iterations as concurrent branches (each a chain of its own kernels), so
  * small images share the GPU instead of running one after another.  Each
  * member's results are bit-identical to sr_iterate(member, max_outer, 0, ...)
- * on that member alone.  There is no stopping test inside the group call
+ * on that member alone.  Members with resident iterations (sr_set_resident)
+ * are not in the graphs: all of them run in one launch per row length
+ * (one cluster of 8 CTAs per member, the same kernel as sr_iterate's, so
+ * also bit for bit), on the group's stream before the graphs.  There is no stopping test inside the group call
  * (tol = 0 semantics); sr_iterate on a member afterwards gives its relative
  * change.  The members must be at the same parity: created or reset with
  * sr_set_phi / sr_set_state together and iterated only through the group, or

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <atomic>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <new>
 #include <string>
@@ -435,7 +436,9 @@ bool make_tensor_map_2d(CUtensorMap* map, const void* base, int rows, int cols, 
 thread_local std::string g_create_err;
 
 std::mutex g_tune_mutex;
-std::map<std::pair<int, int>, std::pair<int, sr_schedule>> g_tuned;  // (H, W) -> (device, schedule)
+// (H, W, warm-up length of the column recursions) -> (device, schedule): the
+// recursion passes' availability and cost depend on tau mu through rec_R
+std::map<std::tuple<int, int, int>, std::pair<int, sr_schedule>> g_tuned;
 
 // Time the candidate row and column schedules on the context's buffers and
 // keep the fastest (once per image size and device in the process).
@@ -454,7 +457,7 @@ sr_status autotune(sr_ctx* c) {
   }
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    auto it = g_tuned.find({c->H, c->W});
+    auto it = g_tuned.find({c->H, c->W, c->rec_R});
     if (it != g_tuned.end() && it->second.first == c->device) {
       c->sched = it->second.second;
       SR_CUDA(c, sched_configure(c, c->sched));
@@ -600,7 +603,7 @@ sr_status autotune(sr_ctx* c) {
   c->sched = best;
   SR_CUDA(c, sched_configure(c, best));
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  g_tuned[{c->H, c->W}] = {c->device, best};
+  g_tuned[{c->H, c->W, c->rec_R}] = {c->device, best};
   return SR_OK;
 }
 
@@ -1785,6 +1788,15 @@ struct sr_group {
   srk::LoopState* loop = nullptr;     // device, one per member
   srk::LoopState* loop_host = nullptr;  // pinned copy
   int lanes = 32;  // concurrent chains of members (sr_group_tune)
+  // members with resident iterations (sr_set_resident): one launch per row
+  // length runs all of them, one cluster each; the graphs hold the others
+  std::vector<int> res;                        // member indices, ordered by row length
+  std::vector<int> res_off, res_cnt;           // per row-length class
+  std::vector<size_t> res_smem;                // largest shared memory of the class
+  std::vector<srk::Geo> res_geo;               // a member's geometry (row length)
+  srk::ResMember* res_dev = nullptr;           // [2][res.size()] descriptors per parity
+  std::vector<char> in_graph;                  // per member: 1 if it runs in the graphs
+  int n_graph = 0;
 };
 
 namespace {
@@ -1795,7 +1807,29 @@ void group_release(sr_group* g) {
   if (g->run_graph) cudaGraphExecDestroy(g->run_graph);
   if (g->loop) cudaFree(g->loop);
   if (g->loop_host) cudaFreeHost(g->loop_host);
+  if (g->res_dev) cudaFree(g->res_dev);
   delete g;
+}
+
+// The resident members' launches, one per row-length class, on the group's
+// stream (ResArgs as in iterate_resident, the members' descriptors at the
+// group's parity).
+cudaError_t group_resident_launch(sr_group* g, int max_outer, double tol, int check_every,
+                                  int check_last) {
+  const int nres = (int)g->res.size();
+  const int p = g->m[0]->cur;
+  for (size_t k = 0; k < g->res_off.size(); ++k) {
+    srk::ResArgs a{};
+    a.members = g->res_dev + (size_t)p * nres + g->res_off[k];
+    a.max_outer = max_outer;
+    a.tol = tol;
+    a.check_every = check_every;
+    a.check_last = check_last;
+    const cudaError_t e = srk::launch_resident(a, g->res_cnt[k], g->res_geo[k], g->res_smem[k],
+                                               g->m[0]->stream, false);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // The graph of sr_group_run: for every member a while-node whose body is
@@ -1818,6 +1852,7 @@ cudaError_t group_build_run(sr_group* g, int step, int parity, std::string& why)
   cudaError_t e = cudaGraphCreate(&top, 0);
   for (int idx = 0; idx < n && e == cudaSuccess; ++idx) {
     const int mi = order[idx];
+    if (!g->in_graph[mi]) continue;
     sr_ctx* c = g->m[mi];
     const int lane = (int)(std::min_element(load.begin(), load.end()) - load.begin());
     load[lane] += (long long)c->H * c->W;
@@ -1880,6 +1915,7 @@ cudaError_t group_build(sr_group* g, int p, std::string& why) {
   cudaGraph_t parent = nullptr;
   cudaError_t e = cudaGraphCreate(&parent, 0);
   for (int idx = 0; idx < n && e == cudaSuccess; ++idx) {
+    if (!g->in_graph[order[idx]]) continue;
     sr_ctx* c = g->m[order[idx]];
     const int lane = (int)(std::min_element(load.begin(), load.end()) - load.begin());
     load[lane] += (long long)c->H * c->W;
@@ -1934,6 +1970,37 @@ sr_status sr_group_create(sr_ctx* const* members, int n, sr_group** out) {
   g->device = c0->device;
   if (const char* env = std::getenv("SR_GROUP_LANES")) g->lanes = std::max(1, std::atoi(env));
   cudaError_t e = cudaSuccess;
+  g->in_graph.assign(n, 1);
+  for (int k = 0; k < n; ++k)
+    if (members[k]->resident && resident_ok(members[k])) g->res.push_back(k);
+  std::stable_sort(g->res.begin(), g->res.end(),
+                   [&](int a, int b) { return members[a]->L < members[b]->L; });
+  for (size_t j = 0; j < g->res.size(); ++j) {
+    sr_ctx* c = members[g->res[j]];
+    g->in_graph[g->res[j]] = 0;
+    if (j == 0 || members[g->res[j - 1]]->L != c->L) {
+      g->res_off.push_back((int)j);
+      g->res_cnt.push_back(0);
+      g->res_smem.push_back(0);
+      g->res_geo.push_back(c->geo);
+    }
+    g->res_cnt.back() += 1;
+    g->res_smem.back() = std::max(g->res_smem.back(), c->res_smem);
+  }
+  g->n_graph = n - (int)g->res.size();
+  if (!g->res.empty()) {
+    const size_t nres = g->res.size();
+    e = dev_alloc((void**)&g->res_dev, 2 * nres * sizeof(srk::ResMember));
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p)
+      for (size_t j = 0; j < nres && e == cudaSuccess; ++j)
+        e = cudaMemcpy(g->res_dev + p * nres + j, members[g->res[j]]->res_dev + p,
+                       sizeof(srk::ResMember), cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+      group_release(g);
+      if (e == cudaErrorMemoryAllocation) return fail(c0, SR_ENOMEM, "sr_group_create: allocation failed");
+      return cuda_fail(c0, e, "sr_group_create");
+    }
+  }
   std::string why;
   for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = group_build(g, p, why);
   if (e != cudaSuccess) {
@@ -1953,14 +2020,21 @@ sr_status sr_group_iterate(sr_group* g, int max_outer) {
     if (c->cur != c0->cur) return fail(c0, SR_EINVAL, "group members are at different parities");
     if (c->profile) return fail(c0, SR_EINVAL, "group members must not be profiling");
   }
-  for (int k = 0; k < max_outer; ++k) {
-    cudaError_t e = cudaGraphLaunch(g->graph[c0->cur], c0->stream);
+  const int p0 = c0->cur;
+  if (!g->res.empty() && max_outer > 0) {
+    const cudaError_t e = group_resident_launch(g, max_outer, 0.0, 1, 0);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "resident launch (group)");
+  }
+  for (int k = 0; k < max_outer && g->n_graph > 0; ++k) {
+    cudaError_t e = cudaGraphLaunch(g->graph[(p0 + k) & 1], c0->stream);
     if (e != cudaSuccess) return cuda_fail(c0, e, "cudaGraphLaunch (group)");
-    for (sr_ctx* c : g->m) {
-      c->launches += c->graph_kernels;
-      c->cur ^= 1;
-      c->iters += 1;
-    }
+  }
+  for (int k = 0; k < (int)g->m.size(); ++k) {
+    sr_ctx* c = g->m[k];
+    c->launches += g->in_graph[k] ? (long long)c->graph_kernels * max_outer : (max_outer > 0);
+    c->cur ^= max_outer & 1;
+    c->iters += max_outer;
+    if (!g->in_graph[k]) c->inner_steps += (long long)max_outer * c->prm.inner_S;
   }
   return SR_OK;
 }
@@ -1997,12 +2071,33 @@ sr_status sr_group_run(sr_group* g, int max_outer, double tol, int check_every, 
     g->run_parity = c0->cur;
   }
   for (int k = 0; k < n; ++k) g->loop_host[k] = srk::LoopState{tol, 0.0, max_outer, 0};
-  SR_CUDA(c0, cudaMemcpyAsync(g->loop, g->loop_host, sizeof(srk::LoopState) * n,
-                              cudaMemcpyHostToDevice, c0->stream));
-  SR_CUDA(c0, cudaGraphLaunch(g->run_graph, c0->stream));
-  SR_CUDA(c0, cudaMemcpyAsync(g->loop_host, g->loop, sizeof(srk::LoopState) * n,
-                              cudaMemcpyDeviceToHost, c0->stream));
+  if (!g->res.empty()) {
+    // bodies of `step` iterations, the test after each: stop after the first
+    // body whose change is <= tol, or when no further body fits
+    SR_CUDA(c0, group_resident_launch(g, max_outer - max_outer % step, tol, step, 1));
+    for (int k : g->res) {
+      sr_ctx* c = g->m[k];
+      SR_CUDA(c0, cudaMemcpyAsync(c->res_done_host, c->res_done, sizeof(int),
+                                  cudaMemcpyDeviceToHost, c0->stream));
+      SR_CUDA(c0, cudaMemcpyAsync(c->red_host, c->red, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                  c0->stream));
+    }
+  }
+  if (g->n_graph > 0) {
+    SR_CUDA(c0, cudaMemcpyAsync(g->loop, g->loop_host, sizeof(srk::LoopState) * n,
+                                cudaMemcpyHostToDevice, c0->stream));
+    SR_CUDA(c0, cudaGraphLaunch(g->run_graph, c0->stream));
+    SR_CUDA(c0, cudaMemcpyAsync(g->loop_host, g->loop, sizeof(srk::LoopState) * n,
+                                cudaMemcpyDeviceToHost, c0->stream));
+  }
   SR_CUDA(c0, cudaStreamSynchronize(c0->stream));
+  for (int k : g->res) {
+    sr_ctx* c = g->m[k];
+    const double num = c->red_host[0], den = c->red_host[1];
+    g->loop_host[k] = srk::LoopState{tol, std::sqrt(num) / (std::sqrt(den) + 1e-6), max_outer,
+                                     *c->res_done_host};
+    c->launches += 1;
+  }
   sr_status st = SR_OK;
   for (int k = 0; k < n; ++k) {
     sr_ctx* c = g->m[k];
@@ -2026,6 +2121,10 @@ sr_status sr_group_tune(sr_group* g, int* lanes_out) {
   if (!g) return SR_EINVAL;
   sr_ctx* c0 = g->m[0];
   const int n = (int)g->m.size();
+  if (g->n_graph == 0) {  // every member runs resident: no graph lanes to choose
+    if (lanes_out) *lanes_out = g->lanes;
+    return SR_OK;
+  }
   for (sr_ctx* c : g->m)
     if (c->cur != c0->cur) return fail(c0, SR_EINVAL, "group members are at different parities");
   // save every member's state (phi, w at the current parity, e) to restore it

@@ -78,11 +78,12 @@ __host__ __device__ inline Lay make_lay(int M, int N, int R, int rec_R) {
   l.X2 = lay_take(o, l.PL);
   // scratch, one use per phase: the window's staged u planes and vertical
   // sums; the row transforms' exchange rows (+1 row for idle thread slots);
-  // the column recursions' forward values of the run and the warm-up after it
+  // the column solve's copy of the rec_R spectrum rows before and after the
+  // CTA's rows, then the forward values of the run and the warm-up after it
   const int L = N / 2, RS = L + L / 16;
   const int win = 2 * (l.RPC + 2 * R) * l.SW + 2 * l.RPC * l.SW;
   const int fft = 2 * (l.RPC + 1) * RS;
-  const int colu = 2 * (l.RPC + rec_R) * L;
+  const int colu = 2 * rec_R * N + 2 * (l.RPC + rec_R) * L;
   int sc = win > fft ? win : fft;
   sc = sc > colu ? sc : colu;
   l.scr = lay_take(o, sc);
@@ -134,10 +135,11 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
   const Lay ly = make_lay(M, N, R, mb.rec_R);
   const int RPC = ly.RPC, PL = ly.PL, r0 = rank * RPC;
 
-  // row gi (0 <= gi < M) of the plane at offset off, in the owner CTA
+  // row gi (0 <= gi < M) of the plane at offset off, in the owner CTA (the
+  // CTA's own rows through its own shared-memory window)
   auto row_at = [&](int off, int gi) -> const float* {
     const int q = gi / RPC;
-    return rbase[q] + off + (gi - q * RPC) * N;
+    return (q == rank ? sm : rbase[q]) + off + (gi - q * RPC) * N;
   };
 
   // ---- load the CTA's rows of the state
@@ -288,37 +290,46 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
       }
       cl.sync();
       // ---- column solve: forward and backward recursions per column and
-      // real/imaginary part over the CTA's rows, warm-ups from the rows of
-      // the neighbouring CTAs (indices modulo M)
+      // real/imaginary part over the CTA's rows.  The warm-ups read the rec_R
+      // spectrum rows before and after the CTA's rows (indices modulo M),
+      // first copied from the other CTAs into scratch by all threads, so that
+      // the recursions' chains read only this CTA's shared memory.
       {
         const int Rr = mb.rec_R;
-        float* U = sm + ly.scr;  // [(RPC + Rr)][L][2]
+        float* Hx = sm + ly.scr;          // [2 Rr][N]: the rows before, then after
+        float* U = Hx + 2 * Rr * N;       // [(RPC + Rr)][2L]
         float* X2 = sm + ly.X2;
+        const float* Xo = sm + ly.X;
+        const int N4 = N / 4;
+        for (int idx = tid; idx < 2 * Rr * N4; idx += T) {
+          const int hr = idx / N4, c4 = idx - hr * N4;
+          int gi = hr < Rr ? r0 - Rr + hr : r0 + RPC + (hr - Rr);
+          gi %= M;
+          if (gi < 0) gi += M;
+          reinterpret_cast<float4*>(Hx + hr * N)[c4] =
+              reinterpret_cast<const float4*>(row_at(ly.X, gi))[c4];
+        }
+        __syncthreads();
         for (int task = tid; task < 2 * L; task += T) {
-          const int kk = task >> 1, part = task & 1;
-          const float4 p = __ldg(mb.rec + kk);
-          const float r = part ? p.z : p.x, sc = part ? p.w : p.y;
-          int gi = r0 - Rr;
-          while (gi < 0) gi += M;
-          int q = gi / RPC, li = gi - q * RPC;
-          auto step = [&]() {
-            if (++li == RPC) {
-              li = 0;
-              if (++q == kResC) q = 0;
-            }
-          };
+          const float4 p = __ldg(mb.rec + (task >> 1));
+          const float r = (task & 1) ? p.z : p.x, sc = (task & 1) ? p.w : p.y;
           float uu = 0.f;
-          for (int j = 0; j < Rr; ++j) {
-            uu = fmaf(r, uu, rbase[q][ly.X + li * N + task]);
-            step();
-          }
-          for (int j = 0; j < RPC + Rr; ++j) {
-            uu = fmaf(r, uu, rbase[q][ly.X + li * N + task]);
+#pragma unroll 4
+          for (int j = 0; j < Rr; ++j) uu = fmaf(r, uu, Hx[j * N + task]);
+#pragma unroll 4
+          for (int j = 0; j < RPC; ++j) {
+            uu = fmaf(r, uu, Xo[j * N + task]);
             U[j * 2 * L + task] = uu;
-            step();
+          }
+#pragma unroll 4
+          for (int j = 0; j < Rr; ++j) {
+            uu = fmaf(r, uu, Hx[(Rr + j) * N + task]);
+            U[(RPC + j) * 2 * L + task] = uu;
           }
           float v = 0.f;
+#pragma unroll 4
           for (int j = RPC + Rr - 1; j >= RPC; --j) v = fmaf(r, v, U[j * 2 * L + task]);
+#pragma unroll 4
           for (int j = RPC - 1; j >= 0; --j) {
             v = fmaf(r, v, U[j * 2 * L + task]);
             X2[j * 2 * L + task] = sc * v;

@@ -26,21 +26,30 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def _members(seed0):
+# members that take resident iterations when the group is built with them
+RESIDENT_OK = {(128, 128), (256, 64), (64, 64)}
+
+
+def _members(seed0, resident=False):
     ctxs = []
     for k, (H, W) in enumerate(SIZES):
         img = synth.ellipse_scene(seed0 + k, H=H, W=W, scale=max(min(H, W) / 512.0, 0.125))
         ctx = context(H, W, R=4, d=4.0)
+        if resident and (H, W) in RESIDENT_OK:
+            ctx.set_resident(True)
         ctx.edge_function(dev(img))
         ctx.set_phi(dev(synth.inset_rect_sdf(H, W)))
         ctxs.append(ctx)
     return ctxs
 
 
-def test_group_run_stops_each_member_at_its_own_tolerance():
+@pytest.mark.parametrize("resident", [False, True])
+def test_group_run_stops_each_member_at_its_own_tolerance(resident):
+    """With resident, three members run in the resident launch (one cluster
+    each, two row lengths) and three in the graph."""
     B, bodies = 4, 6
     # traces: relative change after every body of B iterations, member alone
-    alone = _members(300)
+    alone = _members(300, resident)
     traces = []
     for ctx in alone:
         tr = []
@@ -58,7 +67,7 @@ def test_group_run_stops_each_member_at_its_own_tolerance():
         n = next((b + 1 for b, r in enumerate(tr) if r <= tol), bodies)
         expect.append(n * B)
     assert len(set(expect)) > 1, "the members should stop at different iterations"
-    grouped = _members(300)
+    grouped = _members(300, resident)
     grp = sr.Group(grouped)
     done, rel, converged = grp.run(bodies * B, tol, check_every=B)
     assert done == expect, (done, expect)
@@ -66,13 +75,14 @@ def test_group_run_stops_each_member_at_its_own_tolerance():
         assert r == traces[k][d // B - 1]
     assert converged == all(tr[e // B - 1] <= tol for tr, e in zip(traces, expect))
     # each member equals the member iterated alone for as many iterations
-    ref = _members(300)
+    ref = _members(300, resident)
     for ctx, d in zip(ref, done):
         ctx.iterate(d)
     for a, b in zip(ref, grouped):
         for x, y in zip(a.get_state(), b.get_state()):
             assert np.array_equal(host(x), host(y))
-    report("group_run", members=len(SIZES), tol=tol, outer_done=str(done))
+    report("group_run", members=len(SIZES), resident=int(resident), tol=tol,
+           outer_done=str(done))
     grp.close()
     for ctx in ref + grouped:
         ctx.close()
@@ -91,6 +101,26 @@ def test_group_run_reports_unconverged_and_odd_check_every():
     grp.close()
     for ctx in grouped:
         ctx.close()
+
+
+@pytest.mark.parametrize("n_iter", [5, 6])
+def test_group_iterate_with_resident_members_matches_members_alone(n_iter):
+    """sr_group_iterate with resident members: odd and even counts (the
+    parity of the state), every member bit-identical to running alone."""
+    grouped = _members(600, resident=True)
+    grp = sr.Group(grouped)
+    grp.iterate(n_iter)
+    grp.iterate(3)
+    alone = _members(600, resident=True)
+    for c in alone:
+        c.iterate(n_iter)
+        c.iterate(3)
+    for a, b in zip(alone, grouped):
+        for x, y in zip(a.get_state(), b.get_state()):
+            assert np.array_equal(host(x), host(y))
+    grp.close()
+    for c in alone + grouped:
+        c.close()
 
 
 def test_group_tune_picks_a_lane_count_and_leaves_the_states():
