@@ -91,7 +91,7 @@ def _peaks():
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
     for name in ("sr_kernels.cu", "sr_fft.cu", "sr_colrec.cu", "sr_tma.cuh", "sr_internal.h",
-                 "sr_dft.cuh", "sr_small.cu", "sr_point.cuh", "sr_resident.cu"):
+                 "sr_dft.cuh", "sr_point.cuh"):
         with open(os.path.join(ROOT, "paper_2003_12693_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -530,7 +530,7 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
                             f"({event_overhead_us:.2f} us, the same pair around an empty kernel), "
                             "scaled so that the classes add up to the graph step")
     if names[dom] == "k_resident":
-        roofline["note"] = ("whole outer iterations in one cluster of 8 CTAs with the state in "
+        roofline["note"] = ("whole outer iterations in one cluster of 8 or 16 CTAs with the state in "
                             "shared memory: bound by the cluster barriers and on-chip latency of "
                             "each phase, not by DRAM (it reads and writes the state once per call)")
     elif names[dom] == "k_solve_small":

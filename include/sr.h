@@ -232,8 +232,11 @@ sr_status sr_set_boundary(sr_ctx* ctx, int neumann);
 /* Resident outer iterations for small images.  on = 1: sr_iterate runs its
  * outer iterations of Alg. 1 in ONE launch per call, with the whole state
  * (phi, w at both parities, e, g, div e, the right-hand side and the half
- * spectrum) held in the shared memory of one cluster of 8 CTAs -- CTA q owns
- * rows [q H/8, (q+1) H/8) -- for all the iterations of the call; neighbour
+ * spectrum) held in the shared memory of one cluster of C CTAs -- CTA q owns
+ * rows [q H/C, (q+1) H/C); C = 16 where H/16 >= 2 rows and the device
+ * schedules clusters of 16, else 8 (the environment variable
+ * SR_RESIDENT_CLUSTER = 8 or 16 fixes it) -- for all the iterations of the
+ * call; neighbour
  * rows, window halos and the column recursions' warm-ups are read from the
  * other CTAs' shared memory (distributed shared memory), and the phases of an
  * iteration are separated by cluster barriers instead of kernel boundaries.
@@ -251,8 +254,8 @@ sr_status sr_set_boundary(sr_ctx* ctx, int neumann);
  * SR_EUNSUPPORTED.  While the context's configuration is changed to one of
  * those (sr_set_boundary, sr_set_phi_solver, sr_set_w_sweeps) sr_iterate
  * uses the default path.  In a group (sr_group_create), members with
- * resident iterations on run together in one launch per row length, one
- * cluster each, with their own stopping tests in sr_group_run; the other
+ * resident iterations on run together in one launch per row length and
+ * cluster size, one cluster each, with their own stopping tests in sr_group_run; the other
  * members run in the group's graphs.  on = 0 restores the default path. */
 sr_status sr_set_resident(sr_ctx* ctx, int on);
 
@@ -390,8 +393,8 @@ sr_status sr_test_fail_allocations(long long n);
  * small images share the GPU instead of running one after another.  Each
  * member's results are bit-identical to sr_iterate(member, max_outer, 0, ...)
  * on that member alone.  Members with resident iterations (sr_set_resident)
- * are not in the graphs: all of them run in one launch per row length
- * (one cluster of 8 CTAs per member, the same kernel as sr_iterate's, so
+ * are not in the graphs: all of them run in one launch per row length and
+ * cluster size (one cluster per member, the same kernel as sr_iterate's, so
  * also bit for bit), on the group's stream before the graphs.  There is no stopping test inside the group call
  * (tol = 0 semantics); sr_iterate on a member afterwards gives its relative
  * change.  The members must be at the same parity: created or reset with

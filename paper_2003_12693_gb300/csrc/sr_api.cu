@@ -112,6 +112,7 @@ struct sr_ctx {
   // outer iterations resident in shared memory (sr_set_resident)
   int resident = 0;
   size_t res_smem = 0;
+  int res_C = 0;                      // CTAs per cluster (8 or 16)
   srk::ResMember* res_dev = nullptr;  // the image's description at parity 0 and 1
   int* res_done = nullptr;            // iterations the last launch ran
   int* res_done_host = nullptr;       // pinned copy
@@ -950,9 +951,11 @@ sr_status read_residual(sr_ctx* c, double* rel) {
 }
 
 // the configuration the resident kernel implements
+bool resident_base_ok(const sr_ctx* c) {
+  return c->fft2 && c->phi_solver == 0 && c->w_sweeps == 0 && c->prm.inner_tol <= 0.f;
+}
 bool resident_ok(const sr_ctx* c) {
-  return c->fft2 && c->phi_solver == 0 && c->w_sweeps == 0 && c->prm.inner_tol <= 0.f &&
-         srk::resident_supported(c->geo, c->mod.R, c->rec_R);
+  return resident_base_ok(c) && srk::resident_supported(c->geo, c->mod.R, c->rec_R, c->res_C);
 }
 
 // sr_iterate with the state resident in shared memory: one launch runs up to
@@ -966,7 +969,7 @@ sr_status iterate_resident(sr_ctx* c, int max_outer, double tol, int* outer_done
   a.check_every = c->prm.check_every;
   a.check_last = rel_change != nullptr;
   sr_status st = run_kernel(c, SR_KCLASS_RESIDENT, c->stream, "k_resident", [&] {
-    return srk::launch_resident(a, 1, c->geo, c->res_smem, c->stream, false);
+    return srk::launch_resident(a, 1, c->geo, c->res_C, c->res_smem, c->stream, false);
   });
   if (st != SR_OK) return st;
   int done = max_outer;
@@ -1571,17 +1574,32 @@ sr_status sr_set_resident(sr_ctx* c, int on) {
     c->resident = 0;
     return SR_OK;
   }
-  if (!resident_ok(c))
-    return fail(c, SR_EUNSUPPORTED,
-                "resident iterations need W in {32, 64, 128, 256}, H a multiple of 8 (>= 16), "
-                "the state within one cluster's shared memory, the periodic FFT solve with the "
-                "column recursions and Eqs. (41)-(42)");
-  const size_t smem = srk::resident_smem(c->geo, c->mod.R, c->rec_R);
-  srk::ResArgs probe{};
-  const cudaError_t pe = srk::launch_resident(probe, 1, c->geo, smem, nullptr, true);
-  if (pe == cudaErrorNotSupported)
-    return fail(c, SR_EUNSUPPORTED, "a cluster of 8 CTAs with this shared memory does not fit");
-  SR_CUDA(c, pe);
+  const char* why =
+      "resident iterations need W in {32, 64, 128, 256}, H a multiple of 8 (>= 16), the state "
+      "within one cluster's shared memory, the periodic FFT solve with the column recursions "
+      "and Eqs. (41)-(42)";
+  if (!resident_base_ok(c)) return fail(c, SR_EUNSUPPORTED, why);
+  // clusters of 16 CTAs where the rows divide and the device schedules them,
+  // else 8; SR_RESIDENT_CLUSTER=8 or 16 fixes the choice
+  std::vector<int> cands = {16, 8};
+  if (const char* env = std::getenv("SR_RESIDENT_CLUSTER")) {
+    const int v = std::atoi(env);
+    if (v == 8 || v == 16) cands = {v};
+  }
+  int C = 0;
+  size_t smem = 0;
+  for (int cand : cands) {
+    if (!srk::resident_supported(c->geo, c->mod.R, c->rec_R, cand)) continue;
+    const size_t sm_c = srk::resident_smem(c->geo, c->mod.R, c->rec_R, cand);
+    srk::ResArgs probe{};
+    const cudaError_t pe = srk::launch_resident(probe, 1, c->geo, cand, sm_c, nullptr, true);
+    if (pe == cudaErrorNotSupported) continue;
+    SR_CUDA(c, pe);
+    C = cand;
+    smem = sm_c;
+    break;
+  }
+  if (!C) return fail(c, SR_EUNSUPPORTED, why);
   if (!c->res_dev) {
     cudaError_t e = dev_alloc((void**)&c->res_dev, 2 * sizeof(srk::ResMember));
     if (e == cudaSuccess) e = dev_alloc((void**)&c->res_done, sizeof(int));
@@ -1614,6 +1632,7 @@ sr_status sr_set_resident(sr_ctx* c, int on) {
   }
   SR_CUDA(c, cudaMemcpy(c->res_dev, mb, sizeof(mb), cudaMemcpyHostToDevice));
   c->res_smem = smem;
+  c->res_C = C;
   c->resident = 1;
   return SR_OK;
 }
@@ -1794,6 +1813,7 @@ struct sr_group {
   std::vector<int> res_off, res_cnt;           // per row-length class
   std::vector<size_t> res_smem;                // largest shared memory of the class
   std::vector<srk::Geo> res_geo;               // a member's geometry (row length)
+  std::vector<int> res_C;                      // the class's cluster size
   srk::ResMember* res_dev = nullptr;           // [2][res.size()] descriptors per parity
   std::vector<char> in_graph;                  // per member: 1 if it runs in the graphs
   int n_graph = 0;
@@ -1825,7 +1845,8 @@ cudaError_t group_resident_launch(sr_group* g, int max_outer, double tol, int ch
     a.tol = tol;
     a.check_every = check_every;
     a.check_last = check_last;
-    const cudaError_t e = srk::launch_resident(a, g->res_cnt[k], g->res_geo[k], g->res_smem[k],
+    const cudaError_t e = srk::launch_resident(a, g->res_cnt[k], g->res_geo[k], g->res_C[k],
+                                               g->res_smem[k],
                                                g->m[0]->stream, false);
     if (e != cudaSuccess) return e;
   }
@@ -1973,16 +1994,20 @@ sr_status sr_group_create(sr_ctx* const* members, int n, sr_group** out) {
   g->in_graph.assign(n, 1);
   for (int k = 0; k < n; ++k)
     if (members[k]->resident && resident_ok(members[k])) g->res.push_back(k);
-  std::stable_sort(g->res.begin(), g->res.end(),
-                   [&](int a, int b) { return members[a]->L < members[b]->L; });
+  // classes of one row length and cluster size: one launch each
+  std::stable_sort(g->res.begin(), g->res.end(), [&](int a, int b) {
+    return std::make_pair(members[a]->L, members[a]->res_C) <
+           std::make_pair(members[b]->L, members[b]->res_C);
+  });
   for (size_t j = 0; j < g->res.size(); ++j) {
     sr_ctx* c = members[g->res[j]];
     g->in_graph[g->res[j]] = 0;
-    if (j == 0 || members[g->res[j - 1]]->L != c->L) {
+    if (j == 0 || members[g->res[j - 1]]->L != c->L || members[g->res[j - 1]]->res_C != c->res_C) {
       g->res_off.push_back((int)j);
       g->res_cnt.push_back(0);
       g->res_smem.push_back(0);
       g->res_geo.push_back(c->geo);
+      g->res_C.push_back(c->res_C);
     }
     g->res_cnt.back() += 1;
     g->res_smem.back() = std::max(g->res_smem.back(), c->res_smem);

@@ -178,5 +178,18 @@ __device__ __forceinline__ void stages(float2 (&x)[1 << LOGE], float2* base, int
   }
 }
 
+// The barriers of stages<LOGL, LOGE, 0, INV, STRIDE, DB, TWG> without the
+// arithmetic, for whole warps that hold no sequence: every __syncthreads of
+// the warps that do is met once.
+template <int LOGL, int LOGE, bool DB = false>
+__device__ __forceinline__ void stage_barriers() {
+  constexpr int NST = TwPlan<LOGL, LOGE>::NST;
+#pragma unroll
+  for (int s = 0; s + 1 < NST; ++s) {
+    __syncthreads();
+    if (!DB) __syncthreads();
+  }
+}
+
 }  // namespace cdft
 }  // namespace srk

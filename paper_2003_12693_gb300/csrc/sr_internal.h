@@ -321,10 +321,11 @@ size_t solve_small_smem(const Geo& geo);
 cudaError_t launch_solve_small(const SmallArgs& a, cudaStream_t s, bool set_attr);
 
 // Outer iterations with the state resident in shared memory (sr_resident.cu):
-// one cluster of kResC CTAs per image, CTA q owning rows [q M/kResC,
-// (q+1) M/kResC); N in {32, 64, 128, 256}, M a multiple of kResC (>= 2 kResC),
-// the recursion column solve (rec_R > 0), periodic boundary.
-constexpr int kResC = 8;
+// one cluster of C CTAs per image (C = 8, or 16 with the non-portable cluster
+// size), CTA q owning rows [q M/C, (q+1) M/C); N in {32, 64, 128, 256}, M a
+// multiple of C (>= 2 C), the recursion column solve (rec_R > 0), periodic
+// boundary.
+constexpr int kResCMax = 16;
 constexpr int kResThreads = 512;
 constexpr size_t kResMaxSmem = 220 * 1024;
 struct ResMember {
@@ -352,11 +353,11 @@ struct ResArgs {
   int check_every;           // checks after every check_every-th and the last iteration
   int check_last;            // tol <= 0: evaluate the test after the last iteration
 };
-size_t resident_smem(const Geo& geo, int R, int rec_R);
-bool resident_supported(const Geo& geo, int R, int rec_R);
-// set_attr: raise the shared-memory limit and check that a cluster fits
-// (cudaErrorNotSupported if not); otherwise launch `members` clusters.
-cudaError_t launch_resident(const ResArgs& a, int members, const Geo& geo, size_t smem,
+size_t resident_smem(const Geo& geo, int R, int rec_R, int C);
+bool resident_supported(const Geo& geo, int R, int rec_R, int C);
+// set_attr: raise the shared-memory limit and check that a cluster of C fits
+// (cudaErrorNotSupported if not); otherwise launch `members` clusters of C.
+cudaError_t launch_resident(const ResArgs& a, int members, const Geo& geo, int C, size_t smem,
                             cudaStream_t s, bool set_attr);
 // Neumann solve helpers: the even extension of each row (out is M x 2N) and
 // out = psi + T[:, :N] (T is M x 2N; psi may be null)

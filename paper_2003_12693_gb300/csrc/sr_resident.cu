@@ -1,8 +1,8 @@
 // Whole outer iterations of Alg. 1 for small images in one launch, with the
 // state resident on chip.
 //
-// An image of M x N pixels is owned by one cluster of kResC CTAs; CTA q holds
-// rows [q M/kResC, (q+1) M/kResC) of every plane (phi, w at two parities, e,
+// An image of M x N pixels is owned by one cluster of C CTAs (8 or 16); CTA q
+// holds rows [q M/C, (q+1) M/C) of every plane (phi, w at two parities, e,
 // g, div e, the right-hand side, the half spectrum and the column solve's
 // output) in its shared memory for all the iterations of the launch.  The
 // phases of one outer iteration are those of the tiled kernels, and they use
@@ -18,7 +18,7 @@
 //     cluster barrier
 //   w/b update of Eqs. (41), (42), (40), (23) into the other w parity, e in
 //   place; on check iterations the FP64 sums of the stopping test
-//   cluster barrier; the stopping decision from the kResC partial sums, taken
+//   cluster barrier; the stopping decision from the C partial sums, taken
 //   identically by every CTA.
 // Neighbour rows of the stencils and the window halos come from the other
 // CTAs' shared memory through the cluster's distributed shared memory.  Global
@@ -57,9 +57,9 @@ __host__ __device__ inline int lay_take(int& o, int n) {
   return r;
 }
 
-__host__ __device__ inline Lay make_lay(int M, int N, int R, int rec_R) {
+__host__ __device__ inline Lay make_lay(int M, int N, int R, int rec_R, int C) {
   Lay l;
-  l.RPC = M / kResC;
+  l.RPC = M / C;
   l.PL = l.RPC * N;
   l.SW = N + 2 * R;
   int o = 0;
@@ -116,23 +116,26 @@ __device__ __forceinline__ void block_sum2(double a, double b, double* out) {
   }
 }
 
+// Work is spread by rows over warps and by columns over lanes, so that no
+// index needs a division by a runtime width.
 template <int LOGL>
 __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
-  constexpr int L = 1 << LOGL, E = 16, LOGTP = LOGL - 4, TP = 1 << LOGTP;
+  constexpr int L = 1 << LOGL, N = 2 * L, E = 16, LOGTP = LOGL - 4, TP = 1 << LOGTP;
   constexpr int RS = L + L / 16;
-  constexpr int T = kResThreads;
+  constexpr int T = kResThreads, NW = T / 32;
   extern __shared__ __align__(16) float sm[];
   __shared__ ResMember mb;
-  __shared__ float* rbase[kResC];
+  __shared__ float* rbase[kResCMax];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const int tid = threadIdx.x;
-  if (tid == 0) mb = a.members[blockIdx.x / kResC];
-  if (tid < kResC) rbase[tid] = cl.map_shared_rank(sm, tid);
+  const int C = (int)cl.num_blocks();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) mb = a.members[blockIdx.x / C];
+  if (tid < C) rbase[tid] = cl.map_shared_rank(sm, tid);
   __syncthreads();
   const Model& m = mb.mod;
-  const int M = mb.geo.M, N = mb.geo.N, R = m.R;
-  const Lay ly = make_lay(M, N, R, mb.rec_R);
+  const int M = mb.geo.M, R = m.R;
+  const Lay ly = make_lay(M, N, R, mb.rec_R, C);
   const int RPC = ly.RPC, PL = ly.PL, r0 = rank * RPC;
 
   // row gi (0 <= gi < M) of the plane at offset off, in the owner CTA (the
@@ -165,44 +168,49 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
     float* u2 = u1 + SH * SW;
     float* V1 = u2 + SH * SW;
     float* V2 = V1 + RPC * SW;
-    for (int idx = tid; idx < SH * SW; idx += T) {
-      const int sr = idx / SW, sc = idx - sr * SW;
-      const int gi = r0 - R + sr, j = sc - R;
-      float h1 = 0.f, h2 = 0.f;
-      if (gi >= 0 && gi < M && j >= 0 && j < N) {
-        const float x = row_at(off_x, gi)[j];
-        const float a1 = row_at(off_w1, gi)[j], a2 = row_at(off_w2, gi)[j];
-        const float h = in_band(x, m) ? band_h(x, m) : 0.f;
-        h1 = h * a1;
-        h2 = h * a2;
+    for (int sr = warp; sr < SH; sr += NW) {
+      const int gi = r0 - R + sr;
+      const bool in = gi >= 0 && gi < M;
+      const float* px = in ? row_at(off_x, gi) : nullptr;
+      const float* p1 = in ? row_at(off_w1, gi) : nullptr;
+      const float* p2 = in ? row_at(off_w2, gi) : nullptr;
+      for (int sc = lane; sc < SW; sc += 32) {
+        const int j = sc - R;
+        float h1 = 0.f, h2 = 0.f;
+        if (in && j >= 0 && j < N) {
+          const float x = px[j];
+          const float h = in_band(x, m) ? band_h(x, m) : 0.f;
+          h1 = h * p1[j];
+          h2 = h * p2[j];
+        }
+        u1[sr * SW + sc] = h1;
+        u2[sr * SW + sc] = h2;
       }
-      u1[idx] = h1;
-      u2[idx] = h2;
     }
     __syncthreads();
-    for (int idx = tid; idx < RPC * SW; idx += T) {
-      const int r = idx / SW, c = idx - r * SW;
-      float acc1 = 0.f, acc2 = 0.f;
-      for (int p = 0; p <= 2 * R; ++p) {
-        acc1 = fmaf(m.kw[p], u1[(r + p) * SW + c], acc1);
-        acc2 = fmaf(m.kw[p], u2[(r + p) * SW + c], acc2);
+    for (int r = warp; r < RPC; r += NW)
+      for (int c = lane; c < SW; c += 32) {
+        float acc1 = 0.f, acc2 = 0.f;
+        for (int p = 0; p <= 2 * R; ++p) {
+          acc1 = fmaf(m.kw[p], u1[(r + p) * SW + c], acc1);
+          acc2 = fmaf(m.kw[p], u2[(r + p) * SW + c], acc2);
+        }
+        V1[r * SW + c] = acc1;
+        V2[r * SW + c] = acc2;
       }
-      V1[idx] = acc1;
-      V2[idx] = acc2;
-    }
     __syncthreads();
     float* v1 = u1;
     float* v2 = u1 + PL;  // PL <= SH * SW: inside the u1 / u2 area
-    for (int idx = tid; idx < PL; idx += T) {
-      const int r = idx / N, j = idx - r * N;
-      float s1 = 0.f, s2 = 0.f;
-      for (int p = 0; p <= 2 * R; ++p) {
-        s1 = fmaf(m.kw[p], V1[r * SW + j + p], s1);
-        s2 = fmaf(m.kw[p], V2[r * SW + j + p], s2);
+    for (int r = warp; r < RPC; r += NW)
+      for (int j = lane; j < N; j += 32) {
+        float s1 = 0.f, s2 = 0.f;
+        for (int p = 0; p <= 2 * R; ++p) {
+          s1 = fmaf(m.kw[p], V1[r * SW + j + p], s1);
+          s2 = fmaf(m.kw[p], V2[r * SW + j + p], s2);
+        }
+        v1[r * N + j] = s1;
+        v2[r * N + j] = s2;
       }
-      v1[idx] = s1;
-      v2[idx] = s2;
-    }
     __syncthreads();
   };
 
@@ -211,6 +219,13 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
     for (int q = tid; q < PL; q += T) any |= in_band(x[q], m);
     return __syncthreads_or(any) != 0;
   };
+
+  // the row transforms: thread slot t = tid / TP takes row t; whole warps
+  // without a row only meet the stages' barriers
+  const int ft = tid >> LOGTP, fu = tid & (TP - 1);
+  const bool flive = ft < RPC;
+  const bool fwarp = (tid & ~31) < RPC * TP;
+  float2* fbase = reinterpret_cast<float2*>(sm + ly.scr) + (size_t)(flive ? ft : RPC) * RS;
 
   int wc = 0;    // local parity of the current w
   int done = 0;
@@ -236,51 +251,56 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
         const float* v2 = v1 + PL;
         float* G = sm + ly.G;
         float* D = sm + ly.D;
-        for (int q = tid; q < PL; q += T) {
-          const int i = q / N, j = q - i * N, gi = r0 + i;
-          const float x = psi[q];
-          const float up = i > 0 ? psi[q - N] : row_at(ly.psi, gi == 0 ? M - 1 : gi - 1)[j];
-          const float dn = i < RPC - 1 ? psi[q + N] : row_at(ly.psi, gi == M - 1 ? 0 : gi + 1)[j];
-          const float lf = psi[i * N + (j == 0 ? N - 1 : j - 1)];
-          const float rt = psi[i * N + (j == N - 1 ? 0 : j + 1)];
-          float dv;
-          if (s == 0) {  // div e, fixed over the inner loop
-            const float e1u = i > 0 ? E1[q - N] : row_at(ly.e1, gi == 0 ? M - 1 : gi - 1)[j];
-            const float e2l = E2[i * N + (j == 0 ? N - 1 : j - 1)];
-            dv = div_e(E1[q], e1u, E2[q], e2l);
-            D[q] = dv;
-          } else {
-            dv = D[q];
+        for (int i = warp; i < RPC; i += NW) {
+          const int gi = r0 + i;
+          const float* up_row = i > 0 ? psi + (i - 1) * N : row_at(ly.psi, gi == 0 ? M - 1 : gi - 1);
+          const float* dn_row = i < RPC - 1 ? psi + (i + 1) * N
+                                            : row_at(ly.psi, gi == M - 1 ? 0 : gi + 1);
+          const float* e1u_row = i > 0 ? E1 + (i - 1) * N : row_at(ly.e1, gi == 0 ? M - 1 : gi - 1);
+          for (int j = lane; j < N; j += 32) {
+            const int q = i * N + j;
+            const float x = psi[q];
+            const float lf = psi[i * N + ((j - 1) & (N - 1))];
+            const float rt = psi[i * N + ((j + 1) & (N - 1))];
+            float dv;
+            if (s == 0) {  // div e, fixed over the inner loop
+              const float e2l = E2[i * N + ((j - 1) & (N - 1))];
+              dv = div_e(E1[q], e1u_row[j], E2[q], e2l);
+              D[q] = dv;
+            } else {
+              dv = D[q];
+            }
+            const float f = rhs_bulk(m, x, up_row[j], dn_row[j], lf, rt, dv);
+            G[q] = band ? rhs_band(m, f, x, W1[q], W2[q], Gg[q], v1[q], v2[q]) : m.tau * f;
           }
-          const float f = rhs_bulk(m, x, up, dn, lf, rt, dv);
-          G[q] = band ? rhs_band(m, f, x, W1[q], W2[q], Gg[q], v1[q], v2[q]) : m.tau * f;
         }
         __syncthreads();
       }
       // ---- row R2C: z[n] = G[2n] + i G[2n+1], FFT_L, even/odd split -> X
       {
-        const int t = tid >> LOGTP, u = tid & (TP - 1);
-        const bool live = t < RPC;
-        float2* base = reinterpret_cast<float2*>(sm + ly.scr) + (size_t)(live ? t : RPC) * RS;
-        const float2* row = reinterpret_cast<const float2*>(sm + ly.G + (live ? t : 0) * N);
         float2 x[E];
+        if (fwarp) {
+          const float2* row = reinterpret_cast<const float2*>(sm + ly.G + (flive ? ft : 0) * N);
 #pragma unroll
-        for (int q = 0; q < E; ++q) x[q] = live ? row[u + (q << LOGTP)] : make_float2(0.f, 0.f);
-        stages<LOGL, 4, 0, false, 1, false, true>(x, base, u, mb.tws16);
+          for (int q = 0; q < E; ++q) x[q] = flive ? row[fu + (q << LOGTP)] : make_float2(0.f, 0.f);
+          stages<LOGL, 4, 0, false, 1, false, true>(x, fbase, fu, mb.tws16);
 #pragma unroll
-        for (int q = 0; q < E; ++q) base[pad(u + (q << LOGTP))] = x[q];
+          for (int q = 0; q < E; ++q) fbase[pad(fu + (q << LOGTP))] = x[q];
+        } else {
+          stage_barriers<LOGL, 4>();
+        }
         __syncthreads();
-        if (live) {
-          float2* Xrow = reinterpret_cast<float2*>(sm + ly.X) + (size_t)t * L;
+        if (flive) {
+          float2* Xrow = reinterpret_cast<float2*>(sm + ly.X) + (size_t)ft * L;
 #pragma unroll
           for (int q = 0; q < E; ++q) {
-            const int kk = u + (q << LOGTP);
+            const int kk = fu + (q << LOGTP);
             const float2 Zk = x[q];
             if (kk == 0) {
               Xrow[0] = make_float2(Zk.x + Zk.y, Zk.x - Zk.y);
               continue;
             }
-            const float2 Zm = base[pad(L - kk)];
+            const float2 Zm = fbase[pad(L - kk)];
             const float2 Ev = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
             const float2 Dd = make_float2(0.5f * (Zk.x - Zm.x), 0.5f * (Zk.y + Zm.y));
             const float2 O = make_float2(Dd.y, -Dd.x);
@@ -300,14 +320,13 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
         float* U = Hx + 2 * Rr * N;       // [(RPC + Rr)][2L]
         float* X2 = sm + ly.X2;
         const float* Xo = sm + ly.X;
-        const int N4 = N / 4;
-        for (int idx = tid; idx < 2 * Rr * N4; idx += T) {
-          const int hr = idx / N4, c4 = idx - hr * N4;
+        for (int hr = warp; hr < 2 * Rr; hr += NW) {
           int gi = hr < Rr ? r0 - Rr + hr : r0 + RPC + (hr - Rr);
           gi %= M;
           if (gi < 0) gi += M;
-          reinterpret_cast<float4*>(Hx + hr * N)[c4] =
-              reinterpret_cast<const float4*>(row_at(ly.X, gi))[c4];
+          const float4* srow = reinterpret_cast<const float4*>(row_at(ly.X, gi));
+          for (int c4 = lane; c4 < N / 4; c4 += 32)
+            reinterpret_cast<float4*>(Hx + hr * N)[c4] = srow[c4];
         }
         __syncthreads();
         for (int task = tid; task < 2 * L; task += T) {
@@ -338,14 +357,12 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
         __syncthreads();
       }
       // ---- row C2R of X2, inverse FFT_L, psi += result
-      {
-        const int t = tid >> LOGTP, u = tid & (TP - 1);
-        const bool live = t < RPC;
-        const float2* Xrow = reinterpret_cast<const float2*>(sm + ly.X2) + (size_t)(live ? t : 0) * L;
+      if (fwarp) {
+        const float2* Xrow = reinterpret_cast<const float2*>(sm + ly.X2) + (size_t)(flive ? ft : 0) * L;
         float2 x[E];
 #pragma unroll
         for (int q = 0; q < E; ++q) {
-          const int kk = u + (q << LOGTP);
+          const int kk = fu + (q << LOGTP);
           const float2 xk = Xrow[kk], xm = Xrow[(L - kk) & (L - 1)];
           if (kk == 0) {
             x[q] = make_float2(xk.x + xk.y, xk.x - xk.y);
@@ -356,16 +373,17 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
           const float2 Xo = cmul(Dd, cconj(__ldg(&mb.twN[kk])));
           x[q] = make_float2(Xe.x - Xo.y, Xe.y + Xo.x);
         }
-        float2* base = reinterpret_cast<float2*>(sm + ly.scr) + (size_t)(live ? t : RPC) * RS;
-        stages<LOGL, 4, 0, true, 1, false, true>(x, base, u, mb.tws16);
-        if (live) {
-          float2* prow = reinterpret_cast<float2*>(psi + t * N);
+        stages<LOGL, 4, 0, true, 1, false, true>(x, fbase, fu, mb.tws16);
+        if (flive) {
+          float2* prow = reinterpret_cast<float2*>(psi + ft * N);
 #pragma unroll
           for (int q = 0; q < E; ++q) {
-            const float2 pv = prow[u + (q << LOGTP)];
-            prow[u + (q << LOGTP)] = make_float2(pv.x + x[q].x, pv.y + x[q].y);
+            const float2 pv = prow[fu + (q << LOGTP)];
+            prow[fu + (q << LOGTP)] = make_float2(pv.x + x[q].x, pv.y + x[q].y);
           }
         }
+      } else {
+        stage_barriers<LOGL, 4>();
       }
       cl.sync();
     }
@@ -379,25 +397,30 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
       float* W2o = sm + ly.w2[wc ^ 1];
       const float* phik = sm + ly.phik;
       double n0 = 0.0, n1 = 0.0;
-      for (int q = tid; q < PL; q += T) {
-        const int i = q / N, j = q - i * N, gi = r0 + i;
-        const float x = psi[q];
-        const float dn = i < RPC - 1 ? psi[q + N] : row_at(ly.psi, gi == M - 1 ? 0 : gi + 1)[j];
-        const float rt = psi[i * N + (j == N - 1 ? 0 : j + 1)];
-        const float b1 = E1[q] + W1[q], b2 = E2[q] + W2[q];
-        float wo1, wo2, eo1, eo2;
-        if (band)
-          wb_point<true>(m, x, dn - x, rt - x, b1, b2, Gg[q], v1[q], v2[q], wo1, wo2, eo1, eo2);
-        else
-          wb_point<false>(m, x, dn - x, rt - x, b1, b2, 0.f, 0.f, 0.f, wo1, wo2, eo1, eo2);
-        W1o[q] = wo1;
-        W2o[q] = wo2;
-        E1[q] = eo1;
-        E2[q] = eo2;
-        if (check) {
-          const double df = (double)x - (double)phik[q];
-          n0 += df * df;
-          n1 += (double)phik[q] * (double)phik[q];
+      for (int i = warp; i < RPC; i += NW) {
+        const int gi = r0 + i;
+        const float* dn_row = i < RPC - 1 ? psi + (i + 1) * N
+                                          : row_at(ly.psi, gi == M - 1 ? 0 : gi + 1);
+        for (int j = lane; j < N; j += 32) {
+          const int q = i * N + j;
+          const float x = psi[q];
+          const float dn = dn_row[j];
+          const float rt = psi[i * N + ((j + 1) & (N - 1))];
+          const float b1 = E1[q] + W1[q], b2 = E2[q] + W2[q];
+          float wo1, wo2, eo1, eo2;
+          if (band)
+            wb_point<true>(m, x, dn - x, rt - x, b1, b2, Gg[q], v1[q], v2[q], wo1, wo2, eo1, eo2);
+          else
+            wb_point<false>(m, x, dn - x, rt - x, b1, b2, 0.f, 0.f, 0.f, wo1, wo2, eo1, eo2);
+          W1o[q] = wo1;
+          W2o[q] = wo2;
+          E1[q] = eo1;
+          E2[q] = eo2;
+          if (check) {
+            const double df = (double)x - (double)phik[q];
+            n0 += df * df;
+            n1 += (double)phik[q] * (double)phik[q];
+          }
         }
       }
       if (check) block_sum2(n0, n1, reinterpret_cast<double*>(sm + ly.part));
@@ -407,7 +430,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
     done = k + 1;
     if (check) {
       double num = 0.0, den = 0.0;
-      for (int q = 0; q < kResC; ++q) {
+      for (int q = 0; q < C; ++q) {
         const double* p = reinterpret_cast<const double*>(rbase[q] + ly.part);
         num += p[0];
         den += p[1];
@@ -440,56 +463,66 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
 }
 
 template <int LOGL>
-cudaError_t go(const ResArgs& a, int members, size_t smem, cudaStream_t s, bool set_attr) {
+cudaError_t go(const ResArgs& a, int members, int C, size_t smem, cudaStream_t s, bool set_attr) {
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(kResThreads);
   cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = kResC;
+  at[0].val.clusterDim.x = C;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
   if (set_attr) {
     // the largest size any context may use, so that contexts of different
-    // sizes can share the kernel
+    // sizes can share the kernel; clusters of 16 need the non-portable size
     cudaError_t e = cudaFuncSetAttribute(k_resident<LOGL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kResMaxSmem);
     if (e != cudaSuccess) return e;
-    cfg.gridDim = dim3(kResC);
+    if (C > 8 &&
+        cudaFuncSetAttribute(k_resident<LOGL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return cudaErrorNotSupported;
+    }
+    cfg.gridDim = dim3(C);
     int clusters = 0;
     e = cudaOccupancyMaxActiveClusters(&clusters, k_resident<LOGL>, &cfg);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // a cluster shape the device refuses is not an error here
+      return cudaErrorNotSupported;
+    }
     return clusters > 0 ? cudaSuccess : cudaErrorNotSupported;
   }
-  cfg.gridDim = dim3(kResC * members);
+  cfg.gridDim = dim3(C * members);
   cfg.stream = s;
   return cudaLaunchKernelEx(&cfg, k_resident<LOGL>, a);
 }
 
 }  // namespace res
 
-size_t resident_smem(const Geo& geo, int R, int rec_R) {
-  const res::Lay l = res::make_lay(geo.M, geo.N, R, rec_R);
+size_t resident_smem(const Geo& geo, int R, int rec_R, int C) {
+  const res::Lay l = res::make_lay(geo.M, geo.N, R, rec_R, C);
   return (size_t)l.total * sizeof(float);
 }
 
-bool resident_supported(const Geo& geo, int R, int rec_R) {
+bool resident_supported(const Geo& geo, int R, int rec_R, int C) {
   if (geo.neumann || rec_R <= 0 || R < 0 || R > kMaxR) return false;
+  if (C != 8 && C != 16) return false;
   if (geo.N != 32 && geo.N != 64 && geo.N != 128 && geo.N != 256) return false;
-  if (geo.M < 2 * kResC || geo.M % kResC) return false;
-  return resident_smem(geo, R, rec_R) <= kResMaxSmem;
+  if (geo.M < 2 * C || geo.M % C) return false;
+  return resident_smem(geo, R, rec_R, C) <= kResMaxSmem;
 }
 
-cudaError_t launch_resident(const ResArgs& a, int members, const Geo& geo, size_t smem,
+cudaError_t launch_resident(const ResArgs& a, int members, const Geo& geo, int C, size_t smem,
                             cudaStream_t s, bool set_attr) {
   switch (geo.L) {
-    case 16: return res::go<4>(a, members, smem, s, set_attr);
-    case 32: return res::go<5>(a, members, smem, s, set_attr);
-    case 64: return res::go<6>(a, members, smem, s, set_attr);
-    case 128: return res::go<7>(a, members, smem, s, set_attr);
+    case 16: return res::go<4>(a, members, C, smem, s, set_attr);
+    case 32: return res::go<5>(a, members, C, smem, s, set_attr);
+    case 64: return res::go<6>(a, members, C, smem, s, set_attr);
+    case 128: return res::go<7>(a, members, C, smem, s, set_attr);
   }
   return cudaErrorInvalidValue;
 }

@@ -1,5 +1,6 @@
 """Resident outer iterations (sr_set_resident): whole iterations of Alg. 1 in
-one launch, the state held in the shared memory of one cluster of 8 CTAs.
+one launch, the state held in the shared memory of one cluster of 8 or 16
+CTAs.
 
 Against the FP64 oracle: one outer iteration from oracle states along the
 128^2 workload's trajectory and from random states with narrow-band pixels
@@ -51,16 +52,26 @@ def test_resident_one_iteration_two_disks(K0):
 @pytest.mark.parametrize("shape,R,d", [((64, 256), 4, 4.0), ((256, 64), 8, 8.0),
                                        ((512, 32), 3, 3.0), ((16, 32), 0, 1.0),
                                        ((32, 128), 2, 2.0), ((128, 128), 8, 8.0)])
-def test_resident_one_iteration_random_states(shape, R, d):
+@pytest.mark.parametrize("cluster", ["8", "16"])
+def test_resident_one_iteration_random_states(shape, R, d, cluster, monkeypatch):
+    """Both cluster sizes (SR_RESIDENT_CLUSTER): 2 to 64 rows per CTA."""
     H, W = shape
     phi, w1, w2, b1, b2, g = (f32(a) for a in synth.random_state(H, W, seed=H + 7 * W + R))
     p = oparams(R=R, d=d)
     ctx = context(H, W, R=R, d=d)
+    monkeypatch.setenv("SR_RESIDENT_CLUSTER", cluster)
+    if H < 2 * int(cluster):
+        with pytest.raises(sr.SRError) as e:
+            ctx.set_resident(True)
+        assert e.value.status == sr.SR_EUNSUPPORTED
+        ctx.close()
+        return
     ctx.set_resident(True)
     state = [phi, w1, w2, b1, b2]
     gpu, ref = one_iteration_both(ctx, state, g, p)
     err, nex = check_one_iteration(gpu, ref, state, g, p)
-    report("resident_one_iteration", shape=f"{H}x{W}", R=R, max_abs_dphi=err, exempt_pixels=nex)
+    report("resident_one_iteration", shape=f"{H}x{W}", R=R, cluster=cluster, max_abs_dphi=err,
+           exempt_pixels=nex)
     assert nex < 0.01 * H * W
     ctx.close()
 
