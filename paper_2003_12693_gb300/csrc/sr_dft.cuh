@@ -124,7 +124,11 @@ __device__ __forceinline__ void stage_table(float2* dst, const float2* __restric
 // stw is the stage-twiddle table: in shared memory, or with TWG in global
 // memory read through the read-only cache (the row passes: every CTA reads
 // the same table, so it stays in L1 and no per-CTA copy is needed).
-template <int LOGL, int LOGE, int S, bool INV, int STRIDE, bool DB = false, bool TWG = false>
+// With WS the exchanges synchronise the warp only: every sequence is held by
+// lanes of one warp (L / E threads dividing 32), so no other warp reads its
+// exchange area, and warps without a sequence need not take part.
+template <int LOGL, int LOGE, int S, bool INV, int STRIDE, bool DB = false, bool TWG = false,
+          bool WS = false>
 __device__ __forceinline__ void stages(float2 (&x)[1 << LOGE], float2* base, int u,
                                        const float2* stw, float2* base2 = nullptr) {
   using TP = TwPlan<LOGL, LOGE>;
@@ -169,25 +173,20 @@ __device__ __forceinline__ void stages(float2 (&x)[1 << LOGE], float2* base, int
 #pragma unroll
         for (int t = 0; t < R; ++t) buf[pad(o + (t << LOGNS)) * STRIDE] = x[b + t * NB];
       }
-      __syncthreads();
+      if constexpr (WS) {
+        static_assert((1 << LOGTP) <= 32, "a warp-synchronous sequence fits one warp");
+        __syncwarp();
+      } else {
+        __syncthreads();
+      }
 #pragma unroll
       for (int m = 0; m < E; ++m) x[m] = buf[pad(u + (m << LOGTP)) * STRIDE];
-      if constexpr (!DB) __syncthreads();
-      stages<LOGL, LOGE, S + 1, INV, STRIDE, DB, TWG>(x, base, u, stw, base2);
+      if constexpr (!DB) {
+        if constexpr (WS) __syncwarp();
+        else __syncthreads();
+      }
+      stages<LOGL, LOGE, S + 1, INV, STRIDE, DB, TWG, WS>(x, base, u, stw, base2);
     }
-  }
-}
-
-// The barriers of stages<LOGL, LOGE, 0, INV, STRIDE, DB, TWG> without the
-// arithmetic, for whole warps that hold no sequence: every __syncthreads of
-// the warps that do is met once.
-template <int LOGL, int LOGE, bool DB = false>
-__device__ __forceinline__ void stage_barriers() {
-  constexpr int NST = TwPlan<LOGL, LOGE>::NST;
-#pragma unroll
-  for (int s = 0; s + 1 < NST; ++s) {
-    __syncthreads();
-    if (!DB) __syncthreads();
   }
 }
 

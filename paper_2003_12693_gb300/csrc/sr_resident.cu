@@ -76,12 +76,13 @@ __host__ __device__ inline Lay make_lay(int M, int N, int R, int rec_R, int C) {
   l.G = lay_take(o, l.PL);
   l.X = lay_take(o, l.PL);   // RPC x L complex = PL floats
   l.X2 = lay_take(o, l.PL);
-  // scratch, one use per phase: the window's staged u planes and vertical
-  // sums; the row transforms' exchange rows (+1 row for idle thread slots);
+  // scratch, one use per phase: the window's sums v1, v2, staged u planes
+  // and vertical sums; the row transforms' exchange rows (+1 row for idle
+  // thread slots);
   // the column solve's copy of the rec_R spectrum rows before and after the
   // CTA's rows, then the forward values of the run and the warm-up after it
   const int L = N / 2, RS = L + L / 16;
-  const int win = 2 * (l.RPC + 2 * R) * l.SW + 2 * l.RPC * l.SW;
+  const int win = 2 * (l.RPC + 2 * R) * l.SW + 2 * l.RPC * l.SW + 2 * l.PL;
   const int fft = 2 * (l.RPC + 1) * RS;
   const int colu = 2 * rec_R * N + 2 * (l.RPC + rec_R) * L;
   int sc = win > fft ? win : fft;
@@ -161,10 +162,15 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
   cl.sync();
 
   // ---- separable window sum of u = h(x) w over the CTA's rows, Sec. 4:
-  // v1, v2 ([RPC][N]) replace the staged u planes at the start of scr
+  // v1, v2 ([RPC][N]) at the start of scr.  After the staging barrier each
+  // warp sums its own rows (row r by warp r mod NW, the rows the callers'
+  // per-pixel loops give the same warp), down the columns, then along the row
+  // it just summed, so only warp barriers follow.
   auto window = [&](int off_x, int off_w1, int off_w2) {
     const int SW = ly.SW, SH = RPC + 2 * R;
-    float* u1 = sm + ly.scr;
+    float* v1 = sm + ly.scr;
+    float* v2 = v1 + PL;
+    float* u1 = v2 + PL;
     float* u2 = u1 + SH * SW;
     float* V1 = u2 + SH * SW;
     float* V2 = V1 + RPC * SW;
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
       }
     }
     __syncthreads();
-    for (int r = warp; r < RPC; r += NW)
+    for (int r = warp; r < RPC; r += NW) {
       for (int c = lane; c < SW; c += 32) {
         float acc1 = 0.f, acc2 = 0.f;
         for (int p = 0; p <= 2 * R; ++p) {
@@ -198,10 +204,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
         V1[r * SW + c] = acc1;
         V2[r * SW + c] = acc2;
       }
-    __syncthreads();
-    float* v1 = u1;
-    float* v2 = u1 + PL;  // PL <= SH * SW: inside the u1 / u2 area
-    for (int r = warp; r < RPC; r += NW)
+      __syncwarp();
       for (int j = lane; j < N; j += 32) {
         float s1 = 0.f, s2 = 0.f;
         for (int p = 0; p <= 2 * R; ++p) {
@@ -211,7 +214,8 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
         v1[r * N + j] = s1;
         v2[r * N + j] = s2;
       }
-    __syncthreads();
+      __syncwarp();
+    }
   };
 
   auto any_band = [&](const float* x) {
@@ -220,8 +224,9 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
     return __syncthreads_or(any) != 0;
   };
 
-  // the row transforms: thread slot t = tid / TP takes row t; whole warps
-  // without a row only meet the stages' barriers
+  // the row transforms: thread slot t = tid / TP takes row t, whose TP
+  // threads are lanes of one warp, so the stages' exchanges synchronise the
+  // warp only; whole warps without a row skip the transforms
   const int ft = tid >> LOGTP, fu = tid & (TP - 1);
   const bool flive = ft < RPC;
   const bool fwarp = (tid & ~31) < RPC * TP;
@@ -278,19 +283,16 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
       }
       // ---- row R2C: z[n] = G[2n] + i G[2n+1], FFT_L, even/odd split -> X
       {
-        float2 x[E];
         if (fwarp) {
+          float2 x[E];
           const float2* row = reinterpret_cast<const float2*>(sm + ly.G + (flive ? ft : 0) * N);
 #pragma unroll
           for (int q = 0; q < E; ++q) x[q] = flive ? row[fu + (q << LOGTP)] : make_float2(0.f, 0.f);
-          stages<LOGL, 4, 0, false, 1, false, true>(x, fbase, fu, mb.tws16);
+          stages<LOGL, 4, 0, false, 1, false, true, true>(x, fbase, fu, mb.tws16);
 #pragma unroll
           for (int q = 0; q < E; ++q) fbase[pad(fu + (q << LOGTP))] = x[q];
-        } else {
-          stage_barriers<LOGL, 4>();
-        }
-        __syncthreads();
-        if (flive) {
+          __syncwarp();
+          if (flive) {
           float2* Xrow = reinterpret_cast<float2*>(sm + ly.X) + (size_t)ft * L;
 #pragma unroll
           for (int q = 0; q < E; ++q) {
@@ -306,30 +308,29 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
             const float2 O = make_float2(Dd.y, -Dd.x);
             Xrow[kk] = cadd(Ev, cmul(__ldg(&mb.twN[kk]), O));
           }
+          }
         }
       }
       cl.sync();
       // ---- column solve: forward and backward recursions per column and
-      // real/imaginary part over the CTA's rows.  The warm-ups read the rec_R
-      // spectrum rows before and after the CTA's rows (indices modulo M),
-      // first copied from the other CTAs into scratch by all threads, so that
-      // the recursions' chains read only this CTA's shared memory.
+      // real/imaginary part (task = 2 k + part, lane-contiguous) over the
+      // CTA's rows.  The warm-ups read the rec_R spectrum rows before and
+      // after the CTA's rows (indices modulo M); each thread first copies its
+      // task's values of those rows from the other CTAs (independent loads),
+      // so that the recursion's chain reads only this CTA's shared memory.
       {
         const int Rr = mb.rec_R;
         float* Hx = sm + ly.scr;          // [2 Rr][N]: the rows before, then after
         float* U = Hx + 2 * Rr * N;       // [(RPC + Rr)][2L]
         float* X2 = sm + ly.X2;
         const float* Xo = sm + ly.X;
-        for (int hr = warp; hr < 2 * Rr; hr += NW) {
-          int gi = hr < Rr ? r0 - Rr + hr : r0 + RPC + (hr - Rr);
-          gi %= M;
-          if (gi < 0) gi += M;
-          const float4* srow = reinterpret_cast<const float4*>(row_at(ly.X, gi));
-          for (int c4 = lane; c4 < N / 4; c4 += 32)
-            reinterpret_cast<float4*>(Hx + hr * N)[c4] = srow[c4];
-        }
-        __syncthreads();
         for (int task = tid; task < 2 * L; task += T) {
+          for (int hr = 0; hr < 2 * Rr; ++hr) {
+            int gi = hr < Rr ? r0 - Rr + hr : r0 + RPC + (hr - Rr);
+            gi %= M;
+            if (gi < 0) gi += M;
+            Hx[hr * N + task] = row_at(ly.X, gi)[task];
+          }
           const float4 p = __ldg(mb.rec + (task >> 1));
           const float r = (task & 1) ? p.z : p.x, sc = (task & 1) ? p.w : p.y;
           float uu = 0.f;
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
           const float2 Xo = cmul(Dd, cconj(__ldg(&mb.twN[kk])));
           x[q] = make_float2(Xe.x - Xo.y, Xe.y + Xo.x);
         }
-        stages<LOGL, 4, 0, true, 1, false, true>(x, fbase, fu, mb.tws16);
+        stages<LOGL, 4, 0, true, 1, false, true, true>(x, fbase, fu, mb.tws16);
         if (flive) {
           float2* prow = reinterpret_cast<float2*>(psi + ft * N);
 #pragma unroll
@@ -382,8 +383,6 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
             prow[fu + (q << LOGTP)] = make_float2(pv.x + x[q].x, pv.y + x[q].y);
           }
         }
-      } else {
-        stage_barriers<LOGL, 4>();
       }
       cl.sync();
     }
