@@ -326,7 +326,7 @@ cudaError_t launch_solve_small(const SmallArgs& a, cudaStream_t s, bool set_attr
 // multiple of C (>= 2 C), the recursion column solve (rec_R > 0), periodic
 // boundary.
 constexpr int kResCMax = 16;
-constexpr int kResThreads = 512;
+constexpr int kResThreads = 256;
 constexpr size_t kResMaxSmem = 220 * 1024;
 struct ResMember {
   Geo geo;

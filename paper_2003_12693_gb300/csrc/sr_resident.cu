@@ -124,6 +124,8 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
   constexpr int L = 1 << LOGL, N = 2 * L, E = 16, LOGTP = LOGL - 4, TP = 1 << LOGTP;
   constexpr int RS = L + L / 16;
   constexpr int T = kResThreads, NW = T / 32;
+  constexpr int NJ = N / 32;       // columns per lane of an image row
+  constexpr int NJW = NJ + 1;      // of a staged window row (N + 2R <= N + 32)
   extern __shared__ __align__(16) float sm[];
   __shared__ ResMember mb;
   __shared__ float* rbase[kResCMax];
@@ -177,42 +179,69 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
     for (int sr = warp; sr < SH; sr += NW) {
       const int gi = r0 - R + sr;
       const bool in = gi >= 0 && gi < M;
-      const float* px = in ? row_at(off_x, gi) : nullptr;
-      const float* p1 = in ? row_at(off_w1, gi) : nullptr;
-      const float* p2 = in ? row_at(off_w2, gi) : nullptr;
-      for (int sc = lane; sc < SW; sc += 32) {
-        const int j = sc - R;
-        float h1 = 0.f, h2 = 0.f;
-        if (in && j >= 0 && j < N) {
-          const float x = px[j];
-          const float h = in_band(x, m) ? band_h(x, m) : 0.f;
-          h1 = h * p1[j];
-          h2 = h * p2[j];
+      const float* px = in ? row_at(off_x, gi) : sm;
+      const float* p1 = in ? row_at(off_w1, gi) : sm;
+      const float* p2 = in ? row_at(off_w2, gi) : sm;
+      float xs[NJW], a1[NJW], a2[NJW];
+      bool ok[NJW];
+#pragma unroll
+      for (int c = 0; c < NJW; ++c) {
+        const int j = lane + 32 * c - R;
+        ok[c] = in && j >= 0 && j < N;
+        xs[c] = ok[c] ? px[j] : 0.f;
+        a1[c] = ok[c] ? p1[j] : 0.f;
+        a2[c] = ok[c] ? p2[j] : 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < NJW; ++c) {
+        const int sc = lane + 32 * c;
+        if (sc < SW) {
+          const float h = ok[c] && in_band(xs[c], m) ? band_h(xs[c], m) : 0.f;
+          u1[sr * SW + sc] = ok[c] ? h * a1[c] : 0.f;
+          u2[sr * SW + sc] = ok[c] ? h * a2[c] : 0.f;
         }
-        u1[sr * SW + sc] = h1;
-        u2[sr * SW + sc] = h2;
       }
     }
     __syncthreads();
     for (int r = warp; r < RPC; r += NW) {
-      for (int c = lane; c < SW; c += 32) {
-        float acc1 = 0.f, acc2 = 0.f;
-        for (int p = 0; p <= 2 * R; ++p) {
-          acc1 = fmaf(m.kw[p], u1[(r + p) * SW + c], acc1);
-          acc2 = fmaf(m.kw[p], u2[(r + p) * SW + c], acc2);
+      float acc1[NJW], acc2[NJW];
+#pragma unroll
+      for (int c = 0; c < NJW; ++c) acc1[c] = acc2[c] = 0.f;
+      for (int p = 0; p <= 2 * R; ++p) {
+        const float kw = m.kw[p];
+#pragma unroll
+        for (int c = 0; c < NJW; ++c) {
+          const int sc = lane + 32 * c;
+          if (sc < SW) {
+            acc1[c] = fmaf(kw, u1[(r + p) * SW + sc], acc1[c]);
+            acc2[c] = fmaf(kw, u2[(r + p) * SW + sc], acc2[c]);
+          }
         }
-        V1[r * SW + c] = acc1;
-        V2[r * SW + c] = acc2;
+      }
+#pragma unroll
+      for (int c = 0; c < NJW; ++c) {
+        const int sc = lane + 32 * c;
+        if (sc < SW) {
+          V1[r * SW + sc] = acc1[c];
+          V2[r * SW + sc] = acc2[c];
+        }
       }
       __syncwarp();
-      for (int j = lane; j < N; j += 32) {
-        float s1 = 0.f, s2 = 0.f;
-        for (int p = 0; p <= 2 * R; ++p) {
-          s1 = fmaf(m.kw[p], V1[r * SW + j + p], s1);
-          s2 = fmaf(m.kw[p], V2[r * SW + j + p], s2);
+      float s1[NJ], s2[NJ];
+#pragma unroll
+      for (int c = 0; c < NJ; ++c) s1[c] = s2[c] = 0.f;
+      for (int p = 0; p <= 2 * R; ++p) {
+        const float kw = m.kw[p];
+#pragma unroll
+        for (int c = 0; c < NJ; ++c) {
+          s1[c] = fmaf(kw, V1[r * SW + lane + 32 * c + p], s1[c]);
+          s2[c] = fmaf(kw, V2[r * SW + lane + 32 * c + p], s2[c]);
         }
-        v1[r * N + j] = s1;
-        v2[r * N + j] = s2;
+      }
+#pragma unroll
+      for (int c = 0; c < NJ; ++c) {
+        v1[r * N + lane + 32 * c] = s1[c];
+        v2[r * N + lane + 32 * c] = s2[c];
       }
       __syncwarp();
     }
@@ -262,21 +291,35 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
           const float* dn_row = i < RPC - 1 ? psi + (i + 1) * N
                                             : row_at(ly.psi, gi == M - 1 ? 0 : gi + 1);
           const float* e1u_row = i > 0 ? E1 + (i - 1) * N : row_at(ly.e1, gi == 0 ? M - 1 : gi - 1);
-          for (int j = lane; j < N; j += 32) {
-            const int q = i * N + j;
-            const float x = psi[q];
-            const float lf = psi[i * N + ((j - 1) & (N - 1))];
-            const float rt = psi[i * N + ((j + 1) & (N - 1))];
-            float dv;
-            if (s == 0) {  // div e, fixed over the inner loop
-              const float e2l = E2[i * N + ((j - 1) & (N - 1))];
-              dv = div_e(E1[q], e1u_row[j], E2[q], e2l);
-              D[q] = dv;
-            } else {
-              dv = D[q];
+          // every load of the row first, then the arithmetic, then the stores
+          float x[NJ], up[NJ], dn[NJ], lf[NJ], rt[NJ], dv[NJ];
+          float w1[NJ], w2[NJ], gg[NJ], vv1[NJ], vv2[NJ];
+#pragma unroll
+          for (int c = 0; c < NJ; ++c) {
+            const int j = lane + 32 * c, q = i * N + j;
+            x[c] = psi[q];
+            up[c] = up_row[j];
+            dn[c] = dn_row[j];
+            lf[c] = psi[i * N + ((j - 1) & (N - 1))];
+            rt[c] = psi[i * N + ((j + 1) & (N - 1))];
+            if (s == 0)  // div e, fixed over the inner loop
+              dv[c] = div_e(E1[q], e1u_row[j], E2[q], E2[i * N + ((j - 1) & (N - 1))]);
+            else
+              dv[c] = D[q];
+            if (band) {
+              w1[c] = W1[q];
+              w2[c] = W2[q];
+              gg[c] = Gg[q];
+              vv1[c] = v1[q];
+              vv2[c] = v2[q];
             }
-            const float f = rhs_bulk(m, x, up_row[j], dn_row[j], lf, rt, dv);
-            G[q] = band ? rhs_band(m, f, x, W1[q], W2[q], Gg[q], v1[q], v2[q]) : m.tau * f;
+          }
+#pragma unroll
+          for (int c = 0; c < NJ; ++c) {
+            const int q = i * N + lane + 32 * c;
+            const float f = rhs_bulk(m, x[c], up[c], dn[c], lf[c], rt[c], dv[c]);
+            G[q] = band ? rhs_band(m, f, x[c], w1[c], w2[c], gg[c], vv1[c], vv2[c]) : m.tau * f;
+            if (s == 0) D[q] = dv[c];
           }
         }
         __syncthreads();
@@ -315,22 +358,30 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
       // ---- column solve: forward and backward recursions per column and
       // real/imaginary part (task = 2 k + part, lane-contiguous) over the
       // CTA's rows.  The warm-ups read the rec_R spectrum rows before and
-      // after the CTA's rows (indices modulo M); each thread first copies its
-      // task's values of those rows from the other CTAs (independent loads),
-      // so that the recursion's chain reads only this CTA's shared memory.
+      // after the CTA's rows (indices modulo M), first copied from the other
+      // CTAs into scratch by all warps, so that the recursions' chains read
+      // only this CTA's shared memory.
       {
         const int Rr = mb.rec_R;
         float* Hx = sm + ly.scr;          // [2 Rr][N]: the rows before, then after
         float* U = Hx + 2 * Rr * N;       // [(RPC + Rr)][2L]
         float* X2 = sm + ly.X2;
         const float* Xo = sm + ly.X;
+        for (int hr = warp; hr < 2 * Rr; hr += NW) {
+          int gi = hr < Rr ? r0 - Rr + hr : r0 + RPC + (hr - Rr);
+          gi %= M;
+          if (gi < 0) gi += M;
+          const float4* srow = reinterpret_cast<const float4*>(row_at(ly.X, gi));
+          float4 t[(N / 4 + 31) / 32];
+#pragma unroll
+          for (int c = 0; c < (N / 4 + 31) / 32; ++c)
+            if (lane + 32 * c < N / 4) t[c] = srow[lane + 32 * c];
+#pragma unroll
+          for (int c = 0; c < (N / 4 + 31) / 32; ++c)
+            if (lane + 32 * c < N / 4) reinterpret_cast<float4*>(Hx + hr * N)[lane + 32 * c] = t[c];
+        }
+        __syncthreads();
         for (int task = tid; task < 2 * L; task += T) {
-          for (int hr = 0; hr < 2 * Rr; ++hr) {
-            int gi = hr < Rr ? r0 - Rr + hr : r0 + RPC + (hr - Rr);
-            gi %= M;
-            if (gi < 0) gi += M;
-            Hx[hr * N + task] = row_at(ly.X, gi)[task];
-          }
           const float4 p = __ldg(mb.rec + (task >> 1));
           const float r = (task & 1) ? p.z : p.x, sc = (task & 1) ? p.w : p.y;
           float uu = 0.f;
@@ -400,25 +451,44 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
         const int gi = r0 + i;
         const float* dn_row = i < RPC - 1 ? psi + (i + 1) * N
                                           : row_at(ly.psi, gi == M - 1 ? 0 : gi + 1);
-        for (int j = lane; j < N; j += 32) {
-          const int q = i * N + j;
-          const float x = psi[q];
-          const float dn = dn_row[j];
-          const float rt = psi[i * N + ((j + 1) & (N - 1))];
-          const float b1 = E1[q] + W1[q], b2 = E2[q] + W2[q];
+        float x[NJ], dn[NJ], rt[NJ], e1[NJ], e2[NJ], w1[NJ], w2[NJ], gg[NJ], vv1[NJ], vv2[NJ];
+        float pk[NJ];
+#pragma unroll
+        for (int c = 0; c < NJ; ++c) {
+          const int j = lane + 32 * c, q = i * N + j;
+          x[c] = psi[q];
+          dn[c] = dn_row[j];
+          rt[c] = psi[i * N + ((j + 1) & (N - 1))];
+          e1[c] = E1[q];
+          e2[c] = E2[q];
+          w1[c] = W1[q];
+          w2[c] = W2[q];
+          if (band) {
+            gg[c] = Gg[q];
+            vv1[c] = v1[q];
+            vv2[c] = v2[q];
+          }
+          if (check) pk[c] = phik[q];
+        }
+#pragma unroll
+        for (int c = 0; c < NJ; ++c) {
+          const int q = i * N + lane + 32 * c;
+          const float b1 = e1[c] + w1[c], b2 = e2[c] + w2[c];
           float wo1, wo2, eo1, eo2;
           if (band)
-            wb_point<true>(m, x, dn - x, rt - x, b1, b2, Gg[q], v1[q], v2[q], wo1, wo2, eo1, eo2);
+            wb_point<true>(m, x[c], dn[c] - x[c], rt[c] - x[c], b1, b2, gg[c], vv1[c], vv2[c], wo1,
+                           wo2, eo1, eo2);
           else
-            wb_point<false>(m, x, dn - x, rt - x, b1, b2, 0.f, 0.f, 0.f, wo1, wo2, eo1, eo2);
+            wb_point<false>(m, x[c], dn[c] - x[c], rt[c] - x[c], b1, b2, 0.f, 0.f, 0.f, wo1, wo2,
+                            eo1, eo2);
           W1o[q] = wo1;
           W2o[q] = wo2;
           E1[q] = eo1;
           E2[q] = eo2;
           if (check) {
-            const double df = (double)x - (double)phik[q];
+            const double df = (double)x[c] - (double)pk[c];
             n0 += df * df;
-            n1 += (double)phik[q] * (double)phik[q];
+            n1 += (double)pk[c] * (double)pk[c];
           }
         }
       }
@@ -512,6 +582,8 @@ bool resident_supported(const Geo& geo, int R, int rec_R, int C) {
   if (C != 8 && C != 16) return false;
   if (geo.N != 32 && geo.N != 64 && geo.N != 128 && geo.N != 256) return false;
   if (geo.M < 2 * C || geo.M % C) return false;
+  // one pass of the row transforms: the CTA's rows at L / 16 threads each
+  if ((geo.M / C) * (geo.L / 16) > kResThreads) return false;
   return resident_smem(geo, R, rec_R, C) <= kResMaxSmem;
 }
 
