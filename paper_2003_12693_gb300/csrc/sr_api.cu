@@ -113,6 +113,7 @@ struct sr_ctx {
   int resident = 0;
   size_t res_smem = 0;
   int res_C = 0;                      // CTAs per cluster (8 or 16)
+  float2* res_tws4 = nullptr;         // stage twiddles of the rows, 4 values per thread
   srk::ResMember* res_dev = nullptr;  // the image's description at parity 0 and 1
   int* res_done = nullptr;            // iterations the last launch ran
   int* res_done_host = nullptr;       // pinned copy
@@ -1048,7 +1049,7 @@ void sr_destroy(sr_ctx* c) {
                   c->tws[0], c->tws[1], c->tws[2], c->tws[3], c->wfx1, c->wfx2,
                   c->X2, c->rec, c->aos_T1, c->aos_X2, c->tw_row2, c->tw_n2,
                   c->tws2[0], c->tws2[1], c->G2, c->Xn, c->Xn2, c->rec2, c->res_dev,
-                  c->res_done};
+                  c->res_done, c->res_tws4};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -1607,6 +1608,10 @@ sr_status sr_set_resident(sr_ctx* c, int on) {
     if (e == cudaErrorMemoryAllocation) return fail(c, SR_ENOMEM, "allocation failed");
     SR_CUDA(c, e);
   }
+  if (!c->res_tws4) {
+    const sr_status st = upload(c, &c->res_tws4, stage_twiddle_table(c->L, 2));
+    if (st != SR_OK) return st;
+  }
   srk::ResMember mb[2];
   for (int p = 0; p < 2; ++p) {
     srk::ResMember& r = mb[p];
@@ -1624,7 +1629,7 @@ sr_status sr_set_resident(sr_ctx* c, int on) {
     }
     r.e1 = c->e1;
     r.e2 = c->e2;
-    r.tws16 = c->fft_row.tws16;
+    r.tws4 = c->res_tws4;
     r.twN = c->tw_n;
     r.rec = c->rec;
     r.done = c->res_done;

@@ -340,7 +340,7 @@ struct ResMember {
   float* w2[2];
   float* e1;             // e = b - w (one buffer, updated in place)
   float* e2;
-  const float2* tws16;   // stage twiddles of the row transform (16 values per thread)
+  const float2* tws4;    // stage twiddles of the row transform (4 values per thread)
   const float2* twN;     // exp(-2 pi i k / N), k < L
   const float4* rec;     // per-column (r, s) pairs of the column recursions
   int* done;             // outer iterations run (written once, at the end)

@@ -121,7 +121,11 @@ __device__ __forceinline__ void block_sum2(double a, double b, double* out) {
 // index needs a division by a runtime width.
 template <int LOGL>
 __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
-  constexpr int L = 1 << LOGL, N = 2 * L, E = 16, LOGTP = LOGL - 4, TP = 1 << LOGTP;
+  // the row transforms at 4 values per thread: L / 4 threads per row spread
+  // the transforms over more warps than 16 values would, which shortens the
+  // chain the other warps wait for at the next barrier
+  constexpr int LOGE = 2;
+  constexpr int L = 1 << LOGL, N = 2 * L, E = 1 << LOGE, LOGTP = LOGL - LOGE, TP = 1 << LOGTP;
   constexpr int RS = L + L / 16;
   constexpr int T = kResThreads, NW = T / 32;
   constexpr int NJ = N / 32;       // columns per lane of an image row
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
           const float2* row = reinterpret_cast<const float2*>(sm + ly.G + (flive ? ft : 0) * N);
 #pragma unroll
           for (int q = 0; q < E; ++q) x[q] = flive ? row[fu + (q << LOGTP)] : make_float2(0.f, 0.f);
-          stages<LOGL, 4, 0, false, 1, false, true, true>(x, fbase, fu, mb.tws16);
+          stages<LOGL, LOGE, 0, false, 1, false, true, true>(x, fbase, fu, mb.tws4);
 #pragma unroll
           for (int q = 0; q < E; ++q) fbase[pad(fu + (q << LOGTP))] = x[q];
           __syncwarp();
@@ -425,7 +429,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
           const float2 Xo = cmul(Dd, cconj(__ldg(&mb.twN[kk])));
           x[q] = make_float2(Xe.x - Xo.y, Xe.y + Xo.x);
         }
-        stages<LOGL, 4, 0, true, 1, false, true, true>(x, fbase, fu, mb.tws16);
+        stages<LOGL, LOGE, 0, true, 1, false, true, true>(x, fbase, fu, mb.tws4);
         if (flive) {
           float2* prow = reinterpret_cast<float2*>(psi + ft * N);
 #pragma unroll
@@ -582,8 +586,8 @@ bool resident_supported(const Geo& geo, int R, int rec_R, int C) {
   if (C != 8 && C != 16) return false;
   if (geo.N != 32 && geo.N != 64 && geo.N != 128 && geo.N != 256) return false;
   if (geo.M < 2 * C || geo.M % C) return false;
-  // one pass of the row transforms: the CTA's rows at L / 16 threads each
-  if ((geo.M / C) * (geo.L / 16) > kResThreads) return false;
+  // one pass of the row transforms: the CTA's rows at L / 4 threads each
+  if ((geo.M / C) * (geo.L / 4) > kResThreads) return false;
   return resident_smem(geo, R, rec_R, C) <= kResMaxSmem;
 }
 
