@@ -327,6 +327,47 @@ def batched_sample(stream, n_images: int = 256, iters: int = 100) -> dict:
                    f"about {P * 14 * 4 / 1e9:.1f} GB)"}
 
 
+def resident_sample(stream, wl, iters: int = 100, reps: int = 5) -> dict | None:
+    """Whole-run launches with the state resident in one cluster's shared
+    memory (sr_set_resident) against the default path, both as a user runs
+    many iterations: sr_iterate(iters) per call, CUDA events, no L2 flush
+    (the state is L2-sized).  None where the image size does not allow it."""
+    import numpy as np
+    import torch
+
+    from paper_2003_12693_gb300 import sr
+
+    out = {}
+    for resident in (True, False):
+        ctx = sr.Context(wl.H, wl.W, sr.make_params(win_radius=wl.R, d=wl.d), stream)
+        if resident:
+            try:
+                ctx.set_resident(True)
+            except sr.SRError as e:
+                ctx.close()
+                if e.status == sr.SR_EUNSUPPORTED:
+                    return None
+                raise
+        ctx.edge_function(torch.from_numpy(wl.image().astype(np.float32)).cuda())
+        ctx.set_phi(torch.from_numpy(wl.phi0().astype(np.float32)).cuda())
+        ctx.iterate(iters)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.iterate(iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / (reps * iters)
+        out["resident" if resident else "default"] = {
+            "us_per_iteration": us, "value": wl.H * wl.W / us, "unit": UNIT}
+        ctx.close()
+    out["how"] = (f"sr_iterate({iters}) per call, {reps} calls after one untimed call; resident: "
+                  "one launch per call, the state in one cluster's shared memory; default: the "
+                  "graph of 13 launches per iteration")
+    return out
+
+
 def warm_start_net_sample(stream, H: int = 256, W: int = 256, B: int = 32,
                           steps: int = 20) -> dict:
     """The warm-start network (include/sr_net.h) at its configured size: one
@@ -578,6 +619,7 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
     if rank != 0:
         return
     batched = None if args.no_batched else batched_sample(stream)
+    resident_runs = resident_sample(stream, wl) if world == 1 else None
     wsnet = None if args.no_net else warm_start_net_sample(stream)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -601,6 +643,7 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched": batched,
+        "resident_runs": resident_runs,
         "warm_start_net": wsnet,
         "gpu_launches": launches,
         "prewarm": {"seconds": args.prewarm_s, "steps": prewarm_steps},
@@ -627,9 +670,11 @@ def main():
                     help="print only the warm-start network sample (profiling runs)")
     ap.add_argument("--net-steps", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--resident", default="auto", choices=["auto", "on", "off"],
-                    help="sr_set_resident: whole iterations in one cluster launch where the "
-                         "image size allows it (auto), always (on: fail otherwise) or never")
+    ap.add_argument("--resident", default="off", choices=["auto", "on", "off"],
+                    help="time the steps with sr_set_resident (whole iterations in one cluster "
+                         "launch) where the image size allows it (auto), always (on: fail "
+                         "otherwise) or never (off; the line's resident_runs key compares "
+                         "the two paths on many-iteration calls where the size allows)")
     ap.add_argument("--prewarm-s", type=float, default=1.0,
                     help="untimed back-to-back steps before the warm-up steps (clock ramp)")
     args = ap.parse_args()
