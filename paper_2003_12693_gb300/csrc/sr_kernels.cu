@@ -797,156 +797,6 @@ __global__ void __launch_bounds__(kTN, 4) k_prep(const PrepArgs a) {
   st4(a.G + q.o, make_float4(out[0], out[1], out[2], out[3]));
 }
 
-// The same right-hand side as k_prep<R, DIV> (DIV = kDivStore or kDivLoad),
-// computed by persistent CTAs that stream the tiles: while tile t is
-// computed, the bulk planes of the next LA tiles (psi with a one-pixel halo,
-// and div e or e1, e2 with the rows / columns the backward divergence needs)
-// are already on their way into a ring of NS shared-memory stages by
-// 16-byte asynchronous copies.  One CTA thus keeps several tiles' loads in
-// flight instead of exposing the full load latency once per tile, which is
-// what bounds k_prep.  Neighbour values come from the staged tile (indices
-// wrapped modulo the image, so partial tiles and the periodic stencil need
-// no special case).  The per-pixel arithmetic is k_prep's (rhs_bulk,
-// rhs_band, the Neumann overrides), so the results are the same bit for bit.
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void cp16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int NPEND>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
-}
-
-constexpr int kStreamPW = 40;                    // staged psi row: columns -4 .. 35
-constexpr int kStreamPSZ = 34 * kStreamPW;       // rows -1 .. 32
-template <int DIV>
-__host__ __device__ constexpr int stream_stage_floats() {
-  return kStreamPSZ + (DIV == kDivLoad ? 32 * 32 : 33 * 32 + 32 * 36);
-}
-
-template <int R, int DIV, int NS>
-__global__ void __launch_bounds__(kTN, 2) k_prep_stream(const PrepArgs a, int ntiles, int tiles_x) {
-  extern __shared__ __align__(16) float smem_f[];
-  // tiles in flight beyond the current one: stage (it + LA) % NS was last read
-  // in iteration it - 1, before that iteration's block-wide band test
-  constexpr int LA = NS - 1;
-  constexpr int SS = stream_stage_floats<DIV>();
-  float* band_sm = smem_f + NS * SS;
-  pdl_wait();
-  pdl_trigger();
-  const Model& m = a.mod;
-  const int M = a.geo.M, N = a.geo.N;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTBX + tx;
-  // staged rows i0 - 1 .. i0 + 32 and columns j0 - 4 .. j0 + 35 modulo the
-  // image (sides >= 16, so up to two periods away)
-  auto wrap_r = [M](int i) { return ((i % M) + M) % M; };
-  auto wrap_c = [N](int j) { return ((j % N) + N) % N; };
-  auto issue = [&](int t, int st) {
-    if (t < ntiles) {
-      const int i0 = (t / tiles_x) * kT, j0 = (t % tiles_x) * kT;
-      float* S = smem_f + st * SS;
-      for (int c = tid; c < 34 * 10; c += kTN) {
-        const int r = c / 10 - 1, k = c % 10;
-        cp16(S + (r + 1) * kStreamPW + 4 * k,
-             a.psi + (size_t)wrap_r(i0 + r) * N + wrap_c(j0 - 4 + 4 * k));
-      }
-      float* S2 = S + kStreamPSZ;
-      if (DIV == kDivLoad) {
-        for (int c = tid; c < 32 * 8; c += kTN) {
-          const int r = c / 8, k = c % 8;
-          cp16(S2 + r * 32 + 4 * k, a.D + (size_t)wrap_r(i0 + r) * N + wrap_c(j0 + 4 * k));
-        }
-      } else {
-        for (int c = tid; c < 33 * 8; c += kTN) {  // e1, rows -1 .. 31
-          const int r = c / 8 - 1, k = c % 8;
-          cp16(S2 + (r + 1) * 32 + 4 * k, a.e1 + (size_t)wrap_r(i0 + r) * N + wrap_c(j0 + 4 * k));
-        }
-        float* S3 = S2 + 33 * 32;
-        for (int c = tid; c < 32 * 9; c += kTN) {  // e2, columns -4 .. 31
-          const int r = c / 9, k = c % 9;
-          cp16(S3 + r * 36 + 4 * k, a.e2 + (size_t)wrap_r(i0 + r) * N + wrap_c(j0 - 4 + 4 * k));
-        }
-      }
-    }
-    cp_commit();  // every thread commits one group per call, empty or not
-  };
-  int t = blockIdx.x;
-  for (int k = 0; k < LA; ++k) issue(t + k * (int)gridDim.x, k % NS);
-  for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
-    issue(t + LA * (int)gridDim.x, (it + LA) % NS);
-    cp_wait<LA>();
-    __syncthreads();  // every thread's copies of tile t are in shared memory
-    const float* S = smem_f + (it % NS) * SS;
-    const int i0 = (t / tiles_x) * kT, j0 = (t % tiles_x) * kT;
-    const int i = i0 + ty, j = j0 + 4 * tx;
-    const bool live = i < M && j < N;
-    const float* prow = S + (ty + 1) * kStreamPW + 4 + 4 * tx;
-    const float4 X = *reinterpret_cast<const float4*>(prow);
-    float4 UP = *reinterpret_cast<const float4*>(prow - kStreamPW);
-    float4 DN = *reinterpret_cast<const float4*>(prow + kStreamPW);
-    float LF = prow[-1], RT = prow[4];
-    float4 Dv;
-    if (DIV == kDivLoad) {
-      Dv = *reinterpret_cast<const float4*>(S + kStreamPSZ + ty * 32 + 4 * tx);
-    } else {
-      const float* e1r = S + kStreamPSZ + (ty + 1) * 32 + 4 * tx;
-      float4 E1 = *reinterpret_cast<const float4*>(e1r);
-      float4 E1u = *reinterpret_cast<const float4*>(e1r - 32);
-      const float* e2r = S + kStreamPSZ + 33 * 32 + ty * 36 + 4 + 4 * tx;
-      float4 E2 = *reinterpret_cast<const float4*>(e2r);
-      float e2l = e2r[-1];
-      if (a.geo.neumann) {
-        if (i == 0) E1u = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i == M - 1) E1 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (j == 0) e2l = 0.f;
-        if (j + 4 == N) E2.w = 0.f;
-      }
-      Dv = make_float4(div_e(E1.x, E1u.x, E2.x, e2l), div_e(E1.y, E1u.y, E2.y, E2.x),
-                       div_e(E1.z, E1u.z, E2.z, E2.y), div_e(E1.w, E1u.w, E2.w, E2.z));
-      if (live) st4(a.D + (size_t)i * N + j, Dv);
-    }
-    const bool band = __syncthreads_or(live && any_band4(X, m)) != 0;
-    if (a.geo.neumann) {
-      if (i == 0) UP = X;
-      if (i == M - 1) DN = X;
-      if (j == 0) LF = X.x;
-      if (j + 4 == N) RT = X.w;
-    }
-    float f[4];
-    {
-      const float x[4] = {X.x, X.y, X.z, X.w};
-      const float up[4] = {UP.x, UP.y, UP.z, UP.w}, dn[4] = {DN.x, DN.y, DN.z, DN.w};
-      const float lf[4] = {LF, X.x, X.y, X.z}, rt[4] = {X.y, X.z, X.w, RT};
-      const float dv[4] = {Dv.x, Dv.y, Dv.z, Dv.w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) f[q] = rhs_bulk(m, x[q], up[q], dn[q], lf[q], rt[q], dv[q]);
-    }
-    float out[4];
-    if (band) {  // uniform across the block
-      const size_t o = live ? (size_t)i * N + j : 0;
-      const float4 W1 = ld4_if(live, a.w1 + o), W2 = ld4_if(live, a.w2 + o);
-      const float4 G4 = ld4_if(live, a.g + o);
-      float v1[4], v2[4];
-      band_window<R>(band_sm, a.geo, m, a.psi, a.w1, a.w2, i0, j0, v1, v2);
-      const float x[4] = {X.x, X.y, X.z, X.w};
-      const float w1[4] = {W1.x, W1.y, W1.z, W1.w}, w2[4] = {W2.x, W2.y, W2.z, W2.w};
-      const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) out[q] = rhs_band(m, f[q], x[q], w1[q], w2[q], gg[q], v1[q], v2[q]);
-      __syncthreads();  // band_sm is staged again by the next band tile
-    } else {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) out[q] = m.tau * f[q];
-    }
-    if (live) st4(a.G + (size_t)i * N + j, make_float4(out[0], out[1], out[2], out[3]));
-  }
-  cp_wait<0>();
-}
-
 // w and b update (Eqs. (41), (42), (40), (23)) with the window sum fused in.
 // Soft threshold then projection: w = B/|B| if |B| > t, else 0.  Same
 // structure as k_prep: all bulk loads issued up front, window sum and g only
@@ -1236,11 +1086,7 @@ cudaError_t configure_kernels() {
   if ((e = allow_big_smem(k_prep<r, kDivCompute>)) != cudaSuccess) return e; \
   if ((e = allow_big_smem(k_prep<r, kDivStore>)) != cudaSuccess) return e;   \
   if ((e = allow_big_smem(k_prep<r, kDivLoad>)) != cudaSuccess) return e;    \
-  if ((e = allow_big_smem(k_wb_update<r>)) != cudaSuccess) return e;          \
-  if ((e = allow_big_smem(k_prep_stream<r, kDivStore, 4>)) != cudaSuccess) return e; \
-  if ((e = allow_big_smem(k_prep_stream<r, kDivLoad, 4>)) != cudaSuccess) return e;  \
-  if ((e = allow_big_smem(k_prep_stream<r, kDivStore, 6>)) != cudaSuccess) return e; \
-  if ((e = allow_big_smem(k_prep_stream<r, kDivLoad, 6>)) != cudaSuccess) return e;
+  if ((e = allow_big_smem(k_wb_update<r>)) != cudaSuccess) return e;
   SR_FOR_R(SR_CASE)
 #undef SR_CASE
   return cudaSuccess;
@@ -1339,55 +1185,9 @@ cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// SR_PREP_STREAM=0 keeps the one-tile-per-CTA k_prep for every inner step;
-// otherwise the steps that store or load div e use k_prep_stream with NS
-// stages (SR_PREP_STAGES, 4 or 6).
-static int prep_stream_stages() {
-  static int ns = -1;
-  if (ns < 0) {
-    const char* on = std::getenv("SR_PREP_STREAM");
-    const char* st = std::getenv("SR_PREP_STAGES");
-    ns = (on && on[0] == '0') ? 0 : (st && std::atoi(st) == 6 ? 6 : 4);
-  }
-  return ns;
-}
-
-template <int R, int DIV, int NS>
-static cudaError_t launch_prep_stream(const PrepArgs& a, cudaStream_t s) {
-  const size_t sm = (size_t)(NS * stream_stage_floats<DIV>() + tile32_floats(R)) * sizeof(float);
-  static int per_sm = -1;  // per (R, DIV, NS) instantiation; the shared-memory
-                           // limit is raised by configure_kernels
-  if (per_sm < 0) {
-    const cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prep_stream<R, DIV, NS>, kTN, sm);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-  }
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int tiles_x = (a.geo.N + kT - 1) / kT;
-  const int ntiles = tiles_x * ((a.geo.M + kT - 1) / kT);
-  const int grid = std::max(1, std::min(ntiles, nsm * per_sm));
-  return launch_k(k_prep_stream<R, DIV, NS>, dim3(grid), dim3(kTBX, kTBY), sm, s, a, ntiles, tiles_x);
-}
-
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
   const dim3 g = tile32_grid(a.geo), b(kTBX, kTBY);
   const size_t sm = tile32_smem(a.mod.R);
-  const int ns = prep_stream_stages();
-  if (ns && a.D != nullptr) {
-    switch (a.mod.R) {
-#define SR_CASE(r)                                                                            \
-  case r:                                                                                     \
-    if (ns == 6)                                                                              \
-      return a.D_load ? launch_prep_stream<r, kDivLoad, 6>(a, s) : launch_prep_stream<r, kDivStore, 6>(a, s); \
-    return a.D_load ? launch_prep_stream<r, kDivLoad, 4>(a, s) : launch_prep_stream<r, kDivStore, 4>(a, s);
-      SR_FOR_R(SR_CASE)
-#undef SR_CASE
-      default: return cudaErrorInvalidValue;
-    }
-  }
   switch (a.mod.R) {
 #define SR_CASE(r) \
   case r:                                                                    \
