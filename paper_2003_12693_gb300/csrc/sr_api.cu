@@ -2032,7 +2032,7 @@ sr_status sr_group_create(sr_ctx* const* members, int n, sr_group** out) {
     }
   }
   std::string why;
-  for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = group_build(g, p, why);
+  for (int p = 0; p < 2 && e == cudaSuccess && g->n_graph > 0; ++p) e = group_build(g, p, why);
   if (e != cudaSuccess) {
     group_release(g);
     if (!why.empty()) return fail(c0, SR_ECUDA, "sr_group_create: " + why);
@@ -2086,7 +2086,7 @@ sr_status sr_group_run(sr_group* g, int max_outer, double tol, int check_every, 
     SR_CUDA(c0, cudaMalloc((void**)&g->loop, sizeof(srk::LoopState) * n));
     SR_CUDA(c0, cudaMallocHost((void**)&g->loop_host, sizeof(srk::LoopState) * n));
   }
-  if (!g->run_graph || g->run_step != step || g->run_parity != c0->cur) {
+  if (g->n_graph > 0 && (!g->run_graph || g->run_step != step || g->run_parity != c0->cur)) {
     if (g->run_graph) cudaGraphExecDestroy(g->run_graph);
     g->run_graph = nullptr;
     std::string why;

@@ -123,6 +123,39 @@ def test_group_iterate_with_resident_members_matches_members_alone(n_iter):
         c.close()
 
 
+def test_group_of_resident_members_only():
+    """Every member resident: no graph at all, one launch per row length
+    (two here); run and iterate still match the members alone bit for bit."""
+    sizes = [(128, 128), (64, 64), (256, 64), (64, 64)]
+
+    def members():
+        out = []
+        for k, (H, W) in enumerate(sizes):
+            img = synth.ellipse_scene(700 + k, H=H, W=W, scale=0.125)
+            ctx = context(H, W, R=4, d=4.0)
+            ctx.set_resident(True)
+            ctx.edge_function(dev(img))
+            ctx.set_phi(dev(synth.inset_rect_sdf(H, W)))
+            out.append(ctx)
+        return out
+    grouped = members()
+    grp = sr.Group(grouped)
+    assert grp.tune() in (4, 8, 16, 32, 64)
+    grp.iterate(3)
+    done, rel, _ = grp.run(8, 0.0, check_every=4)
+    assert done == [8] * len(sizes)
+    alone = members()
+    for c in alone:
+        c.iterate(3)
+        c.iterate(8)
+    for a, b in zip(alone, grouped):
+        for x, y in zip(a.get_state(), b.get_state()):
+            assert np.array_equal(host(x), host(y))
+    grp.close()
+    for c in alone + grouped:
+        c.close()
+
+
 def test_group_tune_picks_a_lane_count_and_leaves_the_states():
     """sr_group_tune times the group at several lane counts; the members'
     states come back bit for bit, and the tuned group still iterates every
