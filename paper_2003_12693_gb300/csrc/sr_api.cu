@@ -66,7 +66,6 @@ struct sr_ctx {
   float* stage = nullptr;
   float* G = nullptr;         // increment right-hand side of the current inner step
   float* divE = nullptr;      // div e of the current outer iteration (fixed over the inner loop)
-  int* band_list = nullptr;   // tiles with narrow-band pixels of the current step, then 2 counters
   unsigned char* mask_dev = nullptr;
   float2* X = nullptr;
   float2* X2 = nullptr;       // output of the recursion column pass (schedule 7)
@@ -633,11 +632,8 @@ sr_status enqueue_phi_step(sr_ctx* c, cudaStream_t s, const float* psi_in, const
     pa.G = c->G;
     pa.D = div_mode ? c->divE : nullptr;
     pa.D_load = div_mode == 2;
-    pa.band_list = c->band_list;
-    pa.band_count = c->band_list + c->n_tile32;
     st = run_kernel(c, SR_KCLASS_PREP, s, "k_prep", [&] { return srk::launch_prep(pa, s); });
     if (st != SR_OK) return st;
-    if (srk::prep_split(pa)) c->launches += 1;  // the bulk and the band pass
     src = c->G;
     if (c->phi_solver == 1) {
       srk::AosArgs aa = c->aos;
@@ -1053,7 +1049,7 @@ void sr_destroy(sr_ctx* c) {
                   c->tws[0], c->tws[1], c->tws[2], c->tws[3], c->wfx1, c->wfx2,
                   c->X2, c->rec, c->aos_T1, c->aos_X2, c->tw_row2, c->tw_n2,
                   c->tws2[0], c->tws2[1], c->G2, c->Xn, c->Xn2, c->rec2, c->res_dev,
-                  c->res_done, c->res_tws4, c->band_list};
+                  c->res_done, c->res_tws4};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -1155,8 +1151,6 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
   CREATE_CUDA(dev_alloc((void**)&c->X, (size_t)H * L * sizeof(float2)));
   CREATE_CUDA(dev_alloc((void**)&c->partials, (size_t)c->n_tile * 3 * sizeof(double)));
   CREATE_CUDA(dev_alloc((void**)&c->red, 4 * sizeof(double)));
-  CREATE_CUDA(dev_alloc((void**)&c->band_list, (size_t)(c->n_tile32 + 2) * sizeof(int)));
-  CREATE_CUDA(cudaMemset(c->band_list, 0, (size_t)(c->n_tile32 + 2) * sizeof(int)));
   CREATE_CUDA(host_alloc((void**)&c->red_host, 4 * sizeof(double)));
   for (float** pl : planes) CREATE_CUDA(cudaMemset(*pl, 0, P * sizeof(float)));
 

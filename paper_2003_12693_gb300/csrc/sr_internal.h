@@ -162,11 +162,6 @@ struct PrepArgs {
   // stores it there (D_load false) and the later ones read it (D_load true)
   float* D;
   bool D_load;
-  // with D: the tiles with narrow-band pixels, listed by the bulk pass for
-  // the band pass (band_list[n_tiles], band_count[2]: count, finished CTAs;
-  // zero between steps); null: one kernel does both
-  int* band_list;
-  int* band_count;
 };
 
 // w and b update with the repulsion window sum fused in; b is carried as
@@ -230,8 +225,6 @@ cudaError_t launch_colsolve(const ColArgs& a, cudaStream_t s);
 cudaError_t launch_rowinv(const RowInvArgs& a, int mode, int nthreads, cudaStream_t s);
 cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s);
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
-// whether launch_prep runs the bulk / band pair (two launches) for these args
-bool prep_split(const PrepArgs& a);
 int tile32_blocks(const Geo& geo);  // CTAs of the 32 x 32 tile kernels
 // Row-pass shape of the fixed power-of-two passes (k_rowfwd, k_rowinv) for an
 // H-row image with row transforms of complex length L on a device with nsm

@@ -663,12 +663,10 @@ struct Quad {
   int i, j, iu, id, jl, jr;
   bool live, up_g, dn_g, lf_g, rt_g;
   size_t o;
-  __device__ __forceinline__ Quad(const Geo& geo) : Quad(geo, blockIdx.x, blockIdx.y) {}
-  // the tile (bx, by) of the 32 x 32 grid
-  __device__ __forceinline__ Quad(const Geo& geo, int bx, int by) {
+  __device__ __forceinline__ Quad(const Geo& geo) {
     const int tx = threadIdx.x, ty = threadIdx.y;
-    i = by * kT + ty;
-    j = bx * kT + 4 * tx;
+    i = blockIdx.y * kT + ty;
+    j = blockIdx.x * kT + 4 * tx;
     live = i < geo.M && j < geo.N;
     iu = i > 0 ? i - 1 : geo.M - 1;
     id = i < geo.M - 1 ? i + 1 : 0;
@@ -797,152 +795,6 @@ __global__ void __launch_bounds__(kTN, 4) k_prep(const PrepArgs a) {
   }
   if (!q.live) return;
   st4(a.G + q.o, make_float4(out[0], out[1], out[2], out[3]));
-}
-
-// k_prep split in two for the inner steps that store or load div e.
-// k_prep_bulk covers every tile with few registers (no window sum), so more
-// CTAs share an SM and more loads are in flight; a tile with narrow-band
-// pixels only stores div e (DIV = kDivStore) and appends itself to a list.
-// k_prep_band then takes the listed tiles (persistent CTAs), with div e from
-// D, and does what k_prep does on a band tile.  Per pixel both evaluate
-// k_prep's expressions, so G is the same bit for bit.  The last band CTA to
-// finish resets the list for the next step.
-template <int DIV>
-__global__ void __launch_bounds__(kTN, 6) k_prep_bulk(const PrepArgs a) {
-  pdl_wait();
-  pdl_trigger();
-  const Model& m = a.mod;
-  const int N = a.geo.N;
-  const Quad q(a.geo);
-  const float* psi = a.psi;
-  const float4 X = ld4_if(q.live, psi + q.o);
-  float4 E1 = make_float4(0.f, 0.f, 0.f, 0.f), E2 = E1, E1u = E1, Dv = E1;
-  float e2l = 0.f;
-  if (DIV == kDivLoad) {
-    Dv = ld4_if(q.live, a.D + q.o);
-  } else {
-    E1 = ld4_if(q.live, a.e1 + q.o);
-    E2 = ld4_if(q.live, a.e2 + q.o);
-    E1u = ld4_if(q.live && q.up_g, a.e1 + (size_t)q.iu * N + q.j);
-    e2l = ld_if(q.live && q.lf_g, a.e2 + (size_t)q.i * N + q.jl);
-  }
-  float4 UP = ld4_if(q.live && q.up_g, psi + (size_t)q.iu * N + q.j);
-  float4 DN = ld4_if(q.live && q.dn_g, psi + (size_t)q.id * N + q.j);
-  float LF = ld_if(q.live && q.lf_g, psi + (size_t)q.i * N + q.jl);
-  float RT = ld_if(q.live && q.rt_g, psi + (size_t)q.i * N + q.jr);
-  const bool band = __syncthreads_or(q.live && any_band4(X, m)) != 0;
-  {
-    const float4 su = shfl_up4(X, kTBX), sd = shfl_down4(X, kTBX);
-    const float sl = __shfl_up_sync(0xffffffffu, X.w, 1);
-    const float sr = __shfl_down_sync(0xffffffffu, X.x, 1);
-    if (!q.up_g) UP = su;
-    if (!q.dn_g) DN = sd;
-    if (!q.lf_g) LF = sl;
-    if (!q.rt_g) RT = sr;
-    if (DIV != kDivLoad) {
-      const float4 se = shfl_up4(E1, kTBX);
-      const float sel = __shfl_up_sync(0xffffffffu, E2.w, 1);
-      if (!q.up_g) E1u = se;
-      if (!q.lf_g) e2l = sel;
-      if (a.geo.neumann) {
-        if (q.i == 0) E1u = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (q.i == a.geo.M - 1) E1 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (q.j == 0) e2l = 0.f;
-        if (q.j + 4 == N) E2.w = 0.f;
-      }
-      Dv = make_float4(div_e(E1.x, E1u.x, E2.x, e2l), div_e(E1.y, E1u.y, E2.y, E2.x),
-                       div_e(E1.z, E1u.z, E2.z, E2.y), div_e(E1.w, E1u.w, E2.w, E2.z));
-      if (q.live) st4(a.D + q.o, Dv);
-    }
-  }
-  if (band) {
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-      a.band_list[atomicAdd(a.band_count, 1)] = blockIdx.y * gridDim.x + blockIdx.x;
-    return;
-  }
-  if (a.geo.neumann) {
-    if (q.i == 0) UP = X;
-    if (q.i == a.geo.M - 1) DN = X;
-    if (q.j == 0) LF = X.x;
-    if (q.j + 4 == N) RT = X.w;
-  }
-  if (!q.live) return;
-  const float x[4] = {X.x, X.y, X.z, X.w};
-  const float up[4] = {UP.x, UP.y, UP.z, UP.w}, dn[4] = {DN.x, DN.y, DN.z, DN.w};
-  const float lf[4] = {LF, X.x, X.y, X.z}, rt[4] = {X.y, X.z, X.w, RT};
-  const float dv[4] = {Dv.x, Dv.y, Dv.z, Dv.w};
-  float out[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) out[t] = m.tau * rhs_bulk(m, x[t], up[t], dn[t], lf[t], rt[t], dv[t]);
-  st4(a.G + q.o, make_float4(out[0], out[1], out[2], out[3]));
-}
-
-template <int R>
-__global__ void __launch_bounds__(kTN, 4) k_prep_band(const PrepArgs a, int tiles_x) {
-  extern __shared__ __align__(16) float smem_f[];
-  pdl_wait();
-  pdl_trigger();
-  const Model& m = a.mod;
-  const int N = a.geo.N;
-  const int count = *reinterpret_cast<volatile int*>(a.band_count);
-  for (int e = blockIdx.x; e < count; e += gridDim.x) {
-    const int t = a.band_list[e];
-    const int bx = t % tiles_x, by = t / tiles_x;
-    const Quad q(a.geo, bx, by);
-    const float* psi = a.psi;
-    const float4 X = ld4_if(q.live, psi + q.o);
-    const float4 Dv = ld4_if(q.live, a.D + q.o);
-    float4 UP = ld4_if(q.live && q.up_g, psi + (size_t)q.iu * N + q.j);
-    float4 DN = ld4_if(q.live && q.dn_g, psi + (size_t)q.id * N + q.j);
-    float LF = ld_if(q.live && q.lf_g, psi + (size_t)q.i * N + q.jl);
-    float RT = ld_if(q.live && q.rt_g, psi + (size_t)q.i * N + q.jr);
-    const float4 W1 = ld4_if(q.live, a.w1 + q.o), W2 = ld4_if(q.live, a.w2 + q.o);
-    const float4 G4 = ld4_if(q.live, a.g + q.o);
-    {
-      const float4 su = shfl_up4(X, kTBX), sd = shfl_down4(X, kTBX);
-      const float sl = __shfl_up_sync(0xffffffffu, X.w, 1);
-      const float sr = __shfl_down_sync(0xffffffffu, X.x, 1);
-      if (!q.up_g) UP = su;
-      if (!q.dn_g) DN = sd;
-      if (!q.lf_g) LF = sl;
-      if (!q.rt_g) RT = sr;
-    }
-    if (a.geo.neumann) {
-      if (q.i == 0) UP = X;
-      if (q.i == a.geo.M - 1) DN = X;
-      if (q.j == 0) LF = X.x;
-      if (q.j + 4 == N) RT = X.w;
-    }
-    float f[4];
-    {
-      const float x[4] = {X.x, X.y, X.z, X.w};
-      const float up[4] = {UP.x, UP.y, UP.z, UP.w}, dn[4] = {DN.x, DN.y, DN.z, DN.w};
-      const float lf[4] = {LF, X.x, X.y, X.z}, rt[4] = {X.y, X.z, X.w, RT};
-      const float dv[4] = {Dv.x, Dv.y, Dv.z, Dv.w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) f[k] = rhs_bulk(m, x[k], up[k], dn[k], lf[k], rt[k], dv[k]);
-    }
-    float v1[4], v2[4];
-    band_window<R>(smem_f, a.geo, m, psi, a.w1, a.w2, by * kT, bx * kT, v1, v2);
-    const float x[4] = {X.x, X.y, X.z, X.w};
-    const float w1[4] = {W1.x, W1.y, W1.z, W1.w}, w2[4] = {W2.x, W2.y, W2.z, W2.w};
-    const float gg[4] = {G4.x, G4.y, G4.z, G4.w};
-    float out[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) out[k] = rhs_band(m, f[k], x[k], w1[k], w2[k], gg[k], v1[k], v2[k]);
-    if (q.live) st4(a.G + q.o, make_float4(out[0], out[1], out[2], out[3]));
-    __syncthreads();  // the staging area is filled again for the next tile
-  }
-  // the last CTA to finish empties the list for the next inner step
-  __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    __threadfence();
-    if (atomicAdd(a.band_count + 1, 1) == (int)gridDim.x - 1) {
-      a.band_count[0] = 0;
-      a.band_count[1] = 0;
-      __threadfence();
-    }
-  }
 }
 
 // w and b update (Eqs. (41), (42), (40), (23)) with the window sum fused in.
@@ -1234,8 +1086,7 @@ cudaError_t configure_kernels() {
   if ((e = allow_big_smem(k_prep<r, kDivCompute>)) != cudaSuccess) return e; \
   if ((e = allow_big_smem(k_prep<r, kDivStore>)) != cudaSuccess) return e;   \
   if ((e = allow_big_smem(k_prep<r, kDivLoad>)) != cudaSuccess) return e;    \
-  if ((e = allow_big_smem(k_wb_update<r>)) != cudaSuccess) return e;          \
-  if ((e = allow_big_smem(k_prep_band<r>)) != cudaSuccess) return e;
+  if ((e = allow_big_smem(k_wb_update<r>)) != cudaSuccess) return e;
   SR_FOR_R(SR_CASE)
 #undef SR_CASE
   return cudaSuccess;
@@ -1334,41 +1185,9 @@ cudaError_t launch_wb_update(const WBArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// SR_PREP_SPLIT=0 keeps the single k_prep for every inner step
-static bool prep_split_enabled() {
-  static int on = -1;
-  if (on < 0) {
-    const char* env = std::getenv("SR_PREP_SPLIT");
-    on = (env && env[0] == '0') ? 0 : 1;
-  }
-  return on != 0;
-}
-
-bool prep_split(const PrepArgs& a) { return a.D != nullptr && a.band_list && prep_split_enabled(); }
-
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
   const dim3 g = tile32_grid(a.geo), b(kTBX, kTBY);
   const size_t sm = tile32_smem(a.mod.R);
-  if (prep_split(a)) {
-    cudaError_t e = a.D_load ? launch_k(k_prep_bulk<kDivLoad>, g, b, 0, s, a)
-                             : launch_k(k_prep_bulk<kDivStore>, g, b, 0, s, a);
-    if (e != cudaSuccess) return e;
-    static int nsm = 0;
-    if (!nsm) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    }
-    const int ntiles = (int)(g.x * g.y);
-    const dim3 gb(std::max(1, std::min(ntiles, 4 * nsm)));
-    switch (a.mod.R) {
-#define SR_CASE(r) \
-  case r: return launch_k(k_prep_band<r>, gb, b, sm, s, a, (int)g.x);
-      SR_FOR_R(SR_CASE)
-#undef SR_CASE
-      default: return cudaErrorInvalidValue;
-    }
-  }
   switch (a.mod.R) {
 #define SR_CASE(r) \
   case r:                                                                    \
