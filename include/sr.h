@@ -79,9 +79,11 @@ sr_status sr_params_default(sr_params* p);
  * W/2 have no prime factor above 31 (SR_EUNSUPPORTED otherwise).  Powers of
  * two use register-resident FFT passes with an autotuned schedule, other
  * sides (e.g. 96, 160, 224) mixed-radix shared-memory row passes with radices
- * 16, 8, 4, 2, 3, 5 and direct DFTs of the other primes, and the column solve
- * by the recursions of column schedule 7 (the environment variable
- * SR_GEN_FFT_COLS=1 at sr_create selects a mixed-radix column FFT instead).
+ * 16, 8, 4, 2, 3, 5 and direct DFTs of the other primes, and for the column
+ * solve the faster, timed at sr_create (once per size and tau mu in the
+ * process), of the recursions of column schedule 7 and a mixed-radix column
+ * FFT with the symbol's division (the environment variable SR_GEN_FFT_COLS =
+ * 1 or 0 at sr_create fixes the column FFT or the recursions).
  * cuda_stream is a cudaStream_t (may be 0). */
 sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx** out);
 

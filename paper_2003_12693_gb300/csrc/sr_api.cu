@@ -43,7 +43,7 @@ struct sr_ctx {
   bool fftgen = false;  // mixed-radix passes (sr_fftgen.cu): a side is not a power of two
   srk::GenPlan plan_row{}, plan_col{};
   bool gen_batched = false;  // member of a group: launch shapes for many images at once
-  bool gen_fft_cols = false; // mixed-radix sides: column FFT instead of the recursions (SR_GEN_FFT_COLS=1)
+  bool gen_fft_cols = false; // mixed-radix sides: column FFT instead of the recursions (timed, or SR_GEN_FFT_COLS)
   float2* gen_tab = nullptr;  // stage twiddles and roots of both plans
   sr_schedule sched{};  // schedule of the fft2 passes
   CUtensorMap tm_X{};   // X as a float32 matrix, boxes for the TMA column pass
@@ -606,6 +606,71 @@ sr_status autotune(sr_ctx* c) {
   SR_CUDA(c, sched_configure(c, best));
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   g_tuned[{c->H, c->W, c->rec_R}] = {c->device, best};
+  return SR_OK;
+}
+
+// Sides that are not powers of two: time the two column passes the
+// mixed-radix path can use (the recursions of column schedule 7, or the
+// mixed-radix column FFT with the symbol of Eq. (32)) and keep the faster,
+// once per size, warm-up length and device in the process.
+// SR_GEN_FFT_COLS=1 (FFT) or 0 (recursions) fixes the choice.
+std::map<std::tuple<int, int, int>, std::pair<int, bool>> g_tuned_gen;
+
+sr_status autotune_gen(sr_ctx* c) {
+  if (const char* env = std::getenv("SR_GEN_FFT_COLS")) {
+    c->gen_fft_cols = env[0] == '1' || c->rec_R <= 0;
+    return SR_OK;
+  }
+  if (c->rec_R <= 0) {
+    c->gen_fft_cols = true;
+    return SR_OK;
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned_gen.find({c->H, c->W, c->rec_R});
+    if (it != g_tuned_gen.end() && it->second.first == c->device) {
+      c->gen_fft_cols = it->second.second;
+      return SR_OK;
+    }
+  }
+  SR_CUDA(c, cudaMemset(c->X, 0, (size_t)c->H * c->L * sizeof(float2)));
+  srk::ColArgs ca{};
+  ca.geo = c->geo;
+  ca.fft = c->fft_col;
+  ca.aM = c->aM;
+  ca.aN = c->aN;
+  ca.X = c->X;
+  ca.err = c->err_dev;
+  ca.rec = c->rec;
+  ca.rec_R = c->rec_R;
+  ca.Xout = c->X2;
+  cudaStream_t s = c->cap_stream;
+  cudaEvent_t e0, e1;
+  SR_CUDA(c, cudaEventCreate(&e0));
+  SR_CUDA(c, cudaEventCreate(&e1));
+  float best[2] = {1e30f, 1e30f};  // [0] recursions, [1] column FFT
+  cudaError_t err = cudaSuccess;
+  for (int round = 0; round < 2 && err == cudaSuccess; ++round)
+    for (int fftc = 0; fftc < 2 && err == cudaSuccess; ++fftc) {
+      auto launch = [&] {
+        return fftc ? srk::launch_colsolve_gen(ca, c->plan_col, false, s)
+                    : srk::launch_colsolve_rec(ca, s);
+      };
+      if ((err = launch()) != cudaSuccess) break;
+      if ((err = cudaEventRecord(e0, s)) != cudaSuccess) break;
+      for (int r = 0; r < 10 && err == cudaSuccess; ++r) err = launch();
+      if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err == cudaSuccess) best[fftc] = std::min(best[fftc], ms);
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(c, err, "mixed-radix column pass autotuner");
+  c->gen_fft_cols = best[1] < best[0];
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tuned_gen[{c->H, c->W, c->rec_R}] = {c->device, c->gen_fft_cols};
   return SR_OK;
 }
 
@@ -1238,8 +1303,7 @@ sr_status sr_create(int H, int W, const sr_params* p, void* cuda_stream, sr_ctx*
     c->plan_col.tw = c->plan_col.roots = c->gen_tab;
     CREATE_CUDA(srk::configure_fftgen());
     c->fftgen = true;
-    const char* env = std::getenv("SR_GEN_FFT_COLS");
-    c->gen_fft_cols = env && env[0] == '1';
+    if (autotune_gen(c) != SR_OK) return bail(SR_ECUDA);
   }
   if (c->fft2) {
     const int cb = srk::colsolve_tma_cb(H);
