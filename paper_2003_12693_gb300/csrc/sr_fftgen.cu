@@ -12,8 +12,6 @@
 // writes y[(j / Ns) Ns R + k + t Ns].  Radices 2, 4, 8, 16, 3 and 5 have
 // dedicated butterflies; any other prime up to kGenMaxRadix goes through a
 // direct length-R DFT with a table of its roots.
-#include <cstdlib>
-
 #include "sr_internal.h"
 
 namespace srk {
@@ -146,47 +144,10 @@ __device__ __forceinline__ void stage_r(const float2* a, float2* b, int nseq, in
                                         const float2* root, bool inv) {
   const int m = n / R;
   if constexpr (!dedicated<R>()) {
-    // a prime without a dedicated butterfly.  With fewer butterflies than
-    // threads: one output y_q per thread (the R outputs of a butterfly on R
-    // threads), so that the O(R) sums run side by side instead of R after
-    // another on one thread, two partial sums halving each sum's chain; with
-    // enough butterflies, one butterfly per thread (its inputs twiddled once)
-    if (nseq * m >= (int)blockDim.x) {
-      for (int idx = threadIdx.x; idx < nseq * m; idx += blockDim.x) {
-        const int q = divm(idx, mag_m), j = idx - q * m;
-        const int jn = divm(j, mag_ns), k = j - jn * Ns;
-        const float2* in = a + (size_t)q * n;
-        float2* out = b + (size_t)q * n;
-        float2 v[R];
-#pragma unroll
-        for (int t = 0; t < R; ++t) v[t] = in[j + t * m];
-        if (Ns > 1) {
-#pragma unroll
-          for (int t = 1; t < R; ++t) {
-            float2 w = __ldg(tw + (t - 1) * Ns + k);
-            if (inv) w.y = -w.y;
-            v[t] = cmul(v[t], w);
-          }
-        }
-        const int o = jn * Ns * R + k;
-#pragma unroll 1
-        for (int y = 0; y < R; ++y) {
-          float2 acc = v[0];
-          int e = 0;  // (t y) mod R
-#pragma unroll
-          for (int t = 1; t < R; ++t) {
-            e += y;
-            if (e >= R) e -= R;
-            float2 w = __ldg(root + e);
-            if (inv) w.y = -w.y;
-            acc.x += v[t].x * w.x - v[t].y * w.y;
-            acc.y += v[t].x * w.y + v[t].y * w.x;
-          }
-          out[o + y * Ns] = acc;
-        }
-      }
-      return;
-    }
+    // a prime without a dedicated butterfly: one output y_q per thread (the
+    // R outputs of a butterfly on R threads), so that the O(R) sums run side
+    // by side instead of R after another on one thread; two partial sums
+    // halve each sum's dependent chain
     for (int idx = threadIdx.x; idx < nseq * m * R; idx += blockDim.x) {
       const int bf = idx / R, y = idx - bf * R;
       const int q = divm(bf, mag_m), j = bf - q * m;
@@ -397,13 +358,7 @@ using fftgen::kGenThreads;
 // batched group the other images fill the GPU, so the CTAs are filled up.
 int gen_rows_per_cta(int n, int count, bool batched) {
   const int fit = n >= kGenSmemFloat2 / 2 ? 1 : kGenSmemFloat2 / 2 / n;
-  static int occ = -1;
-  if (occ < 0) {
-    const char* env = std::getenv("SR_GEN_ROWS");
-    occ = env && env[0] == 'o' ? 1 : 0;
-  }
-  // "occupancy": two buffers of at most about 28 KB, so that eight CTAs share an SM
-  int t = occ ? (28 * 1024) / (2 * n * (int)sizeof(float2)) : (batched ? 16 : count / 256);
+  int t = batched ? 16 : count / 256;
   if (t < 1) t = 1;
   if (t > 16) t = 16;
   return t < fit ? t : fit;
