@@ -131,7 +131,7 @@ __device__ __forceinline__ void dft_fixed(float2 (&x)[R], bool inv) {
 // One Stockham stage of radix R over nseq sequences of length n (a -> b).
 // Primes without a dedicated butterfly take the direct DFT y_q = sum_t x_t
 // root[(t q) mod R], root[e] = exp(-2 pi i e / R) (conjugated when inv),
-// one y_q per thread.
+// each y_q written as soon as it is summed.
 // x / d for x < 2^20 from magic = ceil(2^32 / d) (host-computed): exact, since
 // x (magic d - 2^32) < 2^32 there.  d = 1 is passed as magic 0.
 __device__ __forceinline__ int divm(int x, unsigned magic) {
@@ -143,37 +143,6 @@ __device__ __forceinline__ void stage_r(const float2* a, float2* b, int nseq, in
                                         unsigned mag_m, unsigned mag_ns, const float2* tw,
                                         const float2* root, bool inv) {
   const int m = n / R;
-  if constexpr (!dedicated<R>()) {
-    // a prime without a dedicated butterfly: one output y_q per thread (the
-    // R outputs of a butterfly on R threads), so that the O(R) sums run side
-    // by side instead of R after another on one thread; two partial sums
-    // halve each sum's dependent chain
-    for (int idx = threadIdx.x; idx < nseq * m * R; idx += blockDim.x) {
-      const int bf = idx / R, y = idx - bf * R;
-      const int q = divm(bf, mag_m), j = bf - q * m;
-      const int jn = divm(j, mag_ns), k = j - jn * Ns;
-      const float2* in = a + (size_t)q * n;
-      float2 acc0 = in[j], acc1 = make_float2(0.f, 0.f);
-      int e = 0;  // (t y) mod R
-#pragma unroll
-      for (int t = 1; t < R; ++t) {
-        float2 v = in[j + t * m];
-        if (Ns > 1) {
-          float2 w = __ldg(tw + (t - 1) * Ns + k);
-          if (inv) w.y = -w.y;
-          v = cmul(v, w);
-        }
-        e += y;
-        if (e >= R) e -= R;
-        float2 r = __ldg(root + e);
-        if (inv) r.y = -r.y;
-        float2& acc = (t & 1) ? acc1 : acc0;
-        acc.x += v.x * r.x - v.y * r.y;
-        acc.y += v.x * r.y + v.y * r.x;
-      }
-      b[(size_t)q * n + jn * Ns * R + k + y * Ns] = cadd(acc0, acc1);
-    }
-  } else {
   for (int idx = threadIdx.x; idx < nseq * m; idx += blockDim.x) {
     const int q = divm(idx, mag_m), j = idx - q * m;
     const int jn = divm(j, mag_ns), k = j - jn * Ns;
@@ -191,10 +160,27 @@ __device__ __forceinline__ void stage_r(const float2* a, float2* b, int nseq, in
       }
     }
     const int o = jn * Ns * R + k;
-    dft_fixed<R>(v, inv);
+    if constexpr (dedicated<R>()) {
+      dft_fixed<R>(v, inv);
 #pragma unroll
-    for (int t = 0; t < R; ++t) out[o + t * Ns] = v[t];
-  }
+      for (int t = 0; t < R; ++t) out[o + t * Ns] = v[t];
+    } else {
+#pragma unroll 1
+      for (int y = 0; y < R; ++y) {
+        float2 acc = v[0];
+        int e = 0;  // (t y) mod R
+#pragma unroll
+        for (int t = 1; t < R; ++t) {
+          e += y;
+          if (e >= R) e -= R;
+          float2 w = __ldg(root + e);
+          if (inv) w.y = -w.y;
+          acc.x += v[t].x * w.x - v[t].y * w.y;
+          acc.y += v[t].x * w.y + v[t].y * w.x;
+        }
+        out[o + y * Ns] = acc;
+      }
+    }
   }
 }
 
