@@ -24,8 +24,9 @@
 // CTAs' shared memory through the cluster's distributed shared memory.  Global
 // memory is read once at the start and written once at the end, so a launch
 // costs one load and one store of the state plus the on-chip iterations
-// instead of 2S + 1 dependent kernel launches (3S + 1 for the three-pass
-// solve) per iteration with every plane crossing L2.
+// instead of 4S + 1 dependent kernel launches per iteration (right-hand side,
+// row pass, column pass and inverse row pass per inner step, then the w/b
+// update) with every plane crossing L2.
 //
 // All control flow that contains a cluster barrier is uniform over the
 // cluster: the loop bounds are launch arguments and the stopping decision is
