@@ -48,7 +48,7 @@ using namespace srk::cdft;
 // floats from the dynamic shared-memory base, each 16-byte aligned).
 struct Lay {
   int RPC, PL, SW;  // rows per CTA, floats per plane, staged window row width N + 2R
-  int psi, phik, w1[2], w2[2], e1, e2, g, D, G, X, X2, H, scr, part;
+  int psi, phik, w1[2], w2[2], e1, e2, g, D, G, X, X2, scr, part;
   int total;
 };
 
@@ -77,17 +77,15 @@ __host__ __device__ inline Lay make_lay(int M, int N, int R, int rec_R, int C) {
   l.G = lay_take(o, l.PL);
   l.X = lay_take(o, l.PL);   // RPC x L complex = PL floats
   l.X2 = lay_take(o, l.PL);
-  // the rec_R spectrum rows before and after the CTA's rows, written by the
-  // CTAs that own them (the column solve's warm-ups)
-  l.H = lay_take(o, 2 * rec_R * N);
   // scratch, one use per phase: the window's sums v1, v2, staged u planes
   // and vertical sums; the row transforms' exchange rows (+1 row for idle
-  // thread slots); the column solve's forward values of the run and the
-  // warm-up after it
+  // thread slots);
+  // the column solve's copy of the rec_R spectrum rows before and after the
+  // CTA's rows, then the forward values of the run and the warm-up after it
   const int L = N / 2, RS = L + L / 16;
   const int win = 2 * (l.RPC + 2 * R) * l.SW + 2 * l.RPC * l.SW + 2 * l.PL;
   const int fft = 2 * (l.RPC + 1) * RS;
-  const int colu = 2 * (l.RPC + rec_R) * L;
+  const int colu = 2 * rec_R * N + 2 * (l.RPC + rec_R) * L;
   int sc = win > fft ? win : fft;
   sc = sc > colu ? sc : colu;
   l.scr = lay_take(o, sc);
@@ -259,14 +257,6 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
     for (int q = tid; q < PL; q += T) any |= in_band(x[q], m);
     return __syncthreads_or(any) != 0;
   };
-  // whether the CTA's psi has narrow-band pixels: from the load, then from
-  // each inverse row pass's update (its threads own every row), read after
-  // the cluster barrier that follows it; two flags alternate, the one not in
-  // use is cleared after that barrier
-  __shared__ int bflag[2];
-  if (tid < 2) bflag[tid] = 0;
-  int bpar = 0;
-  bool band_psi = any_band(sm + ly.psi);
 
   // the row transforms: thread slot t = tid / TP takes row t, whose TP
   // threads are lanes of one warp, so the stages' exchanges synchronise the
@@ -294,7 +284,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
     for (int s = 0; s < mb.inner_S; ++s) {
       // ---- right-hand side of the inner step, Eq. (37) in increment form
       {
-        const bool band = band_psi;
+        const bool band = any_band(psi);
         if (band) window(ly.psi, ly.w1[wc], ly.w2[wc]);
         const float* v1 = sm + ly.scr;
         const float* v2 = v1 + PL;
@@ -369,29 +359,6 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
           }
         }
       }
-      // ---- the CTA's spectrum rows into the warm-up copies of the CTAs whose
-      // column recursions start or end in them: row gi is row h of CTA d's
-      // rows before (h = gi - (r0_d - rec_R) mod M) and row h of its rows
-      // after (h = gi - (r0_d + RPC) mod M) when h < rec_R (again every M
-      // rows when M < rec_R)
-      __syncthreads();
-      {
-        const int Rr = mb.rec_R;
-        for (int pi = warp; pi < RPC * C; pi += NW) {
-          const int li = pi / C, d = pi - li * C;
-          const int gi = r0 + li, r0d = d * RPC;
-          const float4* src = reinterpret_cast<const float4*>(sm + ly.X + li * N);
-          for (int side = 0; side < 2; ++side) {
-            int h = side ? gi - r0d - RPC : gi - r0d + Rr;
-            h %= M;
-            if (h < 0) h += M;
-            for (; h < Rr; h += M) {
-              float4* dst = reinterpret_cast<float4*>(rbase[d] + ly.H + (side * Rr + h) * N);
-              for (int c4 = lane; c4 < N / 4; c4 += 32) dst[c4] = src[c4];
-            }
-          }
-        }
-      }
       cl.sync();
       // ---- column solve: forward and backward recursions per column and
       // real/imaginary part (task = 2 k + part, lane-contiguous) over the
@@ -401,10 +368,24 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
       // only this CTA's shared memory.
       {
         const int Rr = mb.rec_R;
-        const float* Hx = sm + ly.H;      // [2 Rr][N]: the rows before, then after
-        float* U = sm + ly.scr;           // [(RPC + Rr)][2L]
+        float* Hx = sm + ly.scr;          // [2 Rr][N]: the rows before, then after
+        float* U = Hx + 2 * Rr * N;       // [(RPC + Rr)][2L]
         float* X2 = sm + ly.X2;
         const float* Xo = sm + ly.X;
+        for (int hr = warp; hr < 2 * Rr; hr += NW) {
+          int gi = hr < Rr ? r0 - Rr + hr : r0 + RPC + (hr - Rr);
+          gi %= M;
+          if (gi < 0) gi += M;
+          const float4* srow = reinterpret_cast<const float4*>(row_at(ly.X, gi));
+          float4 t[(N / 4 + 31) / 32];
+#pragma unroll
+          for (int c = 0; c < (N / 4 + 31) / 32; ++c)
+            if (lane + 32 * c < N / 4) t[c] = srow[lane + 32 * c];
+#pragma unroll
+          for (int c = 0; c < (N / 4 + 31) / 32; ++c)
+            if (lane + 32 * c < N / 4) reinterpret_cast<float4*>(Hx + hr * N)[lane + 32 * c] = t[c];
+        }
+        __syncthreads();
         for (int task = tid; task < 2 * L; task += T) {
           const float4 p = __ldg(mb.rec + (task >> 1));
           const float r = (task & 1) ? p.z : p.x, sc = (task & 1) ? p.w : p.y;
@@ -452,25 +433,18 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
         stages<LOGL, LOGE, 0, true, 1, false, true, true>(x, fbase, fu, mb.tws4);
         if (flive) {
           float2* prow = reinterpret_cast<float2*>(psi + ft * N);
-          int nb = 0;
 #pragma unroll
           for (int q = 0; q < E; ++q) {
             const float2 pv = prow[fu + (q << LOGTP)];
-            const float2 nv = make_float2(pv.x + x[q].x, pv.y + x[q].y);
-            prow[fu + (q << LOGTP)] = nv;
-            nb |= in_band(nv.x, m) | in_band(nv.y, m);
+            prow[fu + (q << LOGTP)] = make_float2(pv.x + x[q].x, pv.y + x[q].y);
           }
-          if (nb) bflag[bpar] = 1;
         }
       }
       cl.sync();
-      band_psi = bflag[bpar] != 0;
-      if (tid == 0) bflag[bpar ^ 1] = 0;
-      bpar ^= 1;
     }
     // ---- w and b update, Eqs. (41), (42), (40), (23), into the other w parity
     {
-      const bool band = band_psi;
+      const bool band = any_band(psi);
       if (band) window(ly.psi, ly.w1[wc], ly.w2[wc]);
       const float* v1 = sm + ly.scr;
       const float* v2 = v1 + PL;
