@@ -257,6 +257,14 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
     for (int q = tid; q < PL; q += T) any |= in_band(x[q], m);
     return __syncthreads_or(any) != 0;
   };
+  // whether the CTA's psi has narrow-band pixels: from the load, then from
+  // each inverse row pass's update (its threads own every row), read after
+  // the cluster barrier that follows it; two flags alternate, the one not in
+  // use is cleared after that barrier
+  __shared__ int bflag[2];
+  if (tid < 2) bflag[tid] = 0;
+  int bpar = 0;
+  bool band_psi = any_band(sm + ly.psi);
 
   // the row transforms: thread slot t = tid / TP takes row t, whose TP
   // threads are lanes of one warp, so the stages' exchanges synchronise the
@@ -284,7 +292,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
     for (int s = 0; s < mb.inner_S; ++s) {
       // ---- right-hand side of the inner step, Eq. (37) in increment form
       {
-        const bool band = any_band(psi);
+        const bool band = band_psi;
         if (band) window(ly.psi, ly.w1[wc], ly.w2[wc]);
         const float* v1 = sm + ly.scr;
         const float* v2 = v1 + PL;
@@ -433,18 +441,25 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
         stages<LOGL, LOGE, 0, true, 1, false, true, true>(x, fbase, fu, mb.tws4);
         if (flive) {
           float2* prow = reinterpret_cast<float2*>(psi + ft * N);
+          int nb = 0;
 #pragma unroll
           for (int q = 0; q < E; ++q) {
             const float2 pv = prow[fu + (q << LOGTP)];
-            prow[fu + (q << LOGTP)] = make_float2(pv.x + x[q].x, pv.y + x[q].y);
+            const float2 nv = make_float2(pv.x + x[q].x, pv.y + x[q].y);
+            prow[fu + (q << LOGTP)] = nv;
+            nb |= in_band(nv.x, m) | in_band(nv.y, m);
           }
+          if (nb) bflag[bpar] = 1;
         }
       }
       cl.sync();
+      band_psi = bflag[bpar] != 0;
+      if (tid == 0) bflag[bpar ^ 1] = 0;
+      bpar ^= 1;
     }
     // ---- w and b update, Eqs. (41), (42), (40), (23), into the other w parity
     {
-      const bool band = any_band(psi);
+      const bool band = band_psi;
       if (band) window(ly.psi, ly.w1[wc], ly.w2[wc]);
       const float* v1 = sm + ly.scr;
       const float* v2 = v1 + PL;
