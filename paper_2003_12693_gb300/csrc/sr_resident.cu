@@ -380,18 +380,34 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
         float* U = Hx + 2 * Rr * N;       // [(RPC + Rr)][2L]
         float* X2 = sm + ly.X2;
         const float* Xo = sm + ly.X;
-        for (int hr = warp; hr < 2 * Rr; hr += NW) {
-          int gi = hr < Rr ? r0 - Rr + hr : r0 + RPC + (hr - Rr);
-          gi %= M;
-          if (gi < 0) gi += M;
-          const float4* srow = reinterpret_cast<const float4*>(row_at(ly.X, gi));
-          float4 t[(N / 4 + 31) / 32];
+        // all of a thread's remote loads are issued before its stores, in
+        // batches of HB rows, so that their latencies overlap
+        constexpr int NC4 = (N / 4 + 31) / 32, HB = 4;
+        for (int hr0 = warp; hr0 < 2 * Rr; hr0 += HB * NW) {
+          float4 t[HB][NC4];
 #pragma unroll
-          for (int c = 0; c < (N / 4 + 31) / 32; ++c)
-            if (lane + 32 * c < N / 4) t[c] = srow[lane + 32 * c];
+          for (int b = 0; b < HB; ++b) {
+            const int hr = hr0 + b * NW;
+            if (hr < 2 * Rr) {
+              int gi = hr < Rr ? r0 - Rr + hr : r0 + RPC + (hr - Rr);
+              gi %= M;
+              if (gi < 0) gi += M;
+              const float4* srow = reinterpret_cast<const float4*>(row_at(ly.X, gi));
 #pragma unroll
-          for (int c = 0; c < (N / 4 + 31) / 32; ++c)
-            if (lane + 32 * c < N / 4) reinterpret_cast<float4*>(Hx + hr * N)[lane + 32 * c] = t[c];
+              for (int c = 0; c < NC4; ++c)
+                if (lane + 32 * c < N / 4) t[b][c] = srow[lane + 32 * c];
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < HB; ++b) {
+            const int hr = hr0 + b * NW;
+            if (hr < 2 * Rr) {
+#pragma unroll
+              for (int c = 0; c < NC4; ++c)
+                if (lane + 32 * c < N / 4)
+                  reinterpret_cast<float4*>(Hx + hr * N)[lane + 32 * c] = t[b][c];
+            }
+          }
         }
         __syncthreads();
         for (int task = tid; task < 2 * L; task += T) {
