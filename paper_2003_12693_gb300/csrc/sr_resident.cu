@@ -48,7 +48,7 @@ using namespace srk::cdft;
 // floats from the dynamic shared-memory base, each 16-byte aligned).
 struct Lay {
   int RPC, PL, SW;  // rows per CTA, floats per plane, staged window row width N + 2R
-  int psi, phik, w1[2], w2[2], e1, e2, g, D, G, X, X2, scr, part;
+  int psi, phik, w1[2], w2[2], e1, e2, g, D, G, X, X2, hu1, hu2, scr, part;
   int total;
 };
 
@@ -77,6 +77,10 @@ __host__ __device__ inline Lay make_lay(int M, int N, int R, int rec_R, int C) {
   l.G = lay_take(o, l.PL);
   l.X = lay_take(o, l.PL);   // RPC x L complex = PL floats
   l.X2 = lay_take(o, l.PL);
+  // u = h(psi) w of the CTA's pixels (the window sum's operand), kept up to
+  // date where psi or w change, so the window's halo needs no band function
+  l.hu1 = lay_take(o, l.PL);
+  l.hu2 = lay_take(o, l.PL);
   // scratch, one use per phase: the window's sums v1, v2, staged u planes
   // and vertical sums; the row transforms' exchange rows (+1 row for idle
   // thread slots);
@@ -166,6 +170,13 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
       for (int q = tid; q < PL / 4; q += T) d4[q] = __ldg(s4 + q);
     }
   }
+  // u = h(psi) w at one of the CTA's pixels, with the current w (parity wcur)
+  auto set_u = [&](int q, float x, int wcur) {
+    const float h = in_band(x, m) ? band_h(x, m) : 0.f;
+    sm[ly.hu1 + q] = h * sm[ly.w1[wcur] + q];
+    sm[ly.hu2 + q] = h * sm[ly.w2[wcur] + q];
+  };
+  for (int q = tid; q < PL; q += T) set_u(q, sm[ly.psi + q], 0);
   cl.sync();
 
   // ---- separable window sum of u = h(x) w over the CTA's rows, Sec. 4:
@@ -173,7 +184,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
   // warp sums its own rows (row r by warp r mod NW, the rows the callers'
   // per-pixel loops give the same warp), down the columns, then along the row
   // it just summed, so only warp barriers follow.
-  auto window = [&](int off_x, int off_w1, int off_w2) {
+  auto window = [&]() {
     const int SW = ly.SW, SH = RPC + 2 * R;
     float* v1 = sm + ly.scr;
     float* v2 = v1 + PL;
@@ -184,26 +195,22 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
     for (int sr = warp; sr < SH; sr += NW) {
       const int gi = r0 - R + sr;
       const bool in = gi >= 0 && gi < M;
-      const float* px = in ? row_at(off_x, gi) : sm;
-      const float* p1 = in ? row_at(off_w1, gi) : sm;
-      const float* p2 = in ? row_at(off_w2, gi) : sm;
-      float xs[NJW], a1[NJW], a2[NJW];
-      bool ok[NJW];
+      const float* p1 = in ? row_at(ly.hu1, gi) : sm;
+      const float* p2 = in ? row_at(ly.hu2, gi) : sm;
+      float a1[NJW], a2[NJW];
 #pragma unroll
       for (int c = 0; c < NJW; ++c) {
         const int j = lane + 32 * c - R;
-        ok[c] = in && j >= 0 && j < N;
-        xs[c] = ok[c] ? px[j] : 0.f;
-        a1[c] = ok[c] ? p1[j] : 0.f;
-        a2[c] = ok[c] ? p2[j] : 0.f;
+        const bool ok = in && j >= 0 && j < N;
+        a1[c] = ok ? p1[j] : 0.f;
+        a2[c] = ok ? p2[j] : 0.f;
       }
 #pragma unroll
       for (int c = 0; c < NJW; ++c) {
         const int sc = lane + 32 * c;
         if (sc < SW) {
-          const float h = ok[c] && in_band(xs[c], m) ? band_h(xs[c], m) : 0.f;
-          u1[sr * SW + sc] = ok[c] ? h * a1[c] : 0.f;
-          u2[sr * SW + sc] = ok[c] ? h * a2[c] : 0.f;
+          u1[sr * SW + sc] = a1[c];
+          u2[sr * SW + sc] = a2[c];
         }
       }
     }
@@ -277,6 +284,10 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
   int wc = 0;    // local parity of the current w
   int done = 0;
   for (int k = 0; k < a.max_outer; ++k) {
+    if (k > 0) {  // u with the w of the update just made, seen by the whole cluster
+      for (int q = tid; q < PL; q += T) set_u(q, sm[ly.psi + q], wc);
+      cl.sync();
+    }
     const bool last = k == a.max_outer - 1;
     const bool check = a.tol > 0.0 ? ((k + 1) % a.check_every == 0 || last)
                                    : (last && a.check_last != 0);
@@ -293,7 +304,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
       // ---- right-hand side of the inner step, Eq. (37) in increment form
       {
         const bool band = band_psi;
-        if (band) window(ly.psi, ly.w1[wc], ly.w2[wc]);
+        if (band) window();
         const float* v1 = sm + ly.scr;
         const float* v2 = v1 + PL;
         float* G = sm + ly.G;
@@ -464,6 +475,9 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
             const float2 nv = make_float2(pv.x + x[q].x, pv.y + x[q].y);
             prow[fu + (q << LOGTP)] = nv;
             nb |= in_band(nv.x, m) | in_band(nv.y, m);
+            const int qq = ft * N + 2 * (fu + (q << LOGTP));
+            set_u(qq, nv.x, wc);
+            set_u(qq + 1, nv.y, wc);
           }
           if (nb) bflag[bpar] = 1;
         }
@@ -476,7 +490,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
     // ---- w and b update, Eqs. (41), (42), (40), (23), into the other w parity
     {
       const bool band = band_psi;
-      if (band) window(ly.psi, ly.w1[wc], ly.w2[wc]);
+      if (band) window();
       const float* v1 = sm + ly.scr;
       const float* v2 = v1 + PL;
       float* W1o = sm + ly.w1[wc ^ 1];
