@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const ResArgs a) {
     sm[ly.hu1 + q] = h * sm[ly.w1[wcur] + q];
     sm[ly.hu2 + q] = h * sm[ly.w2[wcur] + q];
   };
+  __syncthreads();  // the rows were loaded by other threads of the CTA
   for (int q = tid; q < PL; q += T) set_u(q, sm[ly.psi + q], 0);
   cl.sync();
 
