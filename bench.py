@@ -327,6 +327,47 @@ def batched_sample(stream, n_images: int = 256, iters: int = 100) -> dict:
                    f"about {P * 14 * 4 / 1e9:.1f} GB)"}
 
 
+def batched_small_sample(stream, n_images: int = 64, iters: int = 100) -> dict:
+    """Many small images (64 of the 128^2 two-disk workload) as one group:
+    through the group's graphs, and with every member resident (one cluster
+    launch for all of them).  CUDA events on the stream, no L2 flush."""
+    import numpy as np
+    import torch
+
+    from paper_2003_12693_gb300 import sr, synth
+
+    wl = synth.WORKLOADS["two_disks_128"]
+    f = torch.from_numpy(wl.image().astype(np.float32)).cuda()
+    phi0 = torch.from_numpy(wl.phi0().astype(np.float32)).cuda()
+    out = {"images": n_images, "size": f"{wl.H}x{wl.W}", "iterations": iters, "unit": UNIT}
+    for mode in ("graph", "resident"):
+        ctxs = []
+        for _ in range(n_images):
+            c = sr.Context(wl.H, wl.W, sr.make_params(win_radius=wl.R, d=wl.d), stream)
+            if mode == "resident":
+                c.set_resident(True)
+            c.edge_function(f)
+            c.set_phi(phi0)
+            ctxs.append(c)
+        grp = sr.Group(ctxs)
+        grp.tune()
+        grp.iterate(4)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        grp.iterate(iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[mode] = n_images * wl.H * wl.W * iters / (e0.elapsed_time(e1) / 1e3) / 1e6
+        grp.close()
+        for c in ctxs:
+            c.close()
+    out["how"] = ("sr_group_iterate: graph = one CUDA graph per parity with the members' "
+                  "iterations as child graphs on tuned lanes; resident = every member "
+                  "set resident, all in one launch of one cluster per image")
+    return out
+
+
 def resident_sample(stream, wl, iters: int = 100, reps: int = 5) -> dict | None:
     """Whole-run launches with the state resident in one cluster's shared
     memory (sr_set_resident) against the default path, both as a user runs
@@ -619,6 +660,12 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
     if rank != 0:
         return
     batched = None if args.no_batched else batched_sample(stream)
+    batched_small = None
+    if not args.no_batched and world == 1:
+        try:
+            batched_small = batched_small_sample(stream)
+        except Exception as e:  # a side sample: report, do not lose the line
+            batched_small = {"error": f"{type(e).__name__}: {e}"}
     resident_runs = resident_sample(stream, wl) if world == 1 else None
     wsnet = None if args.no_net else warm_start_net_sample(stream)
     cpu = None
@@ -643,6 +690,7 @@ def run_gpu(args, wl, rank: int, world: int, local_rank: int):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched": batched,
+        "batched_small": batched_small,
         "resident_runs": resident_runs,
         "warm_start_net": wsnet,
         "gpu_launches": launches,
