@@ -345,7 +345,7 @@ def batched_small_sample(stream, n_images: int = 64, iters: int = 100) -> dict:
         for _ in range(n_images):
             c = sr.Context(wl.H, wl.W, sr.make_params(win_radius=wl.R, d=wl.d), stream)
             if mode == "resident":
-                c.set_resident(True)
+                c.set_resident(True, cluster=8)  # more images at once than 16-CTA clusters
             c.edge_function(f)
             c.set_phi(phi0)
             ctxs.append(c)
@@ -364,7 +364,8 @@ def batched_small_sample(stream, n_images: int = 64, iters: int = 100) -> dict:
             c.close()
     out["how"] = ("sr_group_iterate: graph = one CUDA graph per parity with the members' "
                   "iterations as child graphs on tuned lanes; resident = every member "
-                  "set resident, all in one launch of one cluster per image")
+                  "set resident with 8-CTA clusters, all in one launch of one cluster "
+                  "per image")
     return out
 
 

@@ -235,10 +235,13 @@ sr_status sr_set_boundary(sr_ctx* ctx, int neumann);
  * outer iterations of Alg. 1 in ONE launch per call, with the whole state
  * (phi, w at both parities, e, g, div e, the right-hand side and the half
  * spectrum) held in the shared memory of one cluster of C CTAs -- CTA q owns
- * rows [q H/C, (q+1) H/C); C = 16 where H/16 >= 2 rows and the device
- * schedules clusters of 16, else 8 (the environment variable
- * SR_RESIDENT_CLUSTER = 8 or 16 fixes it) -- for all the iterations of the
- * call; neighbour
+ * rows [q H/C, (q+1) H/C); with on = 1, C = 16 where H/16 >= 2 rows and
+ * the device schedules clusters of 16, else 8 (the environment variable
+ * SR_RESIDENT_CLUSTER = 8 or 16 fixes it); on = 8 or 16 asks for that C
+ * (SR_EUNSUPPORTED if it does not fit).  16 gives one image the shortest
+ * iterations; 8 lets twice as many images run at once, which serves a group
+ * of many small images better -- for all the iterations of the call;
+ * neighbour
  * rows, window halos and the column recursions' warm-ups are read from the
  * other CTAs' shared memory (distributed shared memory), and the phases of an
  * iteration are separated by cluster barriers instead of kernel boundaries.

@@ -1634,7 +1634,7 @@ long long sr_kernel_launches(const sr_ctx* c, int reset) {
 }
 
 sr_status sr_set_resident(sr_ctx* c, int on) {
-  if (!c || on < 0 || on > 1) return SR_EINVAL;
+  if (!c || !(on == 0 || on == 1 || on == 8 || on == 16)) return SR_EINVAL;
   if (!on) {
     c->resident = 0;
     return SR_OK;
@@ -1647,7 +1647,9 @@ sr_status sr_set_resident(sr_ctx* c, int on) {
   // clusters of 16 CTAs where the rows divide and the device schedules them,
   // else 8; SR_RESIDENT_CLUSTER=8 or 16 fixes the choice
   std::vector<int> cands = {16, 8};
-  if (const char* env = std::getenv("SR_RESIDENT_CLUSTER")) {
+  if (on == 8 || on == 16) {
+    cands = {on};
+  } else if (const char* env = std::getenv("SR_RESIDENT_CLUSTER")) {
     const int v = std::atoi(env);
     if (v == 8 || v == 16) cands = {v};
   }

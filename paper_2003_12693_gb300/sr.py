@@ -298,10 +298,11 @@ class Context:
         """'periodic' (the default reading) or 'neumann' (Eq. (27) literally)."""
         _check(lib().sr_set_boundary(self.handle, {"periodic": 0, "neumann": 1}[boundary]), self)
 
-    def set_resident(self, on: bool = True):
+    def set_resident(self, on: bool = True, cluster: int | None = None):
         """sr_set_resident: outer iterations in one launch with the state in one
-        cluster's shared memory (small images)."""
-        _check(lib().sr_set_resident(self.handle, 1 if on else 0), self)
+        cluster's shared memory (small images); cluster = 8 or 16 asks for
+        that many CTAs per image."""
+        _check(lib().sr_set_resident(self.handle, (cluster or 1) if on else 0), self)
 
     def set_phi_solver(self, solver: str):
         """'fft' (Eqs. (31)-(33), default) or 'aos' (Eqs. (19)-(20) form)."""

@@ -154,6 +154,28 @@ def test_resident_switching_keeps_the_state():
         assert np.all((n == 0) | (np.abs(n - 1) < 1e-5))
 
 
+def test_resident_cluster_size_by_argument():
+    """sr_set_resident(ctx, 8 or 16) fixes the cluster size: the two runs
+    agree with the oracle's one-iteration bar and are refused where the rows
+    do not divide (16 CTAs need H >= 32)."""
+    wl = synth.WORKLOADS["two_disks_128"]
+    p = oracle.Params.from_dict(wl.params())
+    g64 = f32(oracle.edge(wl.image()))
+    state = rounded_state(oracle_state_after(wl.phi0(), g64, 10, p))
+    for cl in (8, 16):
+        ctx = context(wl.H, wl.W, R=wl.R, d=wl.d)
+        ctx.set_resident(True, cluster=cl)
+        gpu, ref = one_iteration_both(ctx, state, g64, p)
+        check_one_iteration(gpu, ref, state, g64, p)
+        ctx.close()
+    ctx = context(16, 32)
+    with pytest.raises(sr.SRError) as e:
+        ctx.set_resident(True, cluster=16)
+    assert e.value.status == sr.SR_EUNSUPPORTED
+    assert sr.lib().sr_set_resident(ctx.handle, 4) == sr.SR_EINVAL  # only 0, 1, 8, 16
+    ctx.close()
+
+
 def test_resident_unsupported_configurations():
     for shape in [(16, 512), (128, 512)]:
         ctx = context(*shape)
