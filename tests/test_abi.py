@@ -66,6 +66,15 @@ def test_null_arguments(srmod):
     assert L.sr_last_error(None) == b""
 
 
+def test_mode_entry_points_reject_null_context(srmod):
+    """The mode switches validate their context before any CUDA call."""
+    L = srmod.lib()
+    for on in (0, 1, 8, 16, 4):
+        assert L.sr_set_resident(None, on) == 1
+    assert L.sr_set_phi_solver(None, 1) == 1
+    assert L.sr_set_boundary(None, 1) == 1
+
+
 def test_w_sweep_entry_points_reject_null_context(srmod):
     L = srmod.lib()
     assert L.sr_set_w_sweeps(None, 2) == 1
