@@ -400,7 +400,9 @@ sr_status sr_test_fail_allocations(long long n);
  * on that member alone.  Members with resident iterations (sr_set_resident)
  * are not in the graphs: all of them run in one launch per row length and
  * cluster size (one cluster per member, the same kernel as sr_iterate's, so
- * also bit for bit), on the group's stream before the graphs.  There is no stopping test inside the group call
+ * also bit for bit), on the group's stream before the graphs.  The group
+ * takes each member's mode (resident or not, sweeps, solver, boundary) as it
+ * is at sr_group_create: change a member's mode before creating the group.  There is no stopping test inside the group call
  * (tol = 0 semantics); sr_iterate on a member afterwards gives its relative
  * change.  The members must be at the same parity: created or reset with
  * sr_set_phi / sr_set_state together and iterated only through the group, or
